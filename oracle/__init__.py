@@ -1,0 +1,266 @@
+"""Plain FP64 CPU oracle for the block-Vecchia log-likelihood (arXiv 2410.04477).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  It shares no code with the CUDA library in
+``paper_2410_04477_gb300``: the arithmetic lives in ``bv_oracle.c`` (compiled here with
+``gcc -O2 -ffp-contract=off -fopenmp``) and in the NumPy modules next to it.
+
+What each function follows (details in the C source):
+  matern_corr / cov       Eq. 5 (Matern), closed forms at nu = 1/2, 3/2, 5/2
+  kmeans / build_blocks   Sec. 2.1 + Algorithm 1 (clustering, block permutation)
+  select_neighbors        Sec. 2.2 + Algorithm 1 (nearest neighbours of each block)
+  block_loglik / loglik   Algorithm 1 (batched steps, literally) and Eq. 4
+  exact_loglik            Eq. 1
+  exact_draw / bv_draw    input generators: exact GP draw, block-Vecchia draw (Eq. 4)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bv_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/_build/liboracle.so (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Theta(ctypes.Structure):
+    """Covariance parameters theta = (sigma^2, beta, nu) of Eq. 5, plus a nugget."""
+    _fields_ = [("sigma2", ctypes.c_double), ("range", ctypes.c_double * 3),
+                ("nu", ctypes.c_double), ("nugget", ctypes.c_double),
+                ("aniso", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def theta(sigma2=1.0, beta=0.1, nu=0.5, nugget=0.0, ranges=None) -> Theta:
+    t = Theta()
+    t.sigma2 = float(sigma2)
+    t.nu = float(nu)
+    t.nugget = float(nugget)
+    if ranges is not None:
+        r = list(ranges) + [1.0] * (3 - len(ranges))
+        t.aniso = 1
+        for k in range(3):
+            t.range[k] = float(r[k])
+    else:
+        t.aniso = 0
+        t.range[0] = float(beta)
+        t.range[1] = t.range[2] = 1.0
+    return t
+
+
+_P = ctypes.POINTER
+_d, _i64, _i32, _u64, _int = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.or_splitmix64.restype = _u64
+            L.or_splitmix64.argtypes = [_u64, _u64]
+            L.or_bessel_k.restype = _d
+            L.or_bessel_k.argtypes = [_d, _d]
+            L.or_matern_corr.restype = _d
+            L.or_matern_corr.argtypes = [_d, _d]
+            L.or_cov.restype = _d
+            L.or_cov.argtypes = [_P(Theta), _int, _P(_d), _P(_d), _int]
+            L.or_block_loglik.restype = _d
+            L.or_block_loglik.argtypes = [_P(Theta), _P(_d), _P(_d), _int, _P(_i32), _i64,
+                                          _P(_i32), _i64, _P(_int)]
+            L.or_loglik.restype = _int
+            L.or_loglik.argtypes = [_P(Theta), _P(_d), _P(_d), _i64, _int, _i64, _P(_i64),
+                                    _P(_i32), _P(_i64), _P(_i32), _P(_d), _P(_d)]
+            L.or_exact_loglik.restype = _int
+            L.or_exact_loglik.argtypes = [_P(Theta), _P(_d), _P(_d), _i64, _int, _P(_d)]
+            L.or_exact_draw.restype = _int
+            L.or_exact_draw.argtypes = [_P(Theta), _P(_d), _i64, _int, _P(_d), _P(_d)]
+            L.or_bv_draw.restype = _int
+            L.or_bv_draw.argtypes = [_P(Theta), _P(_d), _i64, _int, _i64, _P(_i64), _P(_i32),
+                                     _P(_i64), _P(_i32), _P(_d), _P(_d)]
+            L.or_kmeans.restype = _int
+            L.or_kmeans.argtypes = [_P(_d), _i64, _int, _i64, _u64, _int, _P(_i32), _P(_d)]
+            L.or_build_blocks.restype = _i64
+            L.or_build_blocks.argtypes = [_P(_d), _i64, _int, _i64, _u64, _int, _P(_i64),
+                                          _P(_i32), _P(_d)]
+            L.or_select_neighbors.restype = _int
+            L.or_select_neighbors.argtypes = [_P(_d), _i64, _int, _i64, _P(_i64), _P(_i32),
+                                              _P(_d), _i32, _P(_i32), _P(_i64), _P(_i32)]
+            L.or_num_threads.restype = _int
+            L.or_num_threads.argtypes = []
+            _lib = L
+        return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(_P(ct)) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: oracle status {code}")
+        self.code = code
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def splitmix64(stream: int, counter: int) -> int:
+    return int(lib().or_splitmix64(stream, counter))
+
+
+def bessel_k(nu: float, x: float) -> float:
+    return float(lib().or_bessel_k(nu, x))
+
+
+def matern_corr(nu: float, x) -> np.ndarray:
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    f = lib().or_matern_corr
+    return np.array([f(nu, float(v)) for v in x.ravel()]).reshape(x.shape)
+
+
+def cov(th: Theta, si, sj, same: bool) -> float:
+    si = _c(si, np.float64)
+    sj = _c(sj, np.float64)
+    return float(lib().or_cov(ctypes.byref(th), si.size, _ptr(si, _d), _ptr(sj, _d), int(same)))
+
+
+def kmeans(locs, k, seed, iters=20):
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    label = np.empty(n, np.int32)
+    cent = np.empty((k, d), np.float64)
+    st = lib().or_kmeans(_ptr(locs, _d), n, d, k, seed, iters, _ptr(label, _i32), _ptr(cent, _d))
+    if st:
+        raise OracleError(st, "kmeans")
+    return label, cent
+
+
+def build_blocks(locs, bc, seed, iters=20):
+    """K-means blocks in the random permuted order: (block_ptr, point_idx, centroids)."""
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    bp = np.empty(bc + 1, np.int64)
+    pi = np.empty(n, np.int32)
+    ce = np.empty((bc, d), np.float64)
+    nb = lib().or_build_blocks(_ptr(locs, _d), n, d, bc, seed, iters, _ptr(bp, _i64),
+                               _ptr(pi, _i32), _ptr(ce, _d))
+    if nb < 0:
+        raise OracleError(-nb, "build_blocks")
+    return bp[:nb + 1].copy(), pi, ce[:nb].copy()
+
+
+def select_neighbors(locs, block_ptr, point_idx, centroids, m, m_per_block=None):
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    bp = _c(block_ptr, np.int64)
+    pi = _c(point_idx, np.int32)
+    ce = _c(centroids, np.float64)
+    bc = bp.size - 1
+    mp = _c(m_per_block, np.int32) if m_per_block is not None else None
+    nnp = np.empty(bc + 1, np.int64)
+    L = lib()
+    st = L.or_select_neighbors(_ptr(locs, _d), n, d, bc, _ptr(bp, _i64), _ptr(pi, _i32),
+                               _ptr(ce, _d), int(m), _ptr(mp, _i32), _ptr(nnp, _i64), None)
+    if st:
+        raise OracleError(st, "select_neighbors")
+    nni = np.empty(max(int(nnp[-1]), 1), np.int32)
+    st = L.or_select_neighbors(_ptr(locs, _d), n, d, bc, _ptr(bp, _i64), _ptr(pi, _i32),
+                               _ptr(ce, _d), int(m), _ptr(mp, _i32), _ptr(nnp, _i64),
+                               _ptr(nni, _i32))
+    if st:
+        raise OracleError(st, "select_neighbors")
+    return nnp, nni[:int(nnp[-1])].copy()
+
+
+def loglik(th: Theta, locs, y, block_ptr, point_idx, nn_ptr, nn_idx, check=True):
+    """Block-Vecchia log-likelihood (Eq. 4 by Algorithm 1): (ell, per_block, status)."""
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    y = _c(y, np.float64)
+    bp, pi = _c(block_ptr, np.int64), _c(point_idx, np.int32)
+    nnp = _c(nn_ptr, np.int64)
+    nni = _c(nn_idx, np.int32) if len(nn_idx) else np.zeros(1, np.int32)
+    bc = bp.size - 1
+    out = np.zeros(1)
+    per = np.zeros(bc)
+    st = lib().or_loglik(ctypes.byref(th), _ptr(locs, _d), _ptr(y, _d), n, d, bc, _ptr(bp, _i64),
+                         _ptr(pi, _i32), _ptr(nnp, _i64), _ptr(nni, _i32), _ptr(out, _d),
+                         _ptr(per, _d))
+    if check and st:
+        raise OracleError(st, "loglik")
+    return float(out[0]), per, int(st)
+
+
+def block_loglik(th: Theta, locs, y, nn, blk):
+    locs = _c(locs, np.float64)
+    y = _c(y, np.float64)
+    m = len(nn)
+    nn = _c(nn, np.int32) if m else np.zeros(1, np.int32)
+    blk = _c(blk, np.int32)
+    st = ctypes.c_int(0)
+    v = lib().or_block_loglik(ctypes.byref(th), _ptr(locs, _d), _ptr(y, _d), locs.shape[1],
+                              _ptr(nn, _i32), m, _ptr(blk, _i32), blk.size, ctypes.byref(st))
+    return float(v), int(st.value)
+
+
+def exact_loglik(th: Theta, locs, y):
+    locs = _c(locs, np.float64)
+    y = _c(y, np.float64)
+    out = np.zeros(1)
+    st = lib().or_exact_loglik(ctypes.byref(th), _ptr(locs, _d), _ptr(y, _d), locs.shape[0],
+                               locs.shape[1], _ptr(out, _d))
+    if st:
+        raise OracleError(st, "exact_loglik")
+    return float(out[0])
+
+
+def exact_draw(th: Theta, locs, z):
+    locs = _c(locs, np.float64)
+    z = _c(z, np.float64)
+    y = np.empty_like(z)
+    st = lib().or_exact_draw(ctypes.byref(th), _ptr(locs, _d), locs.shape[0], locs.shape[1],
+                             _ptr(z, _d), _ptr(y, _d))
+    if st:
+        raise OracleError(st, "exact_draw")
+    return y
+
+
+def bv_draw(th: Theta, locs, block_ptr, point_idx, nn_ptr, nn_idx, z):
+    locs = _c(locs, np.float64)
+    z = _c(z, np.float64)
+    bp, pi = _c(block_ptr, np.int64), _c(point_idx, np.int32)
+    nnp = _c(nn_ptr, np.int64)
+    nni = _c(nn_idx, np.int32) if len(nn_idx) else np.zeros(1, np.int32)
+    y = np.zeros_like(z)
+    st = lib().or_bv_draw(ctypes.byref(th), _ptr(locs, _d), locs.shape[0], locs.shape[1],
+                          bp.size - 1, _ptr(bp, _i64), _ptr(pi, _i32), _ptr(nnp, _i64),
+                          _ptr(nni, _i32), _ptr(z, _d), _ptr(y, _d))
+    if st:
+        raise OracleError(st, "bv_draw")
+    return y

@@ -1,0 +1,145 @@
+"""Pins for the oracle's preprocessing: K-means blocks, the block order and the block
+nearest-neighbour sets (Sec. 2.1-2.2, Algorithm 1)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+
+
+def _d2(x, c):
+    # D2 written out independently: (x0-c0)^2 + (x1-c1)^2 + ... left to right
+    acc = np.zeros(x.shape[0]) if x.ndim == 2 else 0.0
+    for k in range(c.shape[-1]):
+        t = (x[..., k] - c[..., k])
+        acc = acc + t * t
+    return acc
+
+
+@pytest.mark.parametrize("n,d,k", [(600, 2, 40), (500, 3, 25)])
+def test_kmeans_final_assignment_is_nearest_centre(n, d, k):
+    locs = synth.locs_uniform(n, d, seed=11)
+    label, cent = oracle.kmeans(locs, k, seed=5, iters=20)
+    D = np.stack([_d2(locs, cent[c][None, :]) for c in range(k)], axis=1)
+    np.testing.assert_array_equal(label, np.argmin(D, axis=1))
+
+
+def test_kmeans_matches_library_lloyd_from_same_seeding():
+    sk = pytest.importorskip("sklearn.cluster")
+    locs = synth.locs_uniform(800, 2, seed=2)
+    k = 30
+    # seeding only (0 Lloyd iterations) gives the k-means++ centres
+    _, init = oracle.kmeans(locs, k, seed=9, iters=0)
+    label, cent = oracle.kmeans(locs, k, seed=9, iters=15)
+    km = sk.KMeans(n_clusters=k, init=init, n_init=1, max_iter=15, tol=0.0,
+                   algorithm="lloyd").fit(locs)
+    assert (km.labels_ == label).mean() > 0.99
+    np.testing.assert_allclose(km.cluster_centers_, cent, atol=1e-9)
+
+
+def test_kmeans_inertia_non_increasing():
+    locs = synth.locs_uniform(700, 2, seed=4)
+    prev = np.inf
+    for it in range(0, 12):
+        label, cent = oracle.kmeans(locs, 35, seed=1, iters=it)
+        # inertia of the centres after `it` updates, with their own optimal labels
+        D = np.stack([_d2(locs, cent[c][None, :]) for c in range(35)], axis=1)
+        inertia = D.min(axis=1).sum()
+        assert inertia <= prev * (1 + 1e-12)
+        prev = inertia
+
+
+def test_kmeanspp_first_centre_and_distinct_seeds():
+    locs = synth.locs_uniform(300, 2, seed=8)
+    _, c0 = oracle.kmeans(locs, 1, seed=77, iters=0)
+    r0 = oracle.splitmix64(77 ^ 0x6B6D65616E732B2B, 0)
+    first = (r0 * 300) >> 64
+    np.testing.assert_array_equal(c0[0], locs[first])
+    _, c = oracle.kmeans(locs, 50, seed=77, iters=0)
+    # k-means++ never picks an already chosen point while unchosen points have D2 > 0
+    assert len({tuple(v) for v in c}) == 50
+
+
+@pytest.mark.parametrize("n,d,bc", [(2000, 2, 200), (900, 3, 90)])
+def test_blocks_partition_and_centroids(n, d, bc):
+    locs = synth.locs_uniform(n, d, seed=0)
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=0, iters=20)
+    nb = len(bp) - 1
+    assert nb <= bc and nb > 0.9 * bc
+    assert bp[0] == 0 and bp[-1] == n and np.all(np.diff(bp) >= 1)
+    np.testing.assert_array_equal(np.sort(pi), np.arange(n))      # each point once
+    for i in range(nb):
+        mem = pi[bp[i]:bp[i + 1]]
+        assert np.all(np.diff(mem) > 0)                            # ascending index
+        np.testing.assert_allclose(ce[i], locs[mem].mean(axis=0), atol=1e-12)
+    # blocks are K-means clusters: every point is nearest to its own block centroid
+    D = np.stack([_d2(locs, ce[i][None, :]) for i in range(nb)], axis=1)
+    own = np.empty(n, np.int64)
+    for i in range(nb):
+        own[pi[bp[i]:bp[i + 1]]] = i
+    # the centroids here are the means of the final members, one update after the final
+    # labels, so allow the few points that a last Lloyd step would still move
+    assert (np.argmin(D, axis=1) == own).mean() > 0.97
+
+
+def test_block_order_is_a_seeded_permutation():
+    locs = synth.locs_uniform(1000, 2, seed=3)
+    a = oracle.build_blocks(locs, 100, seed=1)
+    b = oracle.build_blocks(locs, 100, seed=1)
+    c = oracle.build_blocks(locs, 100, seed=2)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert not np.array_equal(a[1], c[1])
+
+
+def _brute_nn(locs, bp, pi, ce, m):
+    out = []
+    for i in range(len(bp) - 1):
+        cand = pi[:bp[i]].astype(np.int64)
+        if len(cand) == 0:
+            out.append(np.zeros(0, np.int64))
+            continue
+        d2 = _d2(locs[cand], ce[i][None, :])
+        order = np.lexsort((cand, d2))
+        out.append(cand[order[:min(m, len(cand))]])
+    return out
+
+
+@pytest.mark.parametrize("n,d,bc,m", [(2000, 2, 200, 30), (800, 3, 80, 50), (300, 2, 30, 400)])
+def test_neighbors_match_brute_force(n, d, bc, m):
+    locs = synth.locs_uniform(n, d, seed=5)
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=3)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+    want = _brute_nn(locs, bp, pi, ce, m)
+    assert nnp[0] == 0 and nnp[1] == 0                             # first block: none
+    for i, w in enumerate(want):
+        np.testing.assert_array_equal(nni[nnp[i]:nnp[i + 1]], w)
+        assert nnp[i + 1] - nnp[i] == min(m, bp[i])
+        earlier = set(pi[:bp[i]].tolist())
+        assert set(nni[nnp[i]:nnp[i + 1]].tolist()) <= earlier
+
+
+def test_neighbors_nested_in_m_and_per_block_sizes():
+    locs = synth.locs_uniform(1200, 2, seed=6)
+    bp, pi, ce = oracle.build_blocks(locs, 120, seed=4)
+    p10, i10 = oracle.select_neighbors(locs, bp, pi, ce, 10)
+    p40, i40 = oracle.select_neighbors(locs, bp, pi, ce, 40)
+    for b in range(len(bp) - 1):
+        a = i10[p10[b]:p10[b + 1]]
+        np.testing.assert_array_equal(a, i40[p40[b]:p40[b]+len(a)])
+    mpb = (np.arange(len(bp) - 1) % 7 * 5).astype(np.int32)
+    pv, iv = oracle.select_neighbors(locs, bp, pi, ce, -1, m_per_block=mpb)
+    for b in range(len(bp) - 1):
+        assert pv[b + 1] - pv[b] == min(mpb[b], bp[b])
+        np.testing.assert_array_equal(iv[pv[b]:pv[b + 1]], i40[p40[b]:p40[b] + pv[b + 1] - pv[b]])
+
+
+def test_ties_broken_by_index():
+    # a lattice puts many candidates at exactly the same distance from a centroid
+    g = np.arange(8) / 8.0
+    locs = np.array([(x, y) for x in g for y in g])
+    bp, pi, ce = oracle.build_blocks(locs, 16, seed=1)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 9)
+    want = _brute_nn(locs, bp, pi, ce, 9)
+    for i, w in enumerate(want):
+        np.testing.assert_array_equal(nni[nnp[i]:nnp[i + 1]], w)
