@@ -1,0 +1,229 @@
+/*
+ * bv.h -- C ABI of the GB300-native block-Vecchia Gaussian-process library.
+ *
+ * The library evaluates the block-Vecchia approximation of the Gaussian log-likelihood
+ * (Pan, Abdulah, Genton, Sun, "Block Vecchia Approximation for Scalable and Efficient
+ * Gaussian Process Computations", arXiv 2410.04477):
+ *
+ *   ell(theta) = sum_i log p(y_{B_i} | y_{NN_i})                      (Eq. 4)
+ *
+ * over K-means blocks B_i taken in a random block order, each conditioned on the m_i
+ * nearest points of earlier blocks, with the Matern covariance of Eq. 5 plus a nugget.
+ * The per-block steps are those of Algorithm 1; the library computes them fused on the
+ * GPU (sm_103a).
+ *
+ * Conventions (all entry points):
+ *   - Return value: a bv_status code (BV_OK = 0).  bv_strerror() describes it.
+ *   - Pointers are host pointers unless an argument says "device".  The caller owns
+ *     every buffer it passes; the library copies inputs in and writes outputs to the
+ *     caller's buffers.  The context owns all device memory it allocates and frees it
+ *     in bv_destroy().
+ *   - Work is issued on the context's stream (the one given to bv_create, or a stream
+ *     the context creates).  Calls marked "synchronous" return after the stream drains.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ *   - Indices are 0-based.  Point indices refer to the rows of the location array.
+ */
+#ifndef BV_H
+#define BV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bv_ctx bv_ctx;
+
+/* Covariance parameters theta = (sigma^2, beta, nu) of Eq. 5, plus an absolute nugget
+ * tau^2 added to the diagonal (the same observation with itself).  With aniso = 0 the
+ * range is range[0] and distances are Euclidean (Eq. 5); with aniso = 1 the scaled
+ * distance is sqrt(sum_k ((s_ik - s_jk) / range[k])^2).  Supported smoothness: nu in
+ * {0.5, 1.5, 2.5} (the paper's low / medium / high smoothness, Sec. 3.1). */
+typedef struct bv_theta {
+    double sigma2;
+    double range[3];
+    double nu;
+    double nugget;
+    int32_t aniso;
+    int32_t reserved;
+} bv_theta;
+
+typedef enum bv_status {
+    BV_OK = 0,
+    BV_EINVAL = 1,    /* invalid argument (size, pointer, theta outside its domain)      */
+    BV_ENOMEM = 2,    /* device or host allocation failed                                 */
+    BV_ECUDA = 3,     /* a CUDA runtime call failed (bv_last_cuda_error has the text)     */
+    BV_ENOTPD = 4,    /* a block's covariance was not positive definite; ell = -inf       */
+    BV_ETIMEOUT = 5,  /* a bounded device wait gave up                                    */
+    BV_ESTATE = 6,    /* call out of order (e.g. no data, no blocks, no neighbours yet)   */
+    BV_EINTERNAL = 7  /* internal consistency check failed                                */
+} bv_status;
+
+typedef enum bv_precision {
+    BV_FP64 = 0,  /* every step in FP64                                                    */
+    BV_MIXED = 1  /* covariance generation, triangular solves and Schur-complement updates
+                     in FP32; pivots, log-determinant and quadratic form in FP64           */
+} bv_precision;
+
+/* ---- context -------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to issue
+ * work on, or NULL for a stream owned by the context. */
+int bv_create(bv_ctx** out, int device, void* cuda_stream);
+void bv_destroy(bv_ctx* ctx);
+const char* bv_strerror(int status);
+/* Text of the last failing CUDA call in this process (empty if none). */
+const char* bv_last_cuda_error(void);
+
+/* ---- data ----------------------------------------------------------------------- */
+
+/* One dataset: n locations s_1..s_n in R^d (row-major n x d, d in 1..3) and the
+ * observations y (length n, zero-mean model, Sec. 1; may be NULL and set later).
+ * Synchronous.  Replaces any previous data and drops blocks and neighbours. */
+int bv_set_data(bv_ctx* ctx, const double* locs, const double* y, int64_t n, int32_t d);
+
+/* Several independent datasets evaluated together (one batched launch).  Dataset k has
+ * n_per[k] points; `locs` (sum n_per x d, row-major) and `y` (sum n_per, may be NULL)
+ * hold the datasets one after another.  Point indices in all later calls are global
+ * (into the concatenation). */
+int bv_set_datasets(bv_ctx* ctx, int32_t ndatasets, const int64_t* n_per,
+                    const double* locs, const double* y, int32_t d);
+
+/* Replace the observations (all datasets, concatenated).  `y` is a host pointer, or a
+ * device pointer when y_on_device != 0 (then the copy is asynchronous on the stream). */
+int bv_set_observations(bv_ctx* ctx, const double* y, int32_t y_on_device);
+
+/* ---- preprocessing (one-time; excluded from the timed evaluation, Sec. 3.1) ------ */
+
+/* K-means blocks (Sec. 2.1; Algorithm 1 "Clustering" and "Block permutation"):
+ * k-means++ seeding and `lloyd_iters` Lloyd iterations into bc clusters, empty clusters
+ * dropped, then a random block order zeta.  Deterministic in (locations, bc, seed,
+ * lloyd_iters); bit-identical to the reference definition (exact-integer centroid sums,
+ * squared distances without fused multiply-add, lowest-index ties).  Outputs (may be
+ * NULL): block_ptr[bc_eff+1] and point_idx[n] in block order (block p holds
+ * point_idx[block_ptr[p] .. block_ptr[p+1]), ascending point index inside a block);
+ * *bc_eff the number of non-empty blocks.  Synchronous. */
+int bv_build_blocks(bv_ctx* ctx, int64_t bc, uint64_t seed, int32_t lloyd_iters,
+                    int64_t* block_ptr, int32_t* point_idx, int64_t* bc_eff);
+
+/* Multi-dataset form: dataset k gets bc_per[k] clusters (seeded with seed + k).
+ * bc_eff_per[k] (may be NULL) receives its number of blocks.  Blocks are stored dataset
+ * after dataset. */
+int bv_build_blocks_multi(bv_ctx* ctx, const int64_t* bc_per, uint64_t seed,
+                          int32_t lloyd_iters, int64_t* bc_eff_per);
+
+/* Caller-supplied partition (Algorithm 1 input g and zeta) for the single-dataset case:
+ * bc blocks in the order to evaluate, block_ptr[bc+1], point_idx[n] (a permutation of
+ * 0..n-1), centroids[bc x d] (the query points of the neighbour search; NULL = member
+ * means). */
+int bv_set_blocks(bv_ctx* ctx, int64_t bc, const int64_t* block_ptr, const int32_t* point_idx,
+                  const double* centroids);
+
+/* Block nearest neighbours (Sec. 2.2; Algorithm 1 "Nearest neighbors"): for the block at
+ * position i, the m_i points of blocks 0..i-1 nearest to its centroid, keyed by
+ * (squared distance, point index), m_i = min(m or m_per_block[i], available points).
+ * Bit-identical to the reference definition.  Outputs (may be NULL): nn_ptr[bc_eff+1]
+ * and nn_idx[nn_ptr[bc_eff]] (ascending key order inside a block).  Synchronous. */
+int bv_select_neighbors(bv_ctx* ctx, int32_t m, const int32_t* m_per_block,
+                        int64_t* nn_ptr, int32_t* nn_idx);
+
+/* Caller-supplied conditioning sets (Algorithm 1 input m_1..m_bc with the sets). */
+int bv_set_neighbors(bv_ctx* ctx, const int64_t* nn_ptr, const int32_t* nn_idx);
+
+/* Sizes of the current structure: number of blocks and total conditioning entries. */
+int bv_get_sizes(bv_ctx* ctx, int64_t* n_blocks, int64_t* n_nn_entries);
+
+/* Copy the current structure out (any pointer may be NULL). */
+int bv_get_blocks(bv_ctx* ctx, int64_t* block_ptr, int32_t* point_idx, double* centroids);
+int bv_get_neighbors(bv_ctx* ctx, int64_t* nn_ptr, int32_t* nn_idx);
+
+/* ---- evaluation (the hot path) -------------------------------------------------- */
+
+/* Block-Vecchia log-likelihood (Eq. 4 by Algorithm 1) of dataset 0 at theta.
+ * out_loglik: the scalar ell.  out_per_block (may be NULL): the bc_eff per-block
+ * conditional log-likelihoods.  On a non-positive-definite block returns BV_ENOTPD and
+ * sets *out_loglik = -INFINITY.  Synchronous. */
+int bv_loglik(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_loglik,
+              double* out_per_block);
+
+/* All datasets at once: thetas[ndatasets] (host), out_loglik[ndatasets] (host).
+ * Synchronous. */
+int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
+                    double* out_loglik);
+
+/* Asynchronous form for callers that keep the result on the device: enqueues one
+ * evaluation of every dataset on the context's stream and writes ell to
+ * d_out_loglik[ndatasets] (device).  No host synchronisation; status is checked by the
+ * next synchronous call or bv_sync().  The enqueued sequence is a CUDA graph captured
+ * on first use for each precision. */
+int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
+                    double* d_out_loglik);
+
+/* Wait for the context's stream; report any device-side failure since the last check
+ * (BV_ENOTPD with the first failing block in *failed_block, may be NULL). */
+int bv_sync(bv_ctx* ctx, int64_t* failed_block);
+
+/* Run the launch-shape autotuner for `precision` now (otherwise it runs on first use).
+ * Times each candidate shape of every size bin on the current structure. */
+int bv_autotune(bv_ctx* ctx, int32_t precision);
+
+/* Launch plan of one evaluation at `precision` (built on demand): number of kernel
+ * launches per evaluation, number of size bins, and the algorithmic work of one
+ * evaluation, sum over blocks of (N^3/3 + N^2) flops with N = m_i + b_i (the Cholesky of
+ * the augmented matrix plus its forward solve), and the number of covariance entries
+ * generated, sum of N(N+1)/2.  Any output pointer may be NULL. */
+int bv_plan_info(bv_ctx* ctx, int32_t precision, int32_t* launches_per_eval, int32_t* n_bins,
+                 double* flops_per_eval, double* cov_entries_per_eval);
+
+/* ---- block-Vecchia sampler (Eq. 4 read generatively) ------------------------------ */
+
+/* Draw y from the block-Vecchia model of dataset 0 at theta with the current blocks and
+ * neighbours: blocks in order, y_{B_i} = mu_i(y_{NN_i}) + chol(Sigma^new_i) z_{B_i}.
+ * z[n] (host) holds standard normals indexed by point; y_out[n] (host, may be NULL)
+ * receives the draw, which also becomes the context's observations.  Synchronous. */
+int bv_simulate(bv_ctx* ctx, const bv_theta* theta, const double* z, double* y_out);
+
+/* ---- maximum likelihood --------------------------------------------------------- */
+
+/* Bits of bv_mle's free_mask: which parameters the optimizer moves (others stay at
+ * theta0).  Ranges move together (anisotropic ranges keep their ratios). */
+enum { BV_FREE_SIGMA2 = 1, BV_FREE_RANGE = 2, BV_FREE_NUGGET = 4 };
+
+typedef struct bv_mle_opts {
+    int32_t precision;   /* bv_precision of every evaluation                         */
+    int32_t max_evals;   /* hard cap on log-likelihood evaluations (e.g. 2000)         */
+    double ftol_rel;     /* stop when the simplex's ell spread < ftol_rel * |ell|      */
+    double xtol;         /* ... and its log-parameter spread < xtol                     */
+    double init_step;    /* initial simplex step in log-parameter units (e.g. 0.5)     */
+} bv_mle_opts;
+
+/* Maximise ell over log(sigma^2), log(beta), log(tau^2) (free_mask selects) inside the
+ * box [lo, hi] by a bounded Nelder-Mead search (derivative-free, as the paper's BOBYQA,
+ * Sec. 3.2).  theta0: start point.  Outputs: theta_hat, loglik_hat, n_evals.
+ * Synchronous (one device evaluation per optimizer step). */
+int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+           uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
+           double* loglik_hat, int32_t* n_evals);
+
+/* ---- learned warm start --------------------------------------------------------- */
+
+/* Number of summary features per dataset: a 32-bin empirical semivariogram on
+ * (0, 0.5] plus 8 statistics (log variance of y, block-size mean/std/min/max, mean
+ * conditioning size, log n, dimension). */
+#define BV_NFEAT 40
+
+/* Features of every dataset in the context (GPU), out[ndatasets x BV_NFEAT] (host).
+ * The semivariogram uses a seeded subsample of min(n, max_points) points. */
+int bv_features(bv_ctx* ctx, int32_t max_points, uint64_t seed, float* out);
+
+/* Predict a starting theta for dataset 0 with the warm-start MLP whose weights were
+ * loaded by bv_warmstart_load (nu is taken from theta_in, which also supplies aniso
+ * flags; sigma^2, range and nugget are predicted).  Synchronous. */
+int bv_warmstart_load(bv_ctx* ctx, const char* weights_path);
+int bv_warmstart_predict(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BV_H */

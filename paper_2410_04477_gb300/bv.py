@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the C ABI in include/bv.h (same names, argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libbv.so``; there is no CPU fallback.
+Importing this module raises if the library has not been built, and every call raises
+``BVError`` on a non-OK status.  ``Context`` wraps one ``bv_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbv.so")
+
+BV_OK, BV_EINVAL, BV_ENOMEM, BV_ECUDA, BV_ENOTPD, BV_ETIMEOUT, BV_ESTATE, BV_EINTERNAL = range(8)
+BV_FP64, BV_MIXED = 0, 1
+BV_FREE_SIGMA2, BV_FREE_RANGE, BV_FREE_NUGGET = 1, 2, 4
+BV_NFEAT = 40
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class bv_theta(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("range", ctypes.c_double * 3),
+                ("nu", ctypes.c_double), ("nugget", ctypes.c_double),
+                ("aniso", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class bv_mle_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_evals", ctypes.c_int32),
+                ("ftol_rel", ctypes.c_double), ("xtol", ctypes.c_double),
+                ("init_step", ctypes.c_double)]
+
+
+def theta(sigma2=1.0, beta=0.1, nu=0.5, nugget=0.0, ranges=None) -> bv_theta:
+    t = bv_theta()
+    t.sigma2, t.nu, t.nugget = float(sigma2), float(nu), float(nugget)
+    if ranges is not None:
+        r = list(ranges) + [1.0] * (3 - len(ranges))
+        t.aniso = 1
+        for k in range(3):
+            t.range[k] = float(r[k])
+    else:
+        t.aniso = 0
+        t.range[0] = float(beta)
+        t.range[1] = t.range[2] = float(beta)
+    return t
+
+
+def theta_tuple(t: bv_theta):
+    return dict(sigma2=t.sigma2, range=list(t.range), nu=t.nu, nugget=t.nugget, aniso=t.aniso)
+
+
+_P = ctypes.POINTER
+_d, _f, _i64, _i32, _u64, _u32, _int, _vp = (ctypes.c_double, ctypes.c_float, ctypes.c_int64,
+                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
+                                             ctypes.c_int, ctypes.c_void_p)
+
+_SIGS = {
+    "bv_create": (_int, [_P(_vp), _int, _vp]),
+    "bv_destroy": (None, [_vp]),
+    "bv_strerror": (ctypes.c_char_p, [_int]),
+    "bv_last_cuda_error": (ctypes.c_char_p, []),
+    "bv_set_data": (_int, [_vp, _P(_d), _P(_d), _i64, _i32]),
+    "bv_set_datasets": (_int, [_vp, _i32, _P(_i64), _P(_d), _P(_d), _i32]),
+    "bv_set_observations": (_int, [_vp, _vp, _i32]),
+    "bv_build_blocks": (_int, [_vp, _i64, _u64, _i32, _P(_i64), _P(_i32), _P(_i64)]),
+    "bv_build_blocks_multi": (_int, [_vp, _P(_i64), _u64, _i32, _P(_i64)]),
+    "bv_set_blocks": (_int, [_vp, _i64, _P(_i64), _P(_i32), _P(_d)]),
+    "bv_select_neighbors": (_int, [_vp, _i32, _P(_i32), _P(_i64), _P(_i32)]),
+    "bv_set_neighbors": (_int, [_vp, _P(_i64), _P(_i32)]),
+    "bv_get_sizes": (_int, [_vp, _P(_i64), _P(_i64)]),
+    "bv_get_blocks": (_int, [_vp, _P(_i64), _P(_i32), _P(_d)]),
+    "bv_get_neighbors": (_int, [_vp, _P(_i64), _P(_i32)]),
+    "bv_loglik": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d)]),
+    "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
+    "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
+    "bv_sync": (_int, [_vp, _P(_i64)]),
+    "bv_autotune": (_int, [_vp, _i32]),
+    "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
+    "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
+    "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
+                      _P(bv_theta), _P(_d), _P(_i32)]),
+    "bv_features": (_int, [_vp, _i32, _u64, _P(_f)]),
+    "bv_warmstart_load": (_int, [_vp, ctypes.c_char_p]),
+    "bv_warmstart_predict": (_int, [_vp, _P(bv_theta), _P(bv_theta)]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class BVError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.bv_strerror(status).decode()
+        if status == BV_ECUDA:
+            msg += ": " + _lib.bv_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(st, where, allow=()):
+    if st != BV_OK and st not in allow:
+        raise BVError(st, where)
+    return st
+
+
+def _p(a, ct):
+    return None if a is None else a.ctypes.data_as(_P(ct))
+
+
+def _arr(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Context:
+    """One bv_ctx on a CUDA device (its own stream unless `stream` is given)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        h = _vp()
+        _check(_lib.bv_create(ctypes.byref(h), device, stream), "bv_create")
+        self.h = h
+        self.n = 0
+        self.d = 0
+        self.ndata = 0
+
+    def close(self):
+        if self.h:
+            _lib.bv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # data -----------------------------------------------------------------------------
+    def set_data(self, locs, y=None):
+        locs = _arr(locs, np.float64)
+        n, d = locs.shape
+        yv = None if y is None else _arr(y, np.float64)
+        _check(_lib.bv_set_data(self.h, _p(locs, _d), _p(yv, _d), n, d), "bv_set_data")
+        self.n, self.d, self.ndata = n, d, 1
+
+    def set_datasets(self, locs_list, y_list=None):
+        n_per = np.array([len(l) for l in locs_list], np.int64)
+        locs = _arr(np.concatenate(locs_list), np.float64)
+        d = locs.shape[1]
+        yv = None if y_list is None else _arr(np.concatenate(y_list), np.float64)
+        _check(_lib.bv_set_datasets(self.h, len(locs_list), _p(n_per, _i64), _p(locs, _d),
+                                    _p(yv, _d), d), "bv_set_datasets")
+        self.n, self.d, self.ndata = int(n_per.sum()), d, len(locs_list)
+
+    def set_observations(self, y=None, device_ptr: int | None = None):
+        if device_ptr is not None:
+            _check(_lib.bv_set_observations(self.h, device_ptr, 1), "bv_set_observations")
+        else:
+            yv = _arr(y, np.float64)
+            _check(_lib.bv_set_observations(self.h, yv.ctypes.data, 0), "bv_set_observations")
+
+    # preprocessing ------------------------------------------------------------------------
+    def build_blocks(self, bc, seed=0, iters=20):
+        bp = np.empty(bc + 1, np.int64)
+        pi = np.empty(self.n, np.int32)
+        nb = ctypes.c_int64(0)
+        _check(_lib.bv_build_blocks(self.h, bc, seed, iters, _p(bp, _i64), _p(pi, _i32),
+                                    ctypes.byref(nb)), "bv_build_blocks")
+        return bp[:nb.value + 1].copy(), pi
+
+    def build_blocks_multi(self, bc_per, seed=0, iters=20):
+        bc = _arr(bc_per, np.int64)
+        out = np.empty(len(bc), np.int64)
+        _check(_lib.bv_build_blocks_multi(self.h, _p(bc, _i64), seed, iters, _p(out, _i64)),
+               "bv_build_blocks_multi")
+        return out
+
+    def set_blocks(self, block_ptr, point_idx, centroids=None):
+        bp = _arr(block_ptr, np.int64)
+        pi = _arr(point_idx, np.int32)
+        ce = None if centroids is None else _arr(centroids, np.float64)
+        _check(_lib.bv_set_blocks(self.h, len(bp) - 1, _p(bp, _i64), _p(pi, _i32), _p(ce, _d)),
+               "bv_set_blocks")
+
+    def select_neighbors(self, m, m_per_block=None):
+        nb, _ = self.sizes()
+        mp = None if m_per_block is None else _arr(m_per_block, np.int32)
+        nnp = np.empty(nb + 1, np.int64)
+        _check(_lib.bv_select_neighbors(self.h, int(m), _p(mp, _i32), _p(nnp, _i64), None),
+               "bv_select_neighbors")
+        return self.neighbors()
+
+    def set_neighbors(self, nn_ptr, nn_idx):
+        nnp = _arr(nn_ptr, np.int64)
+        nni = _arr(nn_idx, np.int32) if len(nn_idx) else np.zeros(1, np.int32)
+        _check(_lib.bv_set_neighbors(self.h, _p(nnp, _i64), _p(nni, _i32)), "bv_set_neighbors")
+
+    def sizes(self):
+        nb, nn = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(_lib.bv_get_sizes(self.h, ctypes.byref(nb), ctypes.byref(nn)), "bv_get_sizes")
+        return nb.value, nn.value
+
+    def blocks(self):
+        nb, _ = self.sizes()
+        bp = np.empty(nb + 1, np.int64)
+        pi = np.empty(self.n, np.int32)
+        ce = np.empty((nb, self.d), np.float64)
+        _check(_lib.bv_get_blocks(self.h, _p(bp, _i64), _p(pi, _i32), _p(ce, _d)), "bv_get_blocks")
+        return bp, pi, ce
+
+    def neighbors(self):
+        nb, nn = self.sizes()
+        nnp = np.empty(nb + 1, np.int64)
+        nni = np.empty(max(nn, 1), np.int32)
+        _check(_lib.bv_get_neighbors(self.h, _p(nnp, _i64), _p(nni, _i32)), "bv_get_neighbors")
+        return nnp, nni[:nn].copy()
+
+    # evaluation -------------------------------------------------------------------------
+    def loglik(self, th: bv_theta, precision=BV_FP64, per_block=False, allow_notpd=False):
+        out = ctypes.c_double(0.0)
+        nb, _ = self.sizes()
+        per = np.empty(nb, np.float64) if per_block else None
+        st = _check(_lib.bv_loglik(self.h, ctypes.byref(th), precision, ctypes.byref(out),
+                                   _p(per, _d)), "bv_loglik",
+                    allow=(BV_ENOTPD,) if allow_notpd else ())
+        if per_block:
+            return out.value, per, st
+        return out.value
+
+    def loglik_multi(self, thetas, precision=BV_FP64, allow_notpd=False):
+        arr = (bv_theta * len(thetas))(*thetas)
+        out = np.empty(len(thetas), np.float64)
+        _check(_lib.bv_loglik_multi(self.h, arr, precision, _p(out, _d)), "bv_loglik_multi",
+               allow=(BV_ENOTPD,) if allow_notpd else ())
+        return out
+
+    def loglik_async(self, thetas, precision, d_out_ptr: int):
+        arr = (bv_theta * len(thetas))(*thetas)
+        _check(_lib.bv_loglik_async(self.h, arr, precision, d_out_ptr), "bv_loglik_async")
+
+    def sync(self):
+        fb = ctypes.c_int64(-1)
+        st = _lib.bv_sync(self.h, ctypes.byref(fb))
+        return st, fb.value
+
+    def autotune(self, precision=BV_FP64):
+        _check(_lib.bv_autotune(self.h, precision), "bv_autotune")
+
+    def plan_info(self, precision=BV_FP64):
+        la, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+        fl, en = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(_lib.bv_plan_info(self.h, precision, ctypes.byref(la), ctypes.byref(nb),
+                                 ctypes.byref(fl), ctypes.byref(en)), "bv_plan_info")
+        return dict(launches_per_eval=la.value, n_bins=nb.value, flops=fl.value,
+                    cov_entries=en.value)
+
+    # sampler / MLE / warm start ----------------------------------------------------------
+    def simulate(self, th: bv_theta, z):
+        zv = _arr(z, np.float64)
+        y = np.empty(self.n, np.float64)
+        _check(_lib.bv_simulate(self.h, ctypes.byref(th), _p(zv, _d), _p(y, _d)), "bv_simulate")
+        return y
+
+    def mle(self, th0: bv_theta, lo: bv_theta, hi: bv_theta,
+            free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
+            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5):
+        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step)
+        out = bv_theta()
+        ll = ctypes.c_double(0.0)
+        ne = ctypes.c_int32(0)
+        _check(_lib.bv_mle(self.h, ctypes.byref(th0), ctypes.byref(lo), ctypes.byref(hi),
+                           free_mask, ctypes.byref(o), ctypes.byref(out), ctypes.byref(ll),
+                           ctypes.byref(ne)), "bv_mle")
+        return out, ll.value, ne.value
+
+    def features(self, max_points=10000, seed=0):
+        out = np.empty((self.ndata, BV_NFEAT), np.float32)
+        _check(_lib.bv_features(self.h, max_points, seed, _p(out, _f)), "bv_features")
+        return out
+
+    def warmstart_load(self, path: str):
+        _check(_lib.bv_warmstart_load(self.h, path.encode()), "bv_warmstart_load")
+
+    def warmstart_predict(self, th_in: bv_theta):
+        out = bv_theta()
+        _check(_lib.bv_warmstart_predict(self.h, ctypes.byref(th_in), ctypes.byref(out)),
+               "bv_warmstart_predict")
+        return out

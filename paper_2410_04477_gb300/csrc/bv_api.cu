@@ -1,0 +1,786 @@
+// bv_api.cu -- host side of the C ABI in include/bv.h: context, data, preprocessing
+// drivers, the size-bin launch planner with its autotuner, and the CUDA-graph launch of
+// one log-likelihood evaluation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "bv_internal.h"
+
+// ------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------
+static thread_local std::string g_cuda_err;
+
+void bv_record_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
+    g_cuda_err = std::string(cudaGetErrorString(e)) + " in " + expr + " at " + file + ":" +
+                 std::to_string(line);
+}
+
+extern "C" const char* bv_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+extern "C" const char* bv_strerror(int s) {
+    switch (s) {
+        case BV_OK: return "ok";
+        case BV_EINVAL: return "invalid argument";
+        case BV_ENOMEM: return "out of memory";
+        case BV_ECUDA: return "CUDA error";
+        case BV_ENOTPD: return "covariance matrix not positive definite";
+        case BV_ETIMEOUT: return "device wait timed out";
+        case BV_ESTATE: return "call out of order (missing data, blocks or neighbours)";
+        case BV_EINTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+template <class T>
+static void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+static void free_plan(bv_ctx* c, int prec) {
+    for (auto& b : c->plan[prec]) dfree(b.d_work);
+    c->plan[prec].clear();
+    c->plan_valid[prec] = false;
+    c->tuned[prec] = false;
+    if (c->graph[prec]) cudaGraphExecDestroy(c->graph[prec]);
+    c->graph[prec] = nullptr;
+}
+
+void bv_invalidate_plans(bv_ctx* c) {
+    free_plan(c, 0);
+    free_plan(c, 1);
+}
+
+static void free_neighbors(bv_ctx* c) {
+    bv_invalidate_plans(c);
+    dfree(c->d_nptr);
+    dfree(c->d_nidx);
+    c->h_nptr.clear();
+    c->have_nn = false;
+}
+
+static void free_blocks(bv_ctx* c) {
+    free_neighbors(c);
+    dfree(c->d_bptr);
+    dfree(c->d_pidx);
+    dfree(c->d_cent);
+    dfree(c->d_bds);
+    dfree(c->d_ds_blk_off);
+    dfree(c->d_ell_blk);
+    c->h_bptr.clear();
+    c->h_pidx.clear();
+    c->h_bds.clear();
+    c->ds_blk_off.clear();
+    c->nblk = 0;
+    c->have_blocks = false;
+}
+
+static void free_data(bv_ctx* c) {
+    free_blocks(c);
+    dfree(c->d_locs);
+    dfree(c->d_y);
+    dfree(c->d_out);
+    dfree(c->d_theta);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    c->h_out = nullptr;
+    c->h_theta.clear();
+    c->h_locs.clear();
+    c->pt_off.clear();
+    c->n_tot = 0;
+    c->ndata = 0;
+    c->have_y = false;
+}
+
+// ------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------
+extern "C" int bv_create(bv_ctx** out, int device, void* stream) {
+    if (!out) return BV_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    BV_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(device));
+    bv_ctx* c = new bv_ctx();
+    c->device = device;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            bv_record_cuda_error(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
+            delete c;
+            return BV_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_fail, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_fail, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        bv_record_cuda_error(e, "bv_create", __FILE__, __LINE__);
+        bv_destroy(c);
+        return BV_ECUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = c;
+    return BV_OK;
+}
+
+extern "C" void bv_destroy(bv_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_data(c);
+    dfree(c->d_fail);
+    dfree(c->d_ws);
+    if (c->h_fail) cudaFreeHost(c->h_fail);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ------------------------------------------------------------------------------------
+// data
+// ------------------------------------------------------------------------------------
+extern "C" int bv_set_datasets(bv_ctx* c, int32_t ndata, const int64_t* n_per, const double* locs,
+                               const double* y, int32_t d) {
+    if (!c || ndata <= 0 || !n_per || !locs || d < 1 || d > 3) return BV_EINVAL;
+    int64_t n_tot = 0;
+    for (int k = 0; k < ndata; ++k) {
+        if (n_per[k] <= 0) return BV_EINVAL;
+        n_tot += n_per[k];
+    }
+    if (n_tot >= (int64_t)INT32_MAX) return BV_EINVAL;
+    for (int64_t i = 0; i < n_tot * d; ++i)
+        if (!std::isfinite(locs[i])) return BV_EINVAL;
+    if (y)
+        for (int64_t i = 0; i < n_tot; ++i)
+            if (!std::isfinite(y[i])) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(c->device));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    free_data(c);
+    c->d = d;
+    c->ndata = ndata;
+    c->n_tot = n_tot;
+    c->pt_off.assign(ndata + 1, 0);
+    for (int k = 0; k < ndata; ++k) c->pt_off[k + 1] = c->pt_off[k] + n_per[k];
+    c->h_locs.assign(locs, locs + n_tot * d);
+    std::vector<double> soa((size_t)n_tot * d);
+    for (int64_t i = 0; i < n_tot; ++i)
+        for (int k = 0; k < d; ++k) soa[(size_t)k * n_tot + i] = locs[i * d + k];
+    BV_CUDA(cudaMalloc(&c->d_locs, sizeof(double) * n_tot * d));
+    BV_CUDA(cudaMalloc(&c->d_y, sizeof(double) * n_tot));
+    BV_CUDA(cudaMalloc(&c->d_out, sizeof(double) * ndata));
+    BV_CUDA(cudaMalloc(&c->d_theta, sizeof(DevTheta) * ndata));
+    BV_CUDA(cudaMallocHost(&c->h_out, sizeof(double) * ndata));
+    c->h_theta.assign(ndata, DevTheta{});
+    BV_CUDA(cudaMemcpyAsync(c->d_locs, soa.data(), sizeof(double) * n_tot * d, cudaMemcpyHostToDevice,
+                            c->stream));
+    if (y) {
+        BV_CUDA(cudaMemcpyAsync(c->d_y, y, sizeof(double) * n_tot, cudaMemcpyHostToDevice, c->stream));
+        c->have_y = true;
+    } else {
+        BV_CUDA(cudaMemsetAsync(c->d_y, 0, sizeof(double) * n_tot, c->stream));
+    }
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    return BV_OK;
+}
+
+extern "C" int bv_set_data(bv_ctx* c, const double* locs, const double* y, int64_t n, int32_t d) {
+    return bv_set_datasets(c, 1, &n, locs, y, d);
+}
+
+extern "C" int bv_set_observations(bv_ctx* c, const double* y, int32_t on_device) {
+    if (!c || !y) return BV_EINVAL;
+    if (!c->d_y) return BV_ESTATE;
+    if (on_device) {
+        BV_CUDA(cudaMemcpyAsync(c->d_y, y, sizeof(double) * c->n_tot, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        BV_CUDA(cudaMemcpyAsync(c->d_y, y, sizeof(double) * c->n_tot, cudaMemcpyHostToDevice, c->stream));
+        BV_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    c->have_y = true;
+    return BV_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// blocks
+// ------------------------------------------------------------------------------------
+
+// Upload the host block structure (h_bptr, h_pidx, h_bds, ds_blk_off) and centroids.
+static int upload_blocks(bv_ctx* c, const std::vector<double>& cent) {
+    const int64_t nb = c->nblk;
+    BV_CUDA(cudaMalloc(&c->d_bptr, sizeof(int64_t) * (nb + 1)));
+    BV_CUDA(cudaMalloc(&c->d_pidx, sizeof(int32_t) * c->n_tot));
+    BV_CUDA(cudaMalloc(&c->d_cent, sizeof(double) * nb * c->d));
+    BV_CUDA(cudaMalloc(&c->d_bds, sizeof(int32_t) * nb));
+    BV_CUDA(cudaMalloc(&c->d_ds_blk_off, sizeof(int64_t) * (c->ndata + 1)));
+    BV_CUDA(cudaMalloc(&c->d_ell_blk, sizeof(double) * nb));
+    BV_CUDA(cudaMemcpyAsync(c->d_bptr, c->h_bptr.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->d_pidx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot, cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->d_cent, cent.data(), sizeof(double) * nb * c->d, cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->d_bds, c->h_bds.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->d_ds_blk_off, c->ds_blk_off.data(), sizeof(int64_t) * (c->ndata + 1),
+                            cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_blocks = true;
+    return BV_OK;
+}
+
+extern "C" int bv_build_blocks_multi(bv_ctx* c, const int64_t* bc_per, uint64_t seed, int32_t iters,
+                                     int64_t* bc_eff_per) {
+    if (!c || !bc_per || iters < 0) return BV_EINVAL;
+    if (!c->d_locs) return BV_ESTATE;
+    for (int k = 0; k < c->ndata; ++k)
+        if (bc_per[k] <= 0 || bc_per[k] > c->pt_off[k + 1] - c->pt_off[k]) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(c->device));
+    free_blocks(c);
+    const int d = c->d;
+    std::vector<int64_t> bptr(1, 0);
+    std::vector<int32_t> pidx;
+    std::vector<int32_t> bds;
+    std::vector<double> cent_all;
+    std::vector<int64_t> dsoff(1, 0);
+    pidx.reserve(c->n_tot);
+    for (int ds = 0; ds < c->ndata; ++ds) {
+        const int64_t off = c->pt_off[ds], n = c->pt_off[ds + 1] - off, k = bc_per[ds];
+        const uint64_t sd = seed + (uint64_t)ds;
+        int32_t* d_label = nullptr;
+        double* d_cent = nullptr;
+        int64_t* d_counts = nullptr;
+        BV_CUDA(cudaMalloc(&d_label, sizeof(int32_t) * n));
+        BV_CUDA(cudaMalloc(&d_cent, sizeof(double) * k * d));
+        BV_CUDA(cudaMalloc(&d_counts, sizeof(int64_t) * k));
+        int st = bv_kmeans_device(c->d_locs, c->n_tot, off, n, d, k, sd, iters, d_label, d_cent, c->stream);
+        int sc = 0, q = 0;
+        if (st == BV_OK) {
+            bv_kmeans_scales(c->h_locs.data() + off * d, n, d, &sc, &q);
+            // block centroids: exact-integer means of the final members
+            st = bv_centroids_device(c->d_locs, c->n_tot, off, n, d, d_label, k, q, d_cent, d_counts, c->stream);
+        }
+        std::vector<int32_t> label(n);
+        std::vector<double> cent((size_t)k * d);
+        std::vector<int64_t> counts(k);
+        if (st == BV_OK) {
+            cudaError_t e = cudaMemcpyAsync(label.data(), d_label, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(cent.data(), d_cent, sizeof(double) * k * d, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(counts.data(), d_counts, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                bv_record_cuda_error(e, "kmeans copy-out", __FILE__, __LINE__);
+                st = BV_ECUDA;
+            }
+        }
+        cudaFree(d_label);
+        cudaFree(d_cent);
+        cudaFree(d_counts);
+        if (st != BV_OK) return st;
+        // drop empty clusters, random block order zeta (Fisher-Yates on SplitMix64 draws)
+        std::vector<int64_t> clus_of_blk;
+        for (int64_t cl = 0; cl < k; ++cl)
+            if (counts[cl] > 0) clus_of_blk.push_back(cl);
+        const int64_t nb = (int64_t)clus_of_blk.size();
+        std::vector<int64_t> perm(nb);
+        std::iota(perm.begin(), perm.end(), 0);
+        const uint64_t zs = BV_STREAM_ZETA(sd);
+        for (int64_t i = nb - 1; i >= 1; --i) {
+            const uint64_t r = bv_sm64(zs, (uint64_t)i);
+            const int64_t j = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)(i + 1)) >> 64);
+            std::swap(perm[i], perm[j]);
+        }
+        std::vector<int64_t> pos_of_clus(k, -1);
+        const int64_t b0 = (int64_t)bptr.size() - 1;
+        for (int64_t p = 0; p < nb; ++p) {
+            const int64_t cl = clus_of_blk[perm[p]];
+            pos_of_clus[cl] = p;
+            bptr.push_back(bptr.back() + counts[cl]);
+            for (int j = 0; j < d; ++j) cent_all.push_back(cent[cl * d + j]);
+            bds.push_back(ds);
+        }
+        pidx.resize(off + n);
+        std::vector<int64_t> fill(nb, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t p = pos_of_clus[label[i]];
+            pidx[bptr[b0 + p] + fill[p]++] = (int32_t)(off + i);
+        }
+        dsoff.push_back(dsoff.back() + nb);
+        if (bc_eff_per) bc_eff_per[ds] = nb;
+    }
+    c->h_bptr = std::move(bptr);
+    c->h_pidx = std::move(pidx);
+    c->h_bds = std::move(bds);
+    c->ds_blk_off = std::move(dsoff);
+    c->nblk = c->ds_blk_off.back();
+    return upload_blocks(c, cent_all);
+}
+
+extern "C" int bv_build_blocks(bv_ctx* c, int64_t bc, uint64_t seed, int32_t iters, int64_t* block_ptr,
+                               int32_t* point_idx, int64_t* bc_eff) {
+    if (!c) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    int64_t nb = 0;
+    BV_TRY(bv_build_blocks_multi(c, &bc, seed, iters, &nb));
+    if (bc_eff) *bc_eff = nb;
+    if (block_ptr) memcpy(block_ptr, c->h_bptr.data(), sizeof(int64_t) * (nb + 1));
+    if (point_idx) memcpy(point_idx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot);
+    return BV_OK;
+}
+
+extern "C" int bv_set_blocks(bv_ctx* c, int64_t bc, const int64_t* block_ptr, const int32_t* point_idx,
+                             const double* centroids) {
+    if (!c || bc <= 0 || !block_ptr || !point_idx) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    const int64_t n = c->n_tot;
+    if (block_ptr[0] != 0 || block_ptr[bc] != n) return BV_EINVAL;
+    for (int64_t i = 0; i < bc; ++i)
+        if (block_ptr[i + 1] <= block_ptr[i]) return BV_EINVAL;
+    std::vector<char> seen(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t p = point_idx[i];
+        if (p < 0 || p >= n || seen[p]) return BV_EINVAL;
+        seen[p] = 1;
+    }
+    BV_CUDA(cudaSetDevice(c->device));
+    free_blocks(c);
+    const int d = c->d;
+    std::vector<double> cent((size_t)bc * d);
+    if (centroids) {
+        std::copy(centroids, centroids + bc * d, cent.begin());
+    } else {
+        for (int64_t i = 0; i < bc; ++i)
+            for (int k = 0; k < d; ++k) {
+                double s = 0.0;
+                for (int64_t p = block_ptr[i]; p < block_ptr[i + 1]; ++p) s += c->h_locs[(size_t)point_idx[p] * d + k];
+                cent[(size_t)i * d + k] = s / (double)(block_ptr[i + 1] - block_ptr[i]);
+            }
+    }
+    c->h_bptr.assign(block_ptr, block_ptr + bc + 1);
+    c->h_pidx.assign(point_idx, point_idx + n);
+    c->h_bds.assign(bc, 0);
+    c->ds_blk_off = {0, bc};
+    c->nblk = bc;
+    return upload_blocks(c, cent);
+}
+
+// ------------------------------------------------------------------------------------
+// neighbours
+// ------------------------------------------------------------------------------------
+static int upload_nptr(bv_ctx* c) {
+    BV_CUDA(cudaMalloc(&c->d_nptr, sizeof(int64_t) * (c->nblk + 1)));
+    BV_CUDA(cudaMemcpyAsync(c->d_nptr, c->h_nptr.data(), sizeof(int64_t) * (c->nblk + 1), cudaMemcpyHostToDevice,
+                            c->stream));
+    const int64_t tot = c->h_nptr.back();
+    BV_CUDA(cudaMalloc(&c->d_nidx, sizeof(int32_t) * std::max<int64_t>(tot, 1)));
+    return BV_OK;
+}
+
+extern "C" int bv_select_neighbors(bv_ctx* c, int32_t m, const int32_t* m_per_block, int64_t* nn_ptr,
+                                   int32_t* nn_idx) {
+    if (!c) return BV_EINVAL;
+    if (!c->have_blocks) return BV_ESTATE;
+    if (!m_per_block && m < 0) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(c->device));
+    free_neighbors(c);
+    c->h_nptr.assign(c->nblk + 1, 0);
+    for (int ds = 0; ds < c->ndata; ++ds) {
+        const int64_t base = c->h_bptr[c->ds_blk_off[ds]];
+        for (int64_t i = c->ds_blk_off[ds]; i < c->ds_blk_off[ds + 1]; ++i) {
+            const int64_t want = m_per_block ? (int64_t)m_per_block[i] : (int64_t)m;
+            if (want < 0) return BV_EINVAL;
+            const int64_t avail = c->h_bptr[i] - base;
+            const int64_t mi = std::min(want, avail);
+            if (mi > 4000) return BV_EINVAL;  // exact-key list capacity of the selection kernel
+            c->h_nptr[i + 1] = c->h_nptr[i] + mi;
+        }
+    }
+    BV_TRY(upload_nptr(c));
+    for (int ds = 0; ds < c->ndata; ++ds) {
+        const int64_t off = c->pt_off[ds], n = c->pt_off[ds + 1] - off;
+        double amax = 0.0;
+        for (int64_t i = 0; i < n * c->d; ++i) amax = std::max(amax, fabs(c->h_locs[(size_t)off * c->d + i]));
+        BV_TRY(bv_select_neighbors_device(c->d_locs, c->n_tot, c->d, c->d_bptr, c->d_pidx, c->d_cent,
+                                          c->ds_blk_off[ds], c->ds_blk_off[ds + 1], c->h_nptr.data(), c->d_nptr,
+                                          c->d_nidx, amax, c->stream));
+    }
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_nn = true;
+    if (nn_ptr) memcpy(nn_ptr, c->h_nptr.data(), sizeof(int64_t) * (c->nblk + 1));
+    if (nn_idx && c->h_nptr.back() > 0)
+        BV_CUDA(cudaMemcpy(nn_idx, c->d_nidx, sizeof(int32_t) * c->h_nptr.back(), cudaMemcpyDeviceToHost));
+    return BV_OK;
+}
+
+extern "C" int bv_set_neighbors(bv_ctx* c, const int64_t* nn_ptr, const int32_t* nn_idx) {
+    if (!c || !nn_ptr) return BV_EINVAL;
+    if (!c->have_blocks) return BV_ESTATE;
+    if (nn_ptr[0] != 0) return BV_EINVAL;
+    for (int64_t i = 0; i < c->nblk; ++i)
+        if (nn_ptr[i + 1] < nn_ptr[i]) return BV_EINVAL;
+    const int64_t tot = nn_ptr[c->nblk];
+    if (tot > 0 && !nn_idx) return BV_EINVAL;
+    for (int ds = 0; ds < c->ndata; ++ds)
+        for (int64_t i = c->ds_blk_off[ds]; i < c->ds_blk_off[ds + 1]; ++i)
+            for (int64_t p = nn_ptr[i]; p < nn_ptr[i + 1]; ++p)
+                if (nn_idx[p] < c->pt_off[ds] || nn_idx[p] >= c->pt_off[ds + 1]) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(c->device));
+    free_neighbors(c);
+    c->h_nptr.assign(nn_ptr, nn_ptr + c->nblk + 1);
+    BV_TRY(upload_nptr(c));
+    if (tot > 0)
+        BV_CUDA(cudaMemcpyAsync(c->d_nidx, nn_idx, sizeof(int32_t) * tot, cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_nn = true;
+    return BV_OK;
+}
+
+extern "C" int bv_get_sizes(bv_ctx* c, int64_t* nb, int64_t* nn) {
+    if (!c) return BV_EINVAL;
+    if (nb) *nb = c->nblk;
+    if (nn) *nn = c->have_nn ? c->h_nptr.back() : 0;
+    return BV_OK;
+}
+
+extern "C" int bv_get_blocks(bv_ctx* c, int64_t* block_ptr, int32_t* point_idx, double* centroids) {
+    if (!c) return BV_EINVAL;
+    if (!c->have_blocks) return BV_ESTATE;
+    if (block_ptr) memcpy(block_ptr, c->h_bptr.data(), sizeof(int64_t) * (c->nblk + 1));
+    if (point_idx) memcpy(point_idx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot);
+    if (centroids)
+        BV_CUDA(cudaMemcpy(centroids, c->d_cent, sizeof(double) * c->nblk * c->d, cudaMemcpyDeviceToHost));
+    return BV_OK;
+}
+
+extern "C" int bv_get_neighbors(bv_ctx* c, int64_t* nn_ptr, int32_t* nn_idx) {
+    if (!c) return BV_EINVAL;
+    if (!c->have_nn) return BV_ESTATE;
+    if (nn_ptr) memcpy(nn_ptr, c->h_nptr.data(), sizeof(int64_t) * (c->nblk + 1));
+    if (nn_idx && c->h_nptr.back() > 0)
+        BV_CUDA(cudaMemcpy(nn_idx, c->d_nidx, sizeof(int32_t) * c->h_nptr.back(), cudaMemcpyDeviceToHost));
+    return BV_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// evaluation plan: size bins, launch shapes, workspace
+// ------------------------------------------------------------------------------------
+int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
+    if (!t) return BV_EINVAL;
+    if (!(t->sigma2 > 0.0) || !(t->nugget >= 0.0) || !std::isfinite(t->sigma2) || !std::isfinite(t->nugget))
+        return BV_EINVAL;
+    if (t->nu == 0.5) o->nu_code = NU_HALF;
+    else if (t->nu == 1.5) o->nu_code = NU_3HALF;
+    else if (t->nu == 2.5) o->nu_code = NU_5HALF;
+    else return BV_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+        const double r = t->aniso ? t->range[k] : t->range[0];
+        if (k < d && !(r > 0.0 && std::isfinite(r))) return BV_EINVAL;
+        o->inv_range[k] = (k < d) ? 1.0 / r : 0.0;
+    }
+    o->sigma2 = t->sigma2;
+    o->nugget = t->nugget;
+    o->pad = 0;
+    return BV_OK;
+}
+
+static const int kBinEdges[] = {16, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 288, 320};
+
+static int default_threads(int kind, int nmax) {
+    if (kind == 2) return 256;
+    if (nmax <= 40) return 64;
+    if (nmax <= 112) return 128;
+    return 256;
+}
+
+static LLArgs make_args(bv_ctx* c) {
+    LLArgs a;
+    a.locs = c->d_locs;
+    a.n_tot = c->n_tot;
+    a.d = c->d;
+    a.y = c->d_y;
+    a.bptr = c->d_bptr;
+    a.pidx = c->d_pidx;
+    a.nptr = c->d_nptr;
+    a.nidx = c->d_nidx;
+    a.cent = c->d_cent;
+    a.bds = c->d_bds;
+    a.theta = c->d_theta;
+    a.work = nullptr;
+    a.nwork = 0;
+    a.ell_blk = c->d_ell_blk;
+    a.fail = c->d_fail;
+    a.ws = c->d_ws;
+    a.ws_stride = c->ws_stride;
+    return a;
+}
+
+static int set_grid(bv_ctx* c, BinPlan& bp) {
+    bp.smem = bv_smem_bytes(bp.kind, bp.nmax, c->d, bp.threads);
+    if (bp.kind == 2) {
+        bp.grid = std::min<int>(bp.nwork, c->ws_slots);
+        return BV_OK;
+    }
+    const int occ = bv_occupancy(bp.kind, bp.threads, bp.smem);
+    if (occ <= 0) return BV_EINTERNAL;
+    bp.grid = (int)std::min<int64_t>(bp.nwork, (int64_t)occ * c->num_sms);
+    return BV_OK;
+}
+
+int bv_ensure_plan(bv_ctx* c, int prec) {
+    if (c->plan_valid[prec]) return BV_OK;
+    free_plan(c, prec);
+    const int smem_kind = prec == BV_MIXED ? 1 : 0;
+    const int nsm = bv_smem_max_n(smem_kind, c->d);
+    std::vector<int> Nof(c->nblk);
+    int64_t maxlarge = 0;
+    for (int64_t i = 0; i < c->nblk; ++i) {
+        const int64_t N = (c->h_bptr[i + 1] - c->h_bptr[i]) + (c->h_nptr[i + 1] - c->h_nptr[i]);
+        if (N > BV_LARGE_MAX_N) return BV_EINVAL;
+        Nof[i] = (int)N;
+        if (N > nsm) maxlarge = std::max<int64_t>(maxlarge, N);
+    }
+    // bins: edges up to the shared-memory limit, then one global-memory bin
+    std::vector<int> edges;
+    for (int e : kBinEdges)
+        if (e < nsm) edges.push_back(e);
+    edges.push_back(nsm);
+    std::vector<std::vector<int32_t>> lists(edges.size() + 1);
+    for (int64_t i = 0; i < c->nblk; ++i) {
+        const int N = Nof[i];
+        size_t b = 0;
+        while (b < edges.size() && N > edges[b]) ++b;
+        lists[b].push_back((int32_t)i);
+    }
+    // workspace for the global-memory bin
+    if (maxlarge > 0) {
+        const int64_t R = maxlarge + 1;
+        const int64_t stride = (R * (R + 1)) / 2 + 2 * R + 3 * maxlarge + 8;
+        const int64_t nlarge = (int64_t)lists.back().size();
+        int slots = (int)std::min<int64_t>(nlarge, 2 * (int64_t)c->num_sms);
+        // keep the workspace within a few GB
+        while (slots > 1 && (double)slots * stride * 8.0 > 8e9) --slots;
+        if (stride > c->ws_stride || slots > c->ws_slots) {
+            dfree(c->d_ws);
+            BV_CUDA(cudaMalloc(&c->d_ws, sizeof(double) * stride * slots));
+            c->ws_stride = stride;
+            c->ws_slots = slots;
+        }
+    }
+    for (size_t b = 0; b < lists.size(); ++b) {
+        auto& L = lists[b];
+        if (L.empty()) continue;
+        std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) { return Nof[x] > Nof[y]; });
+        BinPlan bp;
+        bp.kind = b < edges.size() ? smem_kind : 2;
+        bp.nmax = Nof[L.front()];
+        bp.threads = default_threads(bp.kind, bp.nmax);
+        bp.nwork = (int32_t)L.size();
+        bp.h_work = L;
+        bp.d_work = nullptr;
+        BV_CUDA(cudaMalloc(&bp.d_work, sizeof(int32_t) * L.size()));
+        BV_CUDA(cudaMemcpyAsync(bp.d_work, L.data(), sizeof(int32_t) * L.size(), cudaMemcpyHostToDevice, c->stream));
+        BV_TRY(set_grid(c, bp));
+        c->plan[prec].push_back(bp);
+    }
+    // largest bins first so the long blocks start early
+    std::stable_sort(c->plan[prec].begin(), c->plan[prec].end(),
+                     [](const BinPlan& x, const BinPlan& y) { return x.nmax > y.nmax; });
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    c->plan_valid[prec] = true;
+    return BV_OK;
+}
+
+// Enqueue one evaluation of every dataset: theta upload, failure reset, all bins, the
+// per-dataset reduction into d_out.
+static int enqueue_eval(bv_ctx* c, int prec) {
+    BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
+    const LLArgs a = make_args(c);
+    for (const auto& bp : c->plan[prec]) BV_CUDA(bv_launch_bin(bp, a, c->stream));
+    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_ds_blk_off, c->ndata, c->d_fail, c->d_bds, c->d_out, c->stream));
+    return BV_OK;
+}
+
+// Time one bin with the given CTA size (ms, best of `reps`).
+static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const LLArgs a = make_args(c);
+    float best = 1e30f;
+    for (int r = 0; r < reps + 1; ++r) {
+        cudaEventRecord(e0, c->stream);
+        cudaError_t e = bv_launch_bin(bp, a, c->stream);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            best = 1e30f;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+static int autotune(bv_ctx* c, int prec) {
+    if (c->tuned[prec]) return BV_OK;
+    // theta of the current h_theta must be valid: use it as is (the caller set it)
+    BV_CUDA(cudaMemcpyAsync(c->d_theta, c->h_theta.data(), sizeof(DevTheta) * c->ndata, cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
+    for (auto& bp : c->plan[prec]) {
+        if (bp.kind == 2) continue;
+        const int cands[] = {64, 128, 256, 512};
+        int best_t = bp.threads;
+        float best_ms = 1e30f;
+        for (int t : cands) {
+            BinPlan trial = bp;
+            trial.threads = t;
+            if (set_grid(c, trial) != BV_OK) continue;
+            const float ms = time_bin(c, trial, 2);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_t = t;
+            }
+        }
+        bp.threads = best_t;
+        BV_TRY(set_grid(c, bp));
+    }
+    BV_CUDA(cudaGetLastError());
+    c->tuned[prec] = true;
+    return BV_OK;
+}
+
+extern "C" int bv_autotune(bv_ctx* c, int32_t prec) {
+    if (!c || (prec != BV_FP64 && prec != BV_MIXED)) return BV_EINVAL;
+    if (!c->have_nn) return BV_ESTATE;
+    BV_CUDA(cudaSetDevice(c->device));
+    BV_TRY(bv_ensure_plan(c, prec));
+    // a neutral theta for timing if none was set yet
+    for (int k = 0; k < c->ndata; ++k)
+        if (c->h_theta[k].sigma2 <= 0.0) {
+            bv_theta t = {1.0, {0.1, 0.1, 0.1}, 0.5, 1e-3, 0, 0};
+            bv_theta_to_dev(&t, c->d, &c->h_theta[k]);
+        }
+    c->tuned[prec] = false;
+    if (c->graph[prec]) cudaGraphExecDestroy(c->graph[prec]);
+    c->graph[prec] = nullptr;
+    return autotune(c, prec);
+}
+
+// Graph of one evaluation (failure reset, every bin, the reduction), captured once per
+// precision after tuning.  theta is copied in front of each launch.
+static int ensure_graph(bv_ctx* c, int prec) {
+    if (c->graph[prec]) return BV_OK;
+    cudaGraph_t g = nullptr;
+    BV_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int st = enqueue_eval(c, prec);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != BV_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    BV_CUDA(e);
+    e = cudaGraphInstantiate(&c->graph[prec], g, 0);
+    cudaGraphDestroy(g);
+    BV_CUDA(e);
+    return BV_OK;
+}
+
+int bv_enqueue_loglik(bv_ctx* c, int prec, double* d_out, bool) {
+    BV_TRY(bv_ensure_plan(c, prec));
+    BV_TRY(autotune(c, prec));
+    BV_TRY(ensure_graph(c, prec));
+    BV_CUDA(cudaMemcpyAsync(c->d_theta, c->h_theta.data(), sizeof(DevTheta) * c->ndata, cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(cudaGraphLaunch(c->graph[prec], c->stream));
+    if (d_out && d_out != c->d_out)
+        BV_CUDA(cudaMemcpyAsync(d_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToDevice, c->stream));
+    return BV_OK;
+}
+
+static int prepare_eval(bv_ctx* c, const bv_theta* thetas, int32_t prec) {
+    if (!c || !thetas) return BV_EINVAL;
+    if (prec != BV_FP64 && prec != BV_MIXED) return BV_EINVAL;
+    if (!c->have_nn || !c->have_blocks) return BV_ESTATE;
+    BV_CUDA(cudaSetDevice(c->device));
+    for (int k = 0; k < c->ndata; ++k) BV_TRY(bv_theta_to_dev(&thetas[k], c->d, &c->h_theta[k]));
+    return BV_OK;
+}
+
+static int finish_sync(bv_ctx* c, double* out, int nout) {
+    BV_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->h_fail, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nout; ++k) out[k] = c->h_out[k];
+    return *c->h_fail != ~0ull ? BV_ENOTPD : BV_OK;
+}
+
+extern "C" int bv_loglik_multi(bv_ctx* c, const bv_theta* thetas, int32_t prec, double* out) {
+    if (!out) return BV_EINVAL;
+    BV_TRY(prepare_eval(c, thetas, prec));
+    BV_TRY(bv_enqueue_loglik(c, prec, nullptr, true));
+    return finish_sync(c, out, c->ndata);
+}
+
+extern "C" int bv_loglik(bv_ctx* c, const bv_theta* theta, int32_t prec, double* out, double* per_block) {
+    if (!c || !out) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    BV_TRY(prepare_eval(c, theta, prec));
+    BV_TRY(bv_enqueue_loglik(c, prec, nullptr, true));
+    const int st = finish_sync(c, out, 1);
+    if (per_block)
+        BV_CUDA(cudaMemcpy(per_block, c->d_ell_blk, sizeof(double) * c->nblk, cudaMemcpyDeviceToHost));
+    return st;
+}
+
+extern "C" int bv_loglik_async(bv_ctx* c, const bv_theta* thetas, int32_t prec, double* d_out) {
+    if (!d_out) return BV_EINVAL;
+    BV_TRY(prepare_eval(c, thetas, prec));
+    return bv_enqueue_loglik(c, prec, d_out, true);
+}
+
+extern "C" int bv_sync(bv_ctx* c, int64_t* failed_block) {
+    if (!c) return BV_EINVAL;
+    BV_CUDA(cudaSetDevice(c->device));
+    BV_CUDA(cudaMemcpyAsync(c->h_fail, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    const bool failed = *c->h_fail != ~0ull;
+    if (failed_block) *failed_block = failed ? (int64_t)*c->h_fail : -1;
+    return failed ? BV_ENOTPD : BV_OK;
+}
+
+extern "C" int bv_plan_info(bv_ctx* c, int32_t prec, int32_t* launches, int32_t* nbins, double* flops,
+                            double* entries) {
+    if (!c || (prec != BV_FP64 && prec != BV_MIXED)) return BV_EINVAL;
+    if (!c->have_nn) return BV_ESTATE;
+    BV_CUDA(cudaSetDevice(c->device));
+    BV_TRY(bv_ensure_plan(c, prec));
+    if (launches) *launches = (int32_t)c->plan[prec].size() + 2;  // bins + failure reset + reduction
+    if (nbins) *nbins = (int32_t)c->plan[prec].size();
+    double f = 0.0, e = 0.0;
+    for (int64_t i = 0; i < c->nblk; ++i) {
+        const double N = (double)((c->h_bptr[i + 1] - c->h_bptr[i]) + (c->h_nptr[i + 1] - c->h_nptr[i]));
+        f += N * N * N / 3.0 + N * N;
+        e += N * (N + 1.0) / 2.0;
+    }
+    if (flops) *flops = f;
+    if (entries) *entries = e;
+    return BV_OK;
+}

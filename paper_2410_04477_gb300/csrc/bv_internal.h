@@ -1,0 +1,189 @@
+// bv_internal.h -- shared declarations of the CUDA implementation of include/bv.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bv.h"
+
+// ------------------------------------------------------------------------------------
+// Error handling
+// ------------------------------------------------------------------------------------
+void bv_record_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+
+#define BV_CUDA(expr)                                                        \
+    do {                                                                     \
+        cudaError_t bv_e_ = (expr);                                          \
+        if (bv_e_ != cudaSuccess) {                                          \
+            bv_record_cuda_error(bv_e_, #expr, __FILE__, __LINE__);          \
+            return bv_e_ == cudaErrorMemoryAllocation ? BV_ENOMEM : BV_ECUDA; \
+        }                                                                    \
+    } while (0)
+
+#define BV_TRY(expr)                    \
+    do {                                \
+        int bv_s_ = (expr);             \
+        if (bv_s_ != BV_OK) return bv_s_; \
+    } while (0)
+
+// ------------------------------------------------------------------------------------
+// Device-side parameters
+// ------------------------------------------------------------------------------------
+
+// Matern smoothness codes for the closed forms of Eq. 5 at nu = 1/2, 3/2, 5/2.
+enum { NU_HALF = 0, NU_3HALF = 1, NU_5HALF = 2 };
+
+// theta prepared for the kernels: reciprocal ranges per axis (isotropic: all equal).
+struct DevTheta {
+    double sigma2, nugget;
+    double inv_range[3];
+    int32_t nu_code;
+    int32_t pad;
+};
+
+// Everything a log-likelihood kernel reads.  Locations are SoA: coordinate k of point j
+// is locs[k * n_tot + j].  Block p has points pidx[bptr[p] .. bptr[p+1]) and
+// conditioning points nidx[nptr[p] .. nptr[p+1]).
+struct LLArgs {
+    const double* locs;
+    int64_t n_tot;
+    int32_t d;
+    const double* y;
+    const int64_t* bptr;
+    const int32_t* pidx;
+    const int64_t* nptr;
+    const int32_t* nidx;
+    const double* cent;      // block centroids, row-major [nblk x d]
+    const int32_t* bds;      // dataset of every block
+    const DevTheta* theta;   // per dataset
+    const int32_t* work;     // block ids of this launch, largest first
+    int32_t nwork;
+    double* ell_blk;         // per-block conditional log-likelihood (output)
+    unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
+    double* ws;              // global workspace (large-block path)
+    int64_t ws_stride;       // doubles per workspace slot
+};
+
+// Per-size-bin launch plan entry.
+struct BinPlan {
+    int kind;            // 0: FP64 shared-memory, 1: mixed shared-memory, 2: large (global)
+    int nmax;            // largest augmented size N = m + b in the bin
+    int threads;         // CTA size (autotuned)
+    int grid;            // CTAs launched
+    size_t smem;         // dynamic shared memory bytes
+    int32_t* d_work;     // device block ids (largest N first)
+    int32_t nwork;
+    std::vector<int32_t> h_work;
+};
+
+// Launchers (bv_loglik.cu).
+int bv_smem_max_n(int kind, int d);
+size_t bv_smem_bytes(int kind, int nmax, int d, int threads);
+int bv_max_threads_for(int kind);
+int bv_occupancy(int kind, int threads, size_t smem);
+// Largest augmented size the global-memory path accepts (packed indices stay in int32).
+#define BV_LARGE_MAX_N 30000
+cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a, cudaStream_t s);
+cudaError_t bv_launch_reduce(const double* ell_blk, const int64_t* ds_blk_off, int32_t ndata,
+                             const unsigned long long* fail, const int32_t* bds, double* out,
+                             cudaStream_t s);
+cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
+
+// K-means and neighbour search (bv_kmeans.cu, bv_nn.cu).
+int bv_kmeans_device(const double* d_locs_soa, int64_t n_tot, int64_t off, int64_t n, int d,
+                     int64_t k, uint64_t seed, int iters, int32_t* d_label, double* d_cent,
+                     cudaStream_t s);
+int bv_kmeans_scales(const double* h_locs_rowmajor, int64_t n, int d, int* s_out, int* q_out);
+int bv_centroids_device(const double* d_locs_soa, int64_t n_tot, int64_t off, int64_t n, int d,
+                        const int32_t* d_label, int64_t k, int q, double* d_cent,
+                        int64_t* d_counts, cudaStream_t s);
+int bv_select_neighbors_device(const double* d_locs_soa, int64_t n_tot, int d,
+                               const int64_t* d_bptr, const int32_t* d_pidx,
+                               const double* d_cent, int64_t blk_begin, int64_t blk_end,
+                               const int64_t* h_nptr, int64_t* d_nptr, int32_t* d_nidx,
+                               double amax, cudaStream_t s);
+
+// Block-Vecchia sampler (bv_sim.cu).
+int bv_simulate_device(bv_ctx* ctx, const DevTheta& th, const double* d_z, double* d_y);
+
+// SplitMix64 counter-form draws (Steele, Lea and Flood 2014), host and device.
+__host__ __device__ inline uint64_t bv_sm64(uint64_t stream, uint64_t counter) {
+    uint64_t z = stream + (counter + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+#define BV_STREAM_KPP(seed) ((seed) ^ 0x6b6d65616e732b2bull)
+#define BV_STREAM_ZETA(seed) ((seed) ^ 0x7a6574615f6f7264ull)
+
+// ------------------------------------------------------------------------------------
+// The context
+// ------------------------------------------------------------------------------------
+struct bv_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+
+    // data
+    int32_t d = 0;
+    int32_t ndata = 0;
+    int64_t n_tot = 0;
+    std::vector<int64_t> pt_off;     // ndata + 1
+    std::vector<double> h_locs;      // row-major n_tot x d (host copy for planning)
+    double* d_locs = nullptr;        // SoA d x n_tot
+    double* d_y = nullptr;
+    bool have_y = false;
+
+    // blocks (all datasets, dataset after dataset)
+    int64_t nblk = 0;
+    std::vector<int64_t> ds_blk_off;  // ndata + 1
+    std::vector<int64_t> h_bptr;
+    std::vector<int32_t> h_pidx;
+    std::vector<int32_t> h_bds;
+    int64_t* d_bptr = nullptr;
+    int32_t* d_pidx = nullptr;
+    double* d_cent = nullptr;
+    int32_t* d_bds = nullptr;
+    int64_t* d_ds_blk_off = nullptr;
+    bool have_blocks = false;
+
+    // neighbours
+    std::vector<int64_t> h_nptr;
+    int64_t* d_nptr = nullptr;
+    int32_t* d_nidx = nullptr;
+    bool have_nn = false;
+
+    // evaluation state
+    double* d_ell_blk = nullptr;
+    unsigned long long* d_fail = nullptr;
+    double* d_out = nullptr;          // ndata
+    double* h_out = nullptr;          // pinned, ndata
+    DevTheta* d_theta = nullptr;      // ndata
+    std::vector<DevTheta> h_theta;    // ndata (pageable: copies are staged by the driver)
+    unsigned long long* h_fail = nullptr;  // pinned
+    double* d_ws = nullptr;
+    int64_t ws_stride = 0;
+    int ws_slots = 0;
+
+    // per precision: plan, graph
+    std::vector<BinPlan> plan[2];
+    bool plan_valid[2] = {false, false};
+    bool tuned[2] = {false, false};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double* graph_out[2] = {nullptr, nullptr};
+
+    // warm start
+    std::vector<float> mlp_w;
+    bool have_mlp = false;
+};
+
+// helpers in bv_api.cu
+int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* out);
+int bv_ensure_plan(bv_ctx* ctx, int precision);
+void bv_invalidate_plans(bv_ctx* ctx);
+int bv_enqueue_loglik(bv_ctx* ctx, int precision, double* d_out, bool with_theta_copy);

@@ -1,0 +1,538 @@
+// bv_loglik.cu -- fused block-Vecchia log-likelihood kernels (Eq. 4, Algorithm 1).
+//
+// Per block i with m conditioning points and b block points, Algorithm 1 factors
+// Sigma^con, solves for Sigma'^cross and y', forms Sigma^new = Sigma^lk - V^T V and
+// mu = V^T y', factors Sigma^new and solves for v.  All of those are the steps of ONE
+// Cholesky factorisation of the augmented (N+1) x (N+1) matrix (N = m + b)
+//
+//        [ Sigma^con     Sigma^cross   y_NN ]
+//        [ Sigma^crossT  Sigma^lk      y_B  ]
+//        [ y_NN^T        y_B^T         *    ]
+//
+// by block-Cholesky algebra: its leading m x m factor is L = chol(Sigma^con), the rows
+// below it hold V^T = (L^{-1} Sigma^cross)^T and y'^T, the trailing b x b factor is
+// L' = chol(Sigma^new), and the last row's entries under the block columns are
+// v = L'^{-1}(y_B - mu).  So u = sum_{k>=m} z_k^2 and d = sum_{k>=m} log p_k, with z the
+// last row of the factor and p_k the pivots (squared diagonal of the factor), and
+//        ell_i = -(u + d + b log 2 pi) / 2.
+// The kernels generate the matrix (Matern, Eq. 5) straight into shared memory, factor it
+// in place (right-looking, one column per step) and reduce ell_i, so nothing but the
+// locations, y and the index lists is read from HBM and one double per block is written.
+//
+// Paths:
+//   k_ll_fp64<NT>   FP64 packed lower triangle in shared memory (N up to ~234 for d=3)
+//   k_ll_mixed<NT>  FP32 covariance (block-local coordinates), FP32 updates; pivots,
+//                   log-determinant and quadratic form accumulated in FP64
+//   k_ll_large<NT>  FP64, packed triangle in a global-memory workspace slot (any N)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bv_internal.h"
+
+namespace {
+
+constexpr double kLog2Pi = 1.8378770664093454835606594728112;
+
+// Row-major packed lower triangle: element (r, c), c <= r, at r(r+1)/2 + c.
+__device__ __forceinline__ int pk(int r, int c) { return (r * (r + 1) >> 1) + c; }
+
+// Inverse of pk over a full triangle: flat index f -> (r, c).
+__device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
+    int rr = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
+    if (((rr + 1) * (rr + 2) >> 1) <= f) ++rr;
+    if ((rr * (rr + 1) >> 1) > f) --rr;
+    r = rr;
+    c = f - (rr * (rr + 1) >> 1);
+}
+
+// Matern correlation times sigma^2 at scaled distance x (Eq. 5, half-integer closed forms).
+__device__ __forceinline__ double matern64(int nu, double sigma2, double x) {
+    const double e = exp(-x);
+    if (nu == NU_HALF) return sigma2 * e;
+    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
+    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+}
+
+__device__ __forceinline__ float matern32(int nu, float sigma2, float x) {
+    const float e = expf(-x);
+    if (nu == NU_HALF) return sigma2 * e;
+    if (nu == NU_3HALF) return sigma2 * ((1.0f + x) * e);
+    return sigma2 * ((1.0f + x * (1.0f + x * (1.0f / 3.0f))) * e);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
+    atomicMin(fail, (unsigned long long)blk);
+}
+
+// ---------------------------------------------------------------------------------
+// FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2][N+1] | pts[d][N]
+// ---------------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* sm = reinterpret_cast<double*>(smraw);
+    __shared__ double red[NT / 32];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+        const int blk = a.work[w];
+        const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
+        const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
+        const int N = m + b, R = N + 1;
+        const DevTheta th = a.theta[a.bds[blk]];
+        double* A = sm;
+        double* col0 = A + ((R * (R + 1)) >> 1);
+        double* col1 = col0 + R;
+        double* px = col1 + R;
+        const int d = a.d;
+
+        // gather: conditioning points first, then the block (Algorithm 1 order)
+        for (int t = tid; t < N; t += NT) {
+            const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g];
+            A[pk(N, t)] = a.y[g];
+        }
+        if (tid == 0) {
+            A[pk(N, N)] = 0.0;
+            s_fail = 0;
+        }
+        __syncthreads();
+
+        // covariance (Eq. 5 + nugget), lower triangle rows 0..N-1: packed index == flat index
+        const int T = (N * (N + 1)) >> 1;
+        for (int f = tid; f < T; f += NT) {
+            int r, c;
+            tri_rc(f, r, c);
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                acc = fma(t, t, acc);
+            }
+            double v = matern64(th.nu_code, th.sigma2, sqrt(acc));
+            if (r == c) v += th.nugget;
+            A[f] = v;
+        }
+        __syncthreads();
+
+        // column 0
+        if (warp == 0) {
+            const double p = A[0];
+            if (!(p > 0.0) && lane == 0) s_fail = 1;
+            const double rs = rsqrt(p);
+            for (int j = 1 + lane; j <= N; j += 32) {
+                const double v = A[pk(j, 0)] * rs;
+                A[pk(j, 0)] = v;
+                col0[j] = v;
+            }
+        }
+        __syncthreads();
+
+        // right-looking steps: warp 0 finishes column k+1 (update, pivot, scale) while
+        // all warps apply column k to the rest of the trailing triangle; one barrier/step
+        for (int k = 0; k + 1 < N; ++k) {
+            const double* cur = (k & 1) ? col1 : col0;
+            double* nxt = (k & 1) ? col0 : col1;
+            const int kk = k + 1;
+            if (warp == 0) {
+                const double ck = cur[kk];
+                for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
+                __syncwarp();
+                const double p = A[pk(kk, kk)];
+                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                const double rs = rsqrt(p);
+                for (int j = kk + 1 + lane; j <= N; j += 32) {
+                    const double v = A[pk(j, kk)] * rs;
+                    A[pk(j, kk)] = v;
+                    nxt[j] = v;
+                }
+            }
+            const int S = N - kk;  // rows kk+1..N, columns kk+1..row
+            const int TS = (S * (S + 1)) >> 1;
+            for (int f = tid; f < TS; f += NT) {
+                int r, c;
+                tri_rc(f, r, c);
+                const int j = kk + 1 + r, i = kk + 1 + c;
+                A[pk(j, i)] = fma(-cur[j], cur[i], A[pk(j, i)]);
+            }
+            __syncthreads();
+        }
+
+        // u + d over the block columns
+        double part = 0.0;
+        for (int k = m + tid; k < N; k += NT) {
+            const double z = A[pk(N, k)];
+            part += z * z + log(A[pk(k, k)]);
+        }
+        const double s = block_sum<NT>(part, red);
+        if (tid == 0) {
+            double ell = -0.5 * (s + (double)b * kLog2Pi);
+            if (s_fail || !(ell == ell)) {
+                ell = -INFINITY;
+                record_fail(a.fail, blk);
+            }
+            a.ell_blk[blk] = ell;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Mixed: FP32 shared memory.  Layout: A packed float | col[2][N+1] float | pts[d][N] float
+// Coordinates are taken relative to the block centroid in FP64 and rounded to FP32, so
+// FP32 differences keep their relative accuracy for nearby points.
+// ---------------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* sm = reinterpret_cast<float*>(smraw);
+    __shared__ double red[NT / 32];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+        const int blk = a.work[w];
+        const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
+        const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
+        const int N = m + b, R = N + 1;
+        const DevTheta th = a.theta[a.bds[blk]];
+        float* A = sm;
+        float* col0 = A + ((R * (R + 1)) >> 1);
+        float* col1 = col0 + R;
+        float* px = col1 + R;
+        const int d = a.d;
+        const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
+
+        for (int t = tid; t < N; t += NT) {
+            const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+            for (int k = 0; k < d; ++k)
+                px[k * N + t] = (float)((a.locs[(int64_t)k * a.n_tot + g] - a.cent[(int64_t)blk * d + k]) *
+                                        th.inv_range[k]);
+            A[pk(N, t)] = (float)a.y[g];
+        }
+        if (tid == 0) {
+            A[pk(N, N)] = 0.0f;
+            s_fail = 0;
+        }
+        __syncthreads();
+
+        const int T = (N * (N + 1)) >> 1;
+        for (int f = tid; f < T; f += NT) {
+            int r, c;
+            tri_rc(f, r, c);
+            float acc = 0.0f;
+            for (int k = 0; k < d; ++k) {
+                const float t = px[k * N + r] - px[k * N + c];
+                acc = fmaf(t, t, acc);
+            }
+            float v = matern32(th.nu_code, s2, sqrtf(acc));
+            if (r == c) v += tau2;
+            A[f] = v;
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            const float p = A[0];
+            if (!(p > 0.0f) && lane == 0) s_fail = 1;
+            const float rs = rsqrtf(p);
+            for (int j = 1 + lane; j <= N; j += 32) {
+                const float v = A[pk(j, 0)] * rs;
+                A[pk(j, 0)] = v;
+                col0[j] = v;
+            }
+        }
+        __syncthreads();
+
+        for (int k = 0; k + 1 < N; ++k) {
+            const float* cur = (k & 1) ? col1 : col0;
+            float* nxt = (k & 1) ? col0 : col1;
+            const int kk = k + 1;
+            if (warp == 0) {
+                const float ck = cur[kk];
+                for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fmaf(-cur[j], ck, A[pk(j, kk)]);
+                __syncwarp();
+                const float p = A[pk(kk, kk)];
+                if (!(p > 0.0f) && lane == 0) s_fail = 1;
+                const float rs = rsqrtf(p);
+                for (int j = kk + 1 + lane; j <= N; j += 32) {
+                    const float v = A[pk(j, kk)] * rs;
+                    A[pk(j, kk)] = v;
+                    nxt[j] = v;
+                }
+            }
+            const int S = N - kk;
+            const int TS = (S * (S + 1)) >> 1;
+            for (int f = tid; f < TS; f += NT) {
+                int r, c;
+                tri_rc(f, r, c);
+                const int j = kk + 1 + r, i = kk + 1 + c;
+                A[pk(j, i)] = fmaf(-cur[j], cur[i], A[pk(j, i)]);
+            }
+            __syncthreads();
+        }
+
+        // FP64 accumulation of the quadratic form and the log-determinant
+        double part = 0.0;
+        for (int k = m + tid; k < N; k += NT) {
+            const double z = (double)A[pk(N, k)];
+            part += z * z + log((double)A[pk(k, k)]);
+        }
+        const double s = block_sum<NT>(part, red);
+        if (tid == 0) {
+            double ell = -0.5 * (s + (double)b * kLog2Pi);
+            if (s_fail || !(ell == ell)) {
+                ell = -INFINITY;
+                record_fail(a.fail, blk);
+            }
+            a.ell_blk[blk] = ell;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Large blocks: same algorithm in FP64 with the packed triangle in a global workspace
+// slot (one slot per CTA; the grid never exceeds the number of slots).
+// ---------------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
+    __shared__ double red[NT / 32];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
+
+    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+        const int blk = a.work[w];
+        const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
+        const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
+        const int N = m + b, R = N + 1;
+        const DevTheta th = a.theta[a.bds[blk]];
+        const int d = a.d;
+        double* A = slot;
+        double* col0 = A + (((int64_t)R * (R + 1)) >> 1);
+        double* col1 = col0 + R;
+        double* px = col1 + R;
+
+        for (int t = tid; t < N; t += NT) {
+            const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g];
+            A[pk(N, t)] = a.y[g];
+        }
+        if (tid == 0) {
+            A[pk(N, N)] = 0.0;
+            s_fail = 0;
+        }
+        __syncthreads();
+        // covariance row by row (one warp per row, lanes along the contiguous columns)
+        for (int r = warp; r < N; r += NT / 32) {
+            double* row = A + pk(r, 0);
+            for (int c = lane; c <= r; c += 32) {
+                double acc = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                    acc = fma(t, t, acc);
+                }
+                double v = matern64(th.nu_code, th.sigma2, sqrt(acc));
+                if (r == c) v += th.nugget;
+                row[c] = v;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const double p = A[0];
+            if (!(p > 0.0) && lane == 0) s_fail = 1;
+            const double rs = rsqrt(p);
+            for (int j = 1 + lane; j <= N; j += 32) {
+                const double v = A[pk(j, 0)] * rs;
+                A[pk(j, 0)] = v;
+                col0[j] = v;
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k + 1 < N; ++k) {
+            const double* cur = (k & 1) ? col1 : col0;
+            double* nxt = (k & 1) ? col0 : col1;
+            const int kk = k + 1;
+            if (warp == 0) {
+                const double ck = cur[kk];
+                for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
+                __syncwarp();
+                const double p = A[pk(kk, kk)];
+                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                const double rs = rsqrt(p);
+                for (int j = kk + 1 + lane; j <= N; j += 32) {
+                    const double v = A[pk(j, kk)] * rs;
+                    A[pk(j, kk)] = v;
+                    nxt[j] = v;
+                }
+            }
+            // rows kk+1..N: iterate row-wise (contiguous columns) for coalescing
+            for (int j = kk + 1 + warp; j <= N; j += NT / 32) {
+                const double cj = cur[j];
+                double* row = A + pk(j, 0);
+                for (int i = kk + 1 + lane; i <= j; i += 32) row[i] = fma(-cj, cur[i], row[i]);
+            }
+            __syncthreads();
+        }
+        double part = 0.0;
+        for (int k = m + tid; k < N; k += NT) {
+            const double z = A[pk(N, k)];
+            part += z * z + log(A[pk(k, k)]);
+        }
+        const double s = block_sum<NT>(part, red);
+        if (tid == 0) {
+            double ell = -0.5 * (s + (double)b * kLog2Pi);
+            if (s_fail || !(ell == ell)) {
+                ell = -INFINITY;
+                record_fail(a.fail, blk);
+            }
+            a.ell_blk[blk] = ell;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Deterministic per-dataset sum of the per-block terms (fixed thread->block map, Neumaier
+// compensation per thread, fixed-order combination).
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reduce(const double* ell_blk, const int64_t* ds_off,
+                                                double* out) {
+    __shared__ double ss[256], sc[256];
+    const int ds = blockIdx.x, tid = threadIdx.x;
+    const int64_t lo = ds_off[ds], hi = ds_off[ds + 1];
+    double s = 0.0, c = 0.0;
+    for (int64_t i = lo + tid; i < hi; i += 256) {
+        const double x = ell_blk[i];
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    ss[tid] = s;
+    sc[tid] = c;
+    __syncthreads();
+    if (tid == 0) {
+        double S = 0.0, C = 0.0;
+        for (int i = 0; i < 256; ++i) {
+            const double x = ss[i];
+            const double t = S + x;
+            if (fabs(S) >= fabs(x)) C += (S - t) + x;
+            else C += (x - t) + S;
+            S = t;
+            C += sc[i];
+        }
+        double r = S + C;
+        if (!(r == r)) r = -INFINITY;
+        out[ds] = r;
+    }
+}
+
+__global__ void k_fail_reset(unsigned long long* f) { *f = ~0ull; }
+
+template <int NT>
+cudaError_t launch_kind(int kind, int grid, size_t smem, const LLArgs& a, cudaStream_t s) {
+    if (kind == 0) {
+        auto k = k_ll_fp64<NT>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NT, smem, s>>>(a);
+    } else if (kind == 1) {
+        auto k = k_ll_mixed<NT>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NT, smem, s>>>(a);
+    } else {
+        k_ll_large<NT><<<grid, NT, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Shared-memory footprint of one CTA for augmented size N.
+size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
+    (void)threads;
+    const size_t R = (size_t)nmax + 1;
+    const size_t el = kind == 1 ? sizeof(float) : sizeof(double);
+    if (kind == 2) return 0;
+    size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
+    return (bytes + 15) & ~(size_t)15;
+}
+
+// Largest N the shared-memory kernels take (227 KB opt-in per CTA, minus static smem).
+int bv_smem_max_n(int kind, int d) {
+    const size_t cap = 227 * 1024 - 2048;
+    int n = 8;
+    while (bv_smem_bytes(kind, n + 1, d, 0) <= cap) ++n;
+    return n;
+}
+
+int bv_max_threads_for(int kind) { return kind == 2 ? 256 : 512; }
+
+cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
+    if (bp.nwork == 0) return cudaSuccess;
+    LLArgs a = a0;
+    a.work = bp.d_work;
+    a.nwork = bp.nwork;
+    switch (bp.threads) {
+        case 64: return launch_kind<64>(bp.kind, bp.grid, bp.smem, a, s);
+        case 128: return launch_kind<128>(bp.kind, bp.grid, bp.smem, a, s);
+        case 256: return launch_kind<256>(bp.kind, bp.grid, bp.smem, a, s);
+        case 512: return launch_kind<512>(bp.kind, bp.grid, bp.smem, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t bv_launch_reduce(const double* ell_blk, const int64_t* ds_blk_off, int32_t ndata,
+                             const unsigned long long* fail, const int32_t* bds, double* out,
+                             cudaStream_t s) {
+    (void)fail;
+    (void)bds;
+    k_reduce<<<ndata, 256, 0, s>>>(ell_blk, ds_blk_off, out);
+    return cudaGetLastError();
+}
+
+cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {
+    k_fail_reset<<<1, 1, 0, s>>>(fail);
+    return cudaGetLastError();
+}
+
+// Occupancy helper for the planner.
+int bv_occupancy(int kind, int threads, size_t smem) {
+    int nb = 0;
+    cudaError_t e = cudaSuccess;
+#define BV_OCC(NT)                                                                           \
+    if (threads == NT) {                                                                     \
+        if (kind == 0) {                                                                     \
+            cudaFuncSetAttribute(k_ll_fp64<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                 \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT>, NT, smem);  \
+        } else if (kind == 1) {                                                              \
+            cudaFuncSetAttribute(k_ll_mixed<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                 \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT>, NT, smem); \
+        } else {                                                                             \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
+        }                                                                                    \
+    }
+    BV_OCC(64) BV_OCC(128) BV_OCC(256) BV_OCC(512)
+#undef BV_OCC
+    if (e != cudaSuccess) return 0;
+    return nb;
+}

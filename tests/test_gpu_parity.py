@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle on the same
+seeded inputs.  Blocks and neighbour sets must be bit-exact; the FP64 log-likelihood
+within 1e-10 relative (per block within 1e-9 absolute); mixed precision within a stated
+bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def bv():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2410_04477_gb300 import bv as _bv
+    return _bv
+
+
+def _otheta(s2, beta, nu, tau2, ranges=None):
+    return oracle.theta(s2, beta, nu, tau2, ranges)
+
+
+def _gtheta(bv, s2, beta, nu, tau2, ranges=None):
+    return bv.theta(s2, beta, nu, tau2, ranges)
+
+
+def _c1(n=2000, d=2, seed=0, nu=0.5, beta=0.1, tau2=1e-6, ranges=None):
+    locs = synth.locs_uniform(n, d, seed)
+    th = _otheta(1.0, beta, nu, tau2, ranges)
+    y = oracle.exact_draw(th, locs, synth.normal(seed, 20, n))
+    return locs, y, th
+
+
+@pytest.mark.parametrize("n,d,bc,seed", [(2000, 2, 200, 0), (1500, 3, 150, 1), (3000, 2, 37, 2)])
+def test_blocks_bit_exact(bv, n, d, bc, seed):
+    locs = synth.locs_uniform(n, d, seed)
+    bp_o, pi_o, ce_o = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    with bv.Context() as ctx:
+        ctx.set_data(locs)
+        bp, pi = ctx.build_blocks(bc, seed=seed, iters=20)
+        _, _, ce = ctx.blocks()
+    np.testing.assert_array_equal(bp, bp_o)
+    np.testing.assert_array_equal(pi, pi_o)
+    assert ce.tobytes() == ce_o.tobytes()
+
+
+@pytest.mark.parametrize("n,d,bc,m", [(2000, 2, 200, 30), (1200, 3, 120, 60), (400, 2, 40, 10**5),
+                                      (20000, 2, 2000, 30)])
+def test_neighbors_bit_exact(bv, n, d, bc, m):
+    locs = synth.locs_uniform(n, d, 7)
+    with bv.Context() as ctx:
+        ctx.set_data(locs)
+        bp, pi = ctx.build_blocks(bc, seed=3, iters=20)
+        _, _, ce = ctx.blocks()
+        nnp, nni = ctx.select_neighbors(m)
+    bp_o, pi_o, ce_o = oracle.build_blocks(locs, bc, seed=3, iters=20)
+    np.testing.assert_array_equal(pi, pi_o)
+    nnp_o, nni_o = oracle.select_neighbors(locs, bp_o, pi_o, ce_o, m)
+    np.testing.assert_array_equal(nnp, nnp_o)
+    np.testing.assert_array_equal(nni, nni_o)
+
+
+def test_neighbors_lattice_ties(bv):
+    g = np.arange(40) / 40.0
+    locs = np.array([(x, y) for x in g for y in g])
+    with bv.Context() as ctx:
+        ctx.set_data(locs)
+        ctx.build_blocks(160, seed=1, iters=5)
+        nnp, nni = ctx.select_neighbors(24)
+    bp_o, pi_o, ce_o = oracle.build_blocks(locs, 160, seed=1, iters=5)
+    nnp_o, nni_o = oracle.select_neighbors(locs, bp_o, pi_o, ce_o, 24)
+    np.testing.assert_array_equal(nni, nni_o)
+
+
+def _gpu_ll(bv, locs, y, bc, m, th_args, prec=0, seed=0):
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        bp, pi = ctx.build_blocks(bc, seed=seed, iters=20)
+        nnp, nni = ctx.select_neighbors(m)
+        ll, per, st = ctx.loglik(_gtheta(bv, *th_args), prec, per_block=True)
+    return ll, per, (bp, pi, nnp, nni)
+
+
+def _oracle_struct(locs, bc, m, seed=0):
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+    return bp, pi, nnp, nni
+
+
+def _same_struct(g, o):
+    for a, b in zip(g, o):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("nu,beta,tau2", [(0.5, 0.1, 1e-6), (1.5, 0.05, 1e-4), (2.5, 0.03, 1e-3)])
+def test_loglik_fp64_matches_oracle_c1(bv, nu, beta, tau2):
+    locs, y, th = _c1(nu=nu, beta=beta, tau2=tau2)
+    ll, per, gs = _gpu_ll(bv, locs, y, 200, 30, (1.0, beta, nu, tau2))
+    os_ = _oracle_struct(locs, 200, 30)
+    _same_struct(gs, os_)
+    ll_o, per_o, _ = oracle.loglik(th, locs, y, *os_)
+    assert abs(ll - ll_o) <= REL64 * abs(ll_o), (ll, ll_o)
+    np.testing.assert_allclose(per, per_o, rtol=1e-9, atol=1e-9)
+
+
+def test_loglik_fp64_anisotropic_3d(bv):
+    n = 1500
+    locs = synth.locs_uniform(n, 3, 5)
+    rng = [0.1, 0.1, 0.3]
+    th = _otheta(1.3, None, 0.5, 1e-3, rng)
+    y = oracle.exact_draw(th, locs, synth.normal(5, 20, n))
+    ll, per, gs = _gpu_ll(bv, locs, y, 150, 60, (1.3, None, 0.5, 1e-3, rng))
+    os_ = _oracle_struct(locs, 150, 60)
+    _same_struct(gs, os_)
+    ll_o, per_o, _ = oracle.loglik(th, locs, y, *os_)
+    assert abs(ll - ll_o) <= REL64 * abs(ll_o)
+    np.testing.assert_allclose(per, per_o, rtol=1e-9, atol=1e-9)
+
+
+def test_loglik_large_blocks_and_exact_limits(bv):
+    # one block (Eq. 1) and all-previous-points conditioning (Eq. 2-3) -> exact likelihood;
+    # both run the global-memory path (N up to n)
+    n = 1200
+    locs, y, th = _c1(n=n, nu=1.5, beta=0.05, tau2=1e-2, seed=3)
+    exact = oracle.exact_loglik(th, locs, y)
+    gt = _gtheta(bv, 1.0, 0.05, 1.5, 1e-2)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.set_blocks(np.array([0, n]), np.arange(n, dtype=np.int32))
+        ctx.set_neighbors(np.array([0, 0]), np.zeros(0, np.int32))
+        l1 = ctx.loglik(gt, bv.BV_FP64)
+        ctx.build_blocks(40, seed=2, iters=20)
+        ctx.select_neighbors(n)
+        l2 = ctx.loglik(gt, bv.BV_FP64)
+    assert abs(l1 - exact) <= REL64 * abs(exact)
+    assert abs(l2 - exact) <= 1e-9 * abs(exact)
+    l2o, _, _ = oracle.loglik(th, locs, y, *_oracle_struct(locs, 40, n, seed=2))
+    assert abs(l2 - l2o) <= REL64 * abs(l2o)
+
+
+def test_loglik_mixed_precision_bound(bv):
+    locs, y, th = _c1(nu=1.5, beta=0.05, tau2=1e-4)
+    ll64 = _gpu_ll(bv, locs, y, 200, 30, (1.0, 0.05, 1.5, 1e-4), prec=0)[0]
+    llm = _gpu_ll(bv, locs, y, 200, 30, (1.0, 0.05, 1.5, 1e-4), prec=1)[0]
+    llo, _, _ = oracle.loglik(th, locs, y, *_oracle_struct(locs, 200, 30))
+    assert abs(ll64 - llo) <= REL64 * abs(llo)
+    rel = abs(llm - llo) / abs(llo)
+    # mixed precision: FP32 covariance/updates; stated bound for this configuration
+    assert rel < 1e-4, rel
+
+
+def test_singletons_and_no_neighbours(bv):
+    n = 300
+    locs, y, th = _c1(n=n, seed=4, tau2=1e-2)
+    gt = _gtheta(bv, 1.0, 0.1, 0.5, 1e-2)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.set_blocks(np.arange(n + 1), np.arange(n, dtype=np.int32))
+        ctx.set_neighbors(np.zeros(n + 1, np.int64), np.zeros(0, np.int32))
+        ll = ctx.loglik(gt)
+    v = 1.0 + 1e-2
+    want = np.sum(-0.5 * (np.log(2 * np.pi) + np.log(v) + y ** 2 / v))
+    assert abs(ll - want) <= 1e-12 * abs(want)
+
+
+def test_not_positive_definite_status(bv):
+    locs, y, th = _c1(n=400, seed=6)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        bp, pi = ctx.build_blocks(40, seed=1, iters=5)
+        locs2 = locs.copy()
+        locs2[pi[1]] = locs2[pi[0]]  # duplicate site in the first block, no nugget
+        ctx.set_data(locs2, y)
+        ctx.set_blocks(bp, pi)
+        ctx.select_neighbors(10)
+        ll, per, st = ctx.loglik(_gtheta(bv, 1.0, 0.1, 1.5, 0.0), per_block=True, allow_notpd=True)
+    assert st == bv.BV_ENOTPD and ll == -np.inf and per[0] == -np.inf
+
+
+def test_multi_dataset_batched(bv):
+    sizes = [600, 1100, 850]
+    locs_list, y_list, ths = [], [], []
+    for k, n in enumerate(sizes):
+        l, y, _ = _c1(n=n, seed=10 + k, nu=[0.5, 1.5, 2.5][k], beta=[0.1, 0.05, 0.03][k], tau2=1e-3)
+        locs_list.append(l)
+        y_list.append(y)
+        ths.append((1.0 + 0.2 * k, [0.1, 0.05, 0.03][k], [0.5, 1.5, 2.5][k], 1e-3))
+    with bv.Context() as ctx:
+        ctx.set_datasets(locs_list, y_list)
+        ctx.build_blocks_multi([n // 10 for n in sizes], seed=0, iters=20)
+        ctx.select_neighbors(30)
+        out = ctx.loglik_multi([_gtheta(bv, *t) for t in ths])
+        bp, pi, ce = ctx.blocks()
+        nnp, nni = ctx.neighbors()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    nb_per = [len(oracle.build_blocks(locs_list[k], sizes[k] // 10, seed=k)[0]) - 1 for k in range(3)]
+    boff = np.concatenate([[0], np.cumsum(nb_per)])
+    for k in range(3):
+        bpo, pio, ceo = oracle.build_blocks(locs_list[k], sizes[k] // 10, seed=k)
+        sl = slice(boff[k], boff[k + 1] + 1)
+        np.testing.assert_array_equal(bp[sl] - bp[boff[k]], bpo)
+        np.testing.assert_array_equal(pi[bp[boff[k]]:bp[boff[k + 1]]] - off[k], pio)
+        nnpo, nnio = oracle.select_neighbors(locs_list[k], bpo, pio, ceo, 30)
+        seg = nni[nnp[boff[k]]:nnp[boff[k + 1]]] - off[k]
+        np.testing.assert_array_equal(seg, nnio)
+        llo, _, _ = oracle.loglik(_otheta(*ths[k]), locs_list[k], y_list[k], bpo, pio, nnpo, nnio)
+        assert abs(out[k] - llo) <= REL64 * abs(llo)
+
+
+def test_async_device_output(bv):
+    import torch
+    locs, y, th = _c1(n=1000, seed=8)
+    gt = _gtheta(bv, 1.0, 0.1, 0.5, 1e-6)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(100, seed=0)
+        ctx.select_neighbors(30)
+        ref = ctx.loglik(gt)
+        dout = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.loglik_async([gt], bv.BV_FP64, dout.data_ptr())
+        st, fb = ctx.sync()
+        assert st == 0 and fb == -1
+        assert dout.item() == ref
+
+
+def test_sampler_matches_oracle_draw(bv):
+    n = 1500
+    locs = synth.locs_uniform(n, 2, 9)
+    z = synth.normal(9, 21, n)
+    th = _otheta(1.2, 0.05, 1.5, 1e-3)
+    with bv.Context() as ctx:
+        ctx.set_data(locs)
+        ctx.build_blocks(150, seed=4, iters=20)
+        ctx.select_neighbors(80)
+        y = ctx.simulate(_gtheta(bv, 1.2, 0.05, 1.5, 1e-3), z)
+        gs = ctx.blocks()[:2] + ctx.neighbors()
+    os_ = _oracle_struct(locs, 150, 80, seed=4)
+    _same_struct(gs, os_)
+    yo = oracle.bv_draw(th, locs, *os_, z)
+    np.testing.assert_allclose(y, yo, rtol=1e-9, atol=1e-10)
