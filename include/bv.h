@@ -163,6 +163,34 @@ int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
  * (BV_ENOTPD with the first failing block in *failed_block, may be NULL). */
 int bv_sync(bv_ctx* ctx, int64_t* failed_block);
 
+/* FP64 log-likelihood for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment form of bv_loglik.  Some callers may not call
+ * cudaMalloc at all: code running inside a host callback or another library's
+ * stream-ordered section, under a memory manager that owns every device allocation, or
+ * in a latency-bound loop that cannot afford an allocation's implicit synchronisation.
+ * This entry point allocates nothing: the caller passes every input and output as a
+ * device pointer, and the per-block partial results live in a static device array of
+ * BV_NOALLOC_MAX_BLOCKS + 32 doubles (about 8 MiB) that each GPU loading the library
+ * keeps until the process exits.
+ *   d_locs: SoA coordinates, d_locs[k * n + j] = coordinate k of point j (d in 1..3);
+ *   d_y[n]; d_block_ptr[bc+1], d_point_idx[n], d_nn_ptr[bc+1], d_nn_idx[d_nn_ptr[bc]]:
+ *   the block and conditioning structure as produced by bv_build_blocks /
+ *   bv_select_neighbors; d_out_loglik[1] receives ell; d_out_per_block[bc] (may be NULL)
+ *   the per-block terms.  cuda_stream: the stream to use (NULL = legacy default stream).
+ * Limits: bc <= BV_NOALLOC_MAX_BLOCKS, and every block's m_i + b_i at most 235 (d = 1),
+ * 234 (d = 2) or 233 (d = 3); larger sizes return BV_EINVAL before any kernel reads the
+ * structure.  Returns after the stream drains; BV_ENOTPD as bv_loglik.
+ * The first call made with a device current looks up the array's device address for
+ * that device: make that first call outside any stream capture.  Every call reuses the
+ * same array (its status words are reset at the start of each call, its per-block
+ * entries are rewritten), so calls whose work overlaps on the GPU -- different streams
+ * or host threads without synchronisation -- race and must be serialised by the caller. */
+#define BV_NOALLOC_MAX_BLOCKS 1048576
+int bv_loglik_noalloc(const bv_theta* theta, const double* d_locs, const double* d_y, int64_t n,
+                      int32_t d, int64_t bc, const int64_t* d_block_ptr, const int32_t* d_point_idx,
+                      const int64_t* d_nn_ptr, const int32_t* d_nn_idx, double* d_out_loglik,
+                      double* d_out_per_block, void* cuda_stream);
+
 /* Run the launch-shape autotuner for `precision` now (otherwise it runs on first use).
  * Times each candidate shape of every size bin on the current structure. */
 int bv_autotune(bv_ctx* ctx, int32_t precision);

@@ -80,6 +80,8 @@ _SIGS = {
     "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
+    "bv_loglik_noalloc": (_int, [_P(bv_theta), _vp, _vp, _i64, _i32, _i64, _vp, _vp, _vp, _vp,
+                                 _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
@@ -96,6 +98,19 @@ for _name, (_res, _args) in _SIGS.items():
     _fn.argtypes = _args
 
 EXPORTED = tuple(_SIGS)
+
+
+BV_NOALLOC_MAX_BLOCKS = 1048576
+
+
+def loglik_noalloc(th: bv_theta, d_locs: int, d_y: int, n: int, d: int, bc: int, d_block_ptr: int,
+                   d_point_idx: int, d_nn_ptr: int, d_nn_idx: int, d_out: int,
+                   d_out_per_block: int | None = None, stream: int | None = None) -> int:
+    """bv_loglik_noalloc on caller-owned device buffers (raw device pointers); returns the
+    status (BV_OK or BV_ENOTPD), raises on any other."""
+    st = _lib.bv_loglik_noalloc(ctypes.byref(th), d_locs, d_y, n, d, bc, d_block_ptr, d_point_idx,
+                                d_nn_ptr, d_nn_idx, d_out, d_out_per_block, stream)
+    return _check(st, "bv_loglik_noalloc", allow=(BV_ENOTPD,))
 
 
 class BVError(RuntimeError):
