@@ -203,6 +203,11 @@ int bv_autotune(bv_ctx* ctx, int32_t precision);
 int bv_plan_info(bv_ctx* ctx, int32_t precision, int32_t* launches_per_eval, int32_t* n_bins,
                  double* flops_per_eval, double* cov_entries_per_eval);
 
+/* Diagnostic: the library's device FP64 exponential e^{-x} (x >= 0; Tang's table-driven
+ * method, used for the Matern kernel in the FP64 path) evaluated on the GPU for host
+ * inputs x[n] into host out[n]. */
+int bv_exp_neg_check(int64_t n, const double* x, double* out);
+
 /* ---- block-Vecchia sampler (Eq. 4 read generatively) ------------------------------ */
 
 /* Draw y from the block-Vecchia model of dataset 0 at theta with the current blocks and

@@ -84,6 +84,7 @@ _SIGS = {
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
+    "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
                       _P(bv_theta), _P(_d), _P(_i32)]),
@@ -111,6 +112,14 @@ def loglik_noalloc(th: bv_theta, d_locs: int, d_y: int, n: int, d: int, bc: int,
     st = _lib.bv_loglik_noalloc(ctypes.byref(th), d_locs, d_y, n, d, bc, d_block_ptr, d_point_idx,
                                 d_nn_ptr, d_nn_idx, d_out, d_out_per_block, stream)
     return _check(st, "bv_loglik_noalloc", allow=(BV_ENOTPD,))
+
+
+def exp_neg_check(x):
+    """The library's device FP64 e^{-x} for an array x >= 0 (diagnostic)."""
+    xv = _arr(x, np.float64)
+    out = np.empty_like(xv)
+    _check(_lib.bv_exp_neg_check(xv.size, _p(xv, _d), _p(out, _d)), "bv_exp_neg_check")
+    return out
 
 
 class BVError(RuntimeError):

@@ -524,6 +524,7 @@ static LLArgs make_args(bv_ctx* c) {
     a.fail = c->d_fail;
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
+    bv_exp_consts(&a.ex);
     return a;
 }
 

@@ -44,6 +44,17 @@ struct DevTheta {
     int32_t pad;
 };
 
+// Constants of the table-driven FP64 exponential (Tang, "Table-driven implementation of
+// the exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
+// e^{-x} = 2^{n/32} e^{r},  n = round(-x 32/ln2),  r = -x - n (L1 + L2),  L1 + L2 = ln2/32,
+// 2^{n/32} = 2^{floor(n/32)} tab[n mod 32].  Filled on the host in long double.
+struct ExpConsts {
+    double tab[32];   // 2^{j/32}, j = 0..31
+    double k;         // 32 / ln 2
+    double l1, l2;    // ln2/32 split: l1 has its low 21 bits zero so n*l1 is exact
+};
+void bv_exp_consts(ExpConsts* out);
+
 // Everything a log-likelihood kernel reads.  Locations are SoA: coordinate k of point j
 // is locs[k * n_tot + j].  Block p has points pidx[bptr[p] .. bptr[p+1]) and
 // conditioning points nidx[nptr[p] .. nptr[p+1]).
@@ -65,6 +76,7 @@ struct LLArgs {
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
     double* ws;              // global workspace (large-block path)
     int64_t ws_stride;       // doubles per workspace slot
+    ExpConsts ex;            // FP64 exponential constants
 };
 
 // Per-size-bin launch plan entry.

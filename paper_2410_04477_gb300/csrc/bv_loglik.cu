@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "bv_internal.h"
 
@@ -46,13 +47,40 @@ __device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
     c = f - (rr * (rr + 1) >> 1);
 }
 
+// e^{-x} for x >= 0 by Tang's table-driven method (see ExpConsts): reduction to
+// |r| <= ln2/64, e^r - 1 by its Taylor polynomial through r^6 (truncation < 4e-18), one
+// table multiply and an exponent-field scaling.  11 FP64 operations.  Results below
+// e^{-700} are flushed to zero (a covariance entry that small is irrelevant next to the
+// diagonal).  Accuracy: within 2 ulp of e^{-x} (checked against libm in the tests).
+__device__ __forceinline__ double exp_neg(double x, const double* __restrict__ tab, double K, double L1,
+                                          double L2) {
+    const double shift = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+    const double s = fma(x, -K, shift);
+    const int n = __double2loint(s);
+    const double nd = s - shift;               // round(-x K), exact
+    double r = fma(nd, -L1, -x);
+    r = fma(nd, -L2, r);
+    double q = fma(1.0 / 720.0, r, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double p = fma(q * r, r, r);         // e^r - 1
+    const double t = tab[n & 31];
+    const double v = fma(t, p, t);             // 2^{j/32} e^r in [0.98, 2)
+    const int hi = __double2hiint(v) + ((n >> 5) << 20);
+    const double res = __hiloint2double(hi, __double2loint(v));
+    return x > 700.0 ? 0.0 : res;
+}
+
 // Matern correlation times sigma^2 at scaled distance x (Eq. 5, half-integer closed forms).
-__device__ __forceinline__ double matern64(int nu, double sigma2, double x) {
-    const double e = exp(-x);
+__device__ __forceinline__ double matern64t(int nu, double sigma2, double x, const double* tab, double K,
+                                            double L1, double L2) {
+    const double e = exp_neg(x, tab, K, L1, L2);
     if (nu == NU_HALF) return sigma2 * e;
     if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
     return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
 }
+
 
 __device__ __forceinline__ float matern32(int nu, float sigma2, float x) {
     const float e = expf(-x);
@@ -87,8 +115,11 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double* sm = reinterpret_cast<double*>(smraw);
     __shared__ double red[NT / 32];
+    __shared__ double etab[32];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
 
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int blk = a.work[w];
@@ -124,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                 const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                 acc = fma(t, t, acc);
             }
-            double v = matern64(th.nu_code, th.sigma2, sqrt(acc));
+            double v = matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
         }
@@ -312,9 +343,12 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
 template <int NT>
 __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
     __shared__ double red[NT / 32];
+    __shared__ double etab[32];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
+    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
 
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int blk = a.work[w];
@@ -347,7 +381,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
                     const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                     acc = fma(t, t, acc);
                 }
-                double v = matern64(th.nu_code, th.sigma2, sqrt(acc));
+                double v = matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
                 if (r == c) v += th.nugget;
                 row[c] = v;
             }
@@ -445,21 +479,34 @@ __global__ void __launch_bounds__(256) k_reduce(const double* ell_blk, const int
 
 __global__ void k_fail_reset(unsigned long long* f) { *f = ~0ull; }
 
+__global__ void k_exp_check(const double* x, double* out, int64_t n, ExpConsts ex) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = exp_neg(x[i], ex.tab, ex.k, ex.l1, ex.l2);
+}
+
+// Dynamic shared-memory cap of the shared-memory kernels.  Every size bin launches the
+// same instantiation with its own footprint, so the per-function maximum is set once to
+// this cap and never lowered (a launch captured in a graph with a larger footprint must
+// stay valid when a smaller bin is launched later).
+constexpr int kSmemCap = 227 * 1024 - 2048;
+
+template <int NT>
+cudaError_t set_smem_cap() {
+    cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_mixed<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    return e;
+}
+
 template <int NT>
 cudaError_t launch_kind(int kind, int grid, size_t smem, const LLArgs& a, cudaStream_t s) {
-    if (kind == 0) {
-        auto k = k_ll_fp64<NT>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (kind != 2) {  // per device and function; idempotent and cheap
+        cudaError_t e = set_smem_cap<NT>();
         if (e != cudaSuccess) return e;
-        k<<<grid, NT, smem, s>>>(a);
-    } else if (kind == 1) {
-        auto k = k_ll_mixed<NT>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NT, smem, s>>>(a);
-    } else {
-        k_ll_large<NT><<<grid, NT, 0, s>>>(a);
     }
+    if (kind == 0) k_ll_fp64<NT><<<grid, NT, smem, s>>>(a);
+    else if (kind == 1) k_ll_mixed<NT><<<grid, NT, smem, s>>>(a);
+    else k_ll_large<NT><<<grid, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -477,7 +524,7 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
 
 // Largest N the shared-memory kernels take (227 KB opt-in per CTA, minus static smem).
 int bv_smem_max_n(int kind, int d) {
-    const size_t cap = 227 * 1024 - 2048;
+    const size_t cap = kSmemCap;
     int n = 8;
     while (bv_smem_bytes(kind, n + 1, d, 0) <= cap) ++n;
     return n;
@@ -517,22 +564,51 @@ cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {
 int bv_occupancy(int kind, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e = cudaSuccess;
-#define BV_OCC(NT)                                                                           \
-    if (threads == NT) {                                                                     \
-        if (kind == 0) {                                                                     \
-            cudaFuncSetAttribute(k_ll_fp64<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                 \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT>, NT, smem);  \
-        } else if (kind == 1) {                                                              \
-            cudaFuncSetAttribute(k_ll_mixed<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                 \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT>, NT, smem); \
-        } else {                                                                             \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
-        }                                                                                    \
+#define BV_OCC(NT)                                                                            \
+    if (threads == NT) {                                                                      \
+        if (kind != 2) e = set_smem_cap<NT>();                                                \
+        if (e == cudaSuccess) {                                                               \
+            if (kind == 0)                                                                    \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT>, NT, smem);  \
+            else if (kind == 1)                                                               \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT>, NT, smem); \
+            else                                                                              \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
+        }                                                                                     \
     }
     BV_OCC(64) BV_OCC(128) BV_OCC(256) BV_OCC(512)
 #undef BV_OCC
     if (e != cudaSuccess) return 0;
     return nb;
+}
+
+void bv_exp_consts(ExpConsts* o) {
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (int j = 0; j < 32; ++j) o->tab[j] = (double)exp2l((long double)j / 32.0L);
+    const long double L = ln2 / 32.0L;
+    double l1 = (double)L;
+    unsigned long long bits;
+    memcpy(&bits, &l1, sizeof(bits));
+    bits &= ~((1ull << 21) - 1ull);
+    memcpy(&l1, &bits, sizeof(bits));
+    o->l1 = l1;
+    o->l2 = (double)(L - (long double)l1);
+    o->k = (double)(32.0L / ln2);
+}
+
+// Diagnostic: the library's FP64 exp(-x) on the device for host inputs x[n].
+extern "C" int bv_exp_neg_check(int64_t n, const double* x, double* out) {
+    if (n <= 0 || !x || !out) return BV_EINVAL;
+    ExpConsts ex;
+    bv_exp_consts(&ex);
+    double *dx = nullptr, *dy = nullptr;
+    BV_CUDA(cudaMalloc(&dx, sizeof(double) * n));
+    BV_CUDA(cudaMalloc(&dy, sizeof(double) * n));
+    BV_CUDA(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice));
+    k_exp_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, dy, n, ex);
+    BV_CUDA(cudaGetLastError());
+    BV_CUDA(cudaMemcpy(out, dy, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    cudaFree(dx);
+    cudaFree(dy);
+    return BV_OK;
 }

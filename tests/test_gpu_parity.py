@@ -244,3 +244,15 @@ def test_sampler_matches_oracle_draw(bv):
     _same_struct(gs, os_)
     yo = oracle.bv_draw(th, locs, *os_, z)
     np.testing.assert_allclose(y, yo, rtol=1e-9, atol=1e-10)
+
+
+def test_device_exp_within_two_ulp(bv):
+    # the FP64 path's own e^{-x} (Tang's table-driven method) against libm's exp
+    x = np.concatenate([np.linspace(0, 1, 20001), np.linspace(1, 60, 50001), np.linspace(60, 700, 20001),
+                        [0.0, 1e-300, 1e-17, 2.0 ** -30, 699.999]])
+    got = bv.exp_neg_check(x)
+    want = np.exp(-x)
+    ulp = np.spacing(want)
+    err = np.abs(got - want) / ulp
+    assert err.max() <= 2.0, (err.max(), x[np.argmax(err)])
+    assert bv.exp_neg_check(np.array([700.5, 800.0, 1e6])).max() == 0.0
