@@ -240,18 +240,53 @@ int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_the
 
 /* ---- learned warm start --------------------------------------------------------- */
 
-/* Number of summary features per dataset: a 32-bin empirical semivariogram on
- * (0, 0.5] plus 8 statistics (log variance of y, block-size mean/std/min/max, mean
- * conditioning size, log n, dimension). */
-#define BV_NFEAT 40
+/* The paper suggests warm-starting the estimation from a cheaper fit (Sec. 2.3: estimate
+ * at small bc/m, reuse as the starting value).  The library adds a learned warm start: a
+ * small MLP maps per-dataset summary features to a starting theta, and the cold-started
+ * search remains the fallback and the judge of the final estimate. */
 
-/* Features of every dataset in the context (GPU), out[ndatasets x BV_NFEAT] (host).
- * The semivariogram uses a seeded subsample of min(n, max_points) points. */
+/* Features per dataset (BV_NFEAT floats):
+ *   [0..31]  empirical semivariogram gamma_k / var(y) in 32 equal bins of the distance h on
+ *            (0, 0.5]: bin k = min(31, floor(64 h)); gamma_k = mean over pairs in the bin of
+ *            (y_i - y_j)^2 / 2 (0 if the bin is empty), over a seeded subsample of
+ *            min(n, max_points) points (point j kept when floor(r_j n / 2^64) < max_points,
+ *            r_j = SplitMix64 draw j of stream seed);
+ *   [32] log var(y); [33..36] block size mean, std, min, max; [37] mean conditioning
+ *   size m_i; [38] log n; [39] d.
+ * Blocks and neighbours must exist.  out[ndatasets x BV_NFEAT] (host).  Synchronous. */
+#define BV_NFEAT 40
 int bv_features(bv_ctx* ctx, int32_t max_points, uint64_t seed, float* out);
 
-/* Predict a starting theta for dataset 0 with the warm-start MLP whose weights were
- * loaded by bv_warmstart_load (nu is taken from theta_in, which also supplies aniso
- * flags; sigma^2, range and nugget are predicted).  Synchronous. */
+/* MLP: BV_NFEAT inputs (standardised) -> 3 x 128 GELU (exact erf form) -> 6 outputs:
+ * standardised (log sigma^2, log beta, log tau^2) and 3 logits for nu in {0.5, 1.5, 2.5}.
+ * A weights blob is BV_MLP_BLOB floats: BV_NFEAT input means, BV_NFEAT input scales,
+ * 3 target means, 3 target scales, then the BV_MLP_NPARAM parameters
+ * (W1[40x128], b1, W2[128x128], b2, W3[128x128], b3, W4[128x6], b4; row-major [in][out]). */
+#define BV_MLP_NPARAM 39046
+#define BV_MLP_BLOB (BV_MLP_NPARAM + 2 * BV_NFEAT + 6)
+
+/* Train on the GPU with the library's own forward, backward and Adam kernels (FP32):
+ * X[n x BV_NFEAT], T[n x 4] = (log sigma^2, log beta, log tau^2, nu) (host).  Loss = mean
+ * squared error of the standardised regression outputs / 3 + cross-entropy of the nu
+ * class.  Mini-batches of `batch` from a seeded shuffle, `epochs` passes, Adam(lr, 0.9,
+ * 0.999, 1e-8).  blob_out[BV_MLP_BLOB] receives the trained weights and standardisation;
+ * loss_out[epochs] (may be NULL) the mean training loss per epoch. */
+int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t epochs, int32_t batch, float lr,
+                 uint64_t seed, float* blob_out, float* loss_out);
+
+/* Forward pass on the GPU: out[n x 6] = raw outputs (standardised regression outputs,
+ * nu logits) for inputs X[n x BV_NFEAT]. */
+int bv_mlp_forward(const float* blob, const float* X, int64_t n, float* out);
+
+/* Loss and its gradient with respect to the BV_MLP_NPARAM parameters for one batch
+ * (the backward kernels used by training): loss_out[1], grad_out[BV_MLP_NPARAM]. */
+int bv_mlp_loss_grad(const float* blob, const float* X, const float* T, int64_t n, float* loss_out,
+                     float* grad_out);
+
+/* Warm start for dataset 0: load a weights blob from a file (raw floats, BV_MLP_BLOB of
+ * them after a 16-byte header "BVWS", version, count), then predict theta from the
+ * current data's features (max_points 10000, seed 0).  theta_in supplies nu and aniso;
+ * sigma^2, the range (all axes scaled together) and the nugget come from the network. */
 int bv_warmstart_load(bv_ctx* ctx, const char* weights_path);
 int bv_warmstart_predict(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);
 

@@ -18,6 +18,8 @@ BV_OK, BV_EINVAL, BV_ENOMEM, BV_ECUDA, BV_ENOTPD, BV_ETIMEOUT, BV_ESTATE, BV_EIN
 BV_FP64, BV_MIXED = 0, 1
 BV_FREE_SIGMA2, BV_FREE_RANGE, BV_FREE_NUGGET = 1, 2, 4
 BV_NFEAT = 40
+BV_MLP_NPARAM = 39046
+BV_MLP_BLOB = BV_MLP_NPARAM + 2 * BV_NFEAT + 6
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -89,6 +91,9 @@ _SIGS = {
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
                       _P(bv_theta), _P(_d), _P(_i32)]),
     "bv_features": (_int, [_vp, _i32, _u64, _P(_f)]),
+    "bv_mlp_train": (_int, [_P(_f), _P(_f), _i64, _i32, _i32, _f, _u64, _P(_f), _P(_f)]),
+    "bv_mlp_forward": (_int, [_P(_f), _P(_f), _i64, _P(_f)]),
+    "bv_mlp_loss_grad": (_int, [_P(_f), _P(_f), _P(_f), _i64, _P(_f), _P(_f)]),
     "bv_warmstart_load": (_int, [_vp, ctypes.c_char_p]),
     "bv_warmstart_predict": (_int, [_vp, _P(bv_theta), _P(bv_theta)]),
 }
@@ -112,6 +117,39 @@ def loglik_noalloc(th: bv_theta, d_locs: int, d_y: int, n: int, d: int, bc: int,
     st = _lib.bv_loglik_noalloc(ctypes.byref(th), d_locs, d_y, n, d, bc, d_block_ptr, d_point_idx,
                                 d_nn_ptr, d_nn_idx, d_out, d_out_per_block, stream)
     return _check(st, "bv_loglik_noalloc", allow=(BV_ENOTPD,))
+
+
+def mlp_train(X, T, epochs=100, batch=256, lr=1e-3, seed=0):
+    """Train the warm-start MLP on the GPU; returns (blob, per-epoch losses)."""
+    Xv, Tv = _arr(X, np.float32), _arr(T, np.float32)
+    blob = np.empty(BV_MLP_BLOB, np.float32)
+    losses = np.empty(epochs, np.float32)
+    _check(_lib.bv_mlp_train(_p(Xv, _f), _p(Tv, _f), len(Xv), epochs, batch, lr, seed,
+                             _p(blob, _f), _p(losses, _f)), "bv_mlp_train")
+    return blob, losses
+
+
+def mlp_forward(blob, X):
+    b, Xv = _arr(blob, np.float32), _arr(X, np.float32)
+    out = np.empty((len(Xv), 6), np.float32)
+    _check(_lib.bv_mlp_forward(_p(b, _f), _p(Xv, _f), len(Xv), _p(out, _f)), "bv_mlp_forward")
+    return out
+
+
+def mlp_loss_grad(blob, X, T):
+    b, Xv, Tv = _arr(blob, np.float32), _arr(X, np.float32), _arr(T, np.float32)
+    loss = ctypes.c_float(0)
+    g = np.empty(BV_MLP_NPARAM, np.float32)
+    _check(_lib.bv_mlp_loss_grad(_p(b, _f), _p(Xv, _f), _p(Tv, _f), len(Xv), ctypes.byref(loss),
+                                 _p(g, _f)), "bv_mlp_loss_grad")
+    return loss.value, g
+
+
+def save_blob(path, blob):
+    """Weights file for bv_warmstart_load: 16-byte header then the floats."""
+    b = _arr(blob, np.float32)
+    with open(path, "wb") as f:
+        f.write(b"BVWS" + np.array([1, b.size, 0], np.int32).tobytes() + b.tobytes())
 
 
 def exp_neg_check(x):

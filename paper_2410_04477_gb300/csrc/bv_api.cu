@@ -144,6 +144,8 @@ extern "C" void bv_destroy(bv_ctx* c) {
     free_data(c);
     dfree(c->d_fail);
     dfree(c->d_ws);
+    for (auto s : c->side) cudaStreamDestroy(s);
+    for (auto e : c->side_ev) cudaEventDestroy(e);
     if (c->h_fail) cudaFreeHost(c->h_fail);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -498,11 +500,12 @@ int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
 
 static const int kBinEdges[] = {16, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 288, 320};
 
+// CTA sizes of the shared-memory kernels: one panel warp plus 2, 4, 8 or 16 update warps.
 static int default_threads(int kind, int nmax) {
     if (kind == 2) return 256;
-    if (nmax <= 40) return 64;
-    if (nmax <= 112) return 128;
-    return 256;
+    if (nmax <= 48) return 96;
+    if (nmax <= 128) return 160;
+    return 288;
 }
 
 static LLArgs make_args(bv_ctx* c) {
@@ -604,16 +607,6 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
     return BV_OK;
 }
 
-// Enqueue one evaluation of every dataset: theta upload, failure reset, all bins, the
-// per-dataset reduction into d_out.
-static int enqueue_eval(bv_ctx* c, int prec) {
-    BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
-    const LLArgs a = make_args(c);
-    for (const auto& bp : c->plan[prec]) BV_CUDA(bv_launch_bin(bp, a, c->stream));
-    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_ds_blk_off, c->ndata, c->d_fail, c->d_bds, c->d_out, c->stream));
-    return BV_OK;
-}
-
 // Time one bin with the given CTA size (ms, best of `reps`).
 static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     cudaEvent_t e0, e1;
@@ -647,7 +640,7 @@ static int autotune(bv_ctx* c, int prec) {
     BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
     for (auto& bp : c->plan[prec]) {
         if (bp.kind == 2) continue;
-        const int cands[] = {64, 128, 256, 512};
+        const int cands[] = {96, 160, 288, 544};
         int best_t = bp.threads;
         float best_ms = 1e30f;
         for (int t : cands) {
@@ -685,13 +678,42 @@ extern "C" int bv_autotune(bv_ctx* c, int32_t prec) {
     return autotune(c, prec);
 }
 
-// Graph of one evaluation (failure reset, every bin, the reduction), captured once per
-// precision after tuning.  theta is copied in front of each launch.
+// The bins of one evaluation as parallel branches: failure reset, fork, every bin on its
+// own side stream, join, reduction.  Captured into the graph, the branches become
+// independent kernel nodes, so the CTAs of small bins fill the SMs that the tail of a
+// large bin leaves idle.
+static int enqueue_eval_forked(bv_ctx* c, int prec) {
+    const size_t nb = c->plan[prec].size();
+    while (c->side.size() < nb) {
+        cudaStream_t s;
+        BV_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        c->side.push_back(s);
+    }
+    while (c->side_ev.size() < nb + 1) {
+        cudaEvent_t e;
+        BV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->side_ev.push_back(e);
+    }
+    BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
+    BV_CUDA(cudaEventRecord(c->side_ev[0], c->stream));
+    const LLArgs a = make_args(c);
+    for (size_t i = 0; i < nb; ++i) {
+        BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
+        BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
+        BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
+    }
+    for (size_t i = 0; i < nb; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
+    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_ds_blk_off, c->ndata, c->d_fail, c->d_bds, c->d_out, c->stream));
+    return BV_OK;
+}
+
+// Graph of one evaluation, captured once per precision after tuning.  theta is copied in
+// front of each launch.
 static int ensure_graph(bv_ctx* c, int prec) {
     if (c->graph[prec]) return BV_OK;
     cudaGraph_t g = nullptr;
     BV_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    const int st = enqueue_eval(c, prec);
+    const int st = enqueue_eval_forked(c, prec);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != BV_OK) {
         if (g) cudaGraphDestroy(g);

@@ -187,6 +187,8 @@ struct bv_ctx {
     bool plan_valid[2] = {false, false};
     bool tuned[2] = {false, false};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<cudaStream_t> side;   // fork/join streams of the captured graph
+    std::vector<cudaEvent_t> side_ev; // [0] fork, [1..] joins
     double* graph_out[2] = {nullptr, nullptr};
 
     // warm start

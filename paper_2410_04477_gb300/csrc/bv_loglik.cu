@@ -193,13 +193,23 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                     nxt[j] = v;
                 }
             }
-            const int S = N - kk;  // rows kk+1..N, columns kk+1..row
-            const int TS = (S * (S + 1)) >> 1;
-            for (int f = tid; f < TS; f += NT) {
-                int r, c;
-                tri_rc(f, r, c);
-                const int j = kk + 1 + r, i = kk + 1 + c;
-                A[pk(j, i)] = fma(-cur[j], cur[i], A[pk(j, i)]);
+            // warps 1.. update the rest of the trailing triangle (rows kk+1..N, columns
+            // kk+1..row), two independent elements per iteration
+            if (warp > 0) {
+                const int S = N - kk;
+                const int TS = (S * (S + 1)) >> 1;
+                constexpr int NU = NT - 32;
+                for (int f = tid - 32; f < TS; f += 2 * NU) {
+                    int r1, c1, r2, c2;
+                    tri_rc(f, r1, c1);
+                    const bool two = f + NU < TS;
+                    tri_rc(two ? f + NU : f, r2, c2);
+                    const int j1 = kk + 1 + r1, i1 = kk + 1 + c1, j2 = kk + 1 + r2, i2 = kk + 1 + c2;
+                    const double a1 = A[pk(j1, i1)], x1 = cur[j1], y1 = cur[i1];
+                    const double a2 = A[pk(j2, i2)], x2 = cur[j2], y2 = cur[i2];
+                    A[pk(j1, i1)] = fma(-x1, y1, a1);
+                    if (two) A[pk(j2, i2)] = fma(-x2, y2, a2);
+                }
             }
             __syncthreads();
         }
@@ -306,13 +316,21 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
                     nxt[j] = v;
                 }
             }
-            const int S = N - kk;
-            const int TS = (S * (S + 1)) >> 1;
-            for (int f = tid; f < TS; f += NT) {
-                int r, c;
-                tri_rc(f, r, c);
-                const int j = kk + 1 + r, i = kk + 1 + c;
-                A[pk(j, i)] = fmaf(-cur[j], cur[i], A[pk(j, i)]);
+            if (warp > 0) {
+                const int S = N - kk;
+                const int TS = (S * (S + 1)) >> 1;
+                constexpr int NU = NT - 32;
+                for (int f = tid - 32; f < TS; f += 2 * NU) {
+                    int r1, c1, r2, c2;
+                    tri_rc(f, r1, c1);
+                    const bool two = f + NU < TS;
+                    tri_rc(two ? f + NU : f, r2, c2);
+                    const int j1 = kk + 1 + r1, i1 = kk + 1 + c1, j2 = kk + 1 + r2, i2 = kk + 1 + c2;
+                    const float a1 = A[pk(j1, i1)], x1 = cur[j1], y1 = cur[i1];
+                    const float a2 = A[pk(j2, i2)], x2 = cur[j2], y2 = cur[i2];
+                    A[pk(j1, i1)] = fmaf(-x1, y1, a1);
+                    if (two) A[pk(j2, i2)] = fmaf(-x2, y2, a2);
+                }
             }
             __syncthreads();
         }
@@ -530,7 +548,7 @@ int bv_smem_max_n(int kind, int d) {
     return n;
 }
 
-int bv_max_threads_for(int kind) { return kind == 2 ? 256 : 512; }
+int bv_max_threads_for(int kind) { return kind == 2 ? 256 : 544; }
 
 cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     if (bp.nwork == 0) return cudaSuccess;
@@ -538,10 +556,11 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     a.work = bp.d_work;
     a.nwork = bp.nwork;
     switch (bp.threads) {
-        case 64: return launch_kind<64>(bp.kind, bp.grid, bp.smem, a, s);
-        case 128: return launch_kind<128>(bp.kind, bp.grid, bp.smem, a, s);
+        case 96: return launch_kind<96>(bp.kind, bp.grid, bp.smem, a, s);
+        case 160: return launch_kind<160>(bp.kind, bp.grid, bp.smem, a, s);
+        case 288: return launch_kind<288>(bp.kind, bp.grid, bp.smem, a, s);
+        case 544: return launch_kind<544>(bp.kind, bp.grid, bp.smem, a, s);
         case 256: return launch_kind<256>(bp.kind, bp.grid, bp.smem, a, s);
-        case 512: return launch_kind<512>(bp.kind, bp.grid, bp.smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -576,7 +595,7 @@ int bv_occupancy(int kind, int threads, size_t smem) {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
         }                                                                                     \
     }
-    BV_OCC(64) BV_OCC(128) BV_OCC(256) BV_OCC(512)
+    BV_OCC(96) BV_OCC(160) BV_OCC(288) BV_OCC(544) BV_OCC(256)
 #undef BV_OCC
     if (e != cudaSuccess) return 0;
     return nb;

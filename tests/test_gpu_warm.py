@@ -1,0 +1,105 @@
+"""GPU parity of the learned warm start: features against the oracle, the MLP's forward
+pass and backpropagated gradient against the FP64 oracle (relative error <= 1e-4 in
+FP32), training reduces the loss, and the trained network cuts the number of
+log-likelihood calls of the MLE while reaching the same optimum as the cold start."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import warm
+from paper_2410_04477_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bv():
+    from paper_2410_04477_gb300 import bv as _bv
+    return _bv
+
+
+def _blob(seed=0):
+    rng = np.random.default_rng(seed)
+    b = np.empty(warm.BLOB)
+    b[:warm.NFEAT] = rng.normal(size=warm.NFEAT)
+    b[warm.NFEAT:2 * warm.NFEAT] = rng.uniform(0.5, 2.0, warm.NFEAT)
+    b[2 * warm.NFEAT:2 * warm.NFEAT + 3] = rng.normal(size=3)
+    b[2 * warm.NFEAT + 3:2 * warm.NFEAT + 6] = rng.uniform(0.5, 2.0, 3)
+    b[2 * warm.NFEAT + 6:] = rng.normal(scale=0.3, size=warm.NPARAM) / 6
+    return b.astype(np.float32)
+
+
+def test_features_match_oracle(bv):
+    n = 3000
+    locs = synth.locs_uniform(n, 2, 31)
+    th = oracle.theta(1.3, 0.07, 1.5, 1e-2)
+    y = oracle.exact_draw(th, locs, synth.normal(31, 20, n))
+    bp, pi, ce = oracle.build_blocks(locs, 300, seed=3)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 40)
+    want = warm.features(locs, y, bp, nnp, max_points=1500, seed=7)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(300, seed=3)
+        ctx.select_neighbors(40)
+        got = ctx.features(max_points=1500, seed=7)[0]
+    np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-7)
+
+
+def test_mlp_forward_and_gradient_match_oracle(bv):
+    b = _blob()
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(64, warm.NFEAT)).astype(np.float32)
+    T = np.column_stack([rng.normal(size=(64, 3)), rng.choice([0.5, 1.5, 2.5], 64)]).astype(np.float32)
+    out = bv.mlp_forward(b, X)
+    np.testing.assert_allclose(out, warm.mlp_forward(b.astype(np.float64), X.astype(np.float64)),
+                               rtol=1e-4, atol=1e-5)
+    loss, g = bv.mlp_loss_grad(b, X, T)
+    lo, go = warm.mlp_loss_grad(b.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    # per layer as well (weights and biases of every layer carry gradient)
+    off = 0
+    for i, o in warm.LAYERS:
+        for sl in (slice(off, off + i * o), slice(off + i * o, off + i * o + o)):
+            assert np.linalg.norm(g[sl] - go[sl]) <= 2e-4 * max(np.linalg.norm(go[sl]), 1e-6)
+        off += i * o + o
+
+
+def test_training_reduces_loss(bv):
+    rng = np.random.default_rng(4)
+    n = 2048
+    X = rng.normal(size=(n, warm.NFEAT)).astype(np.float32)
+    A = rng.normal(size=(warm.NFEAT, 3)) / np.sqrt(warm.NFEAT)
+    T = np.column_stack([np.tanh(X @ A), np.array([0.5, 1.5, 2.5])[(X[:, 0] > 0).astype(int) + (X[:, 1] > 0.5).astype(int)]])
+    blob, losses = bv.mlp_train(X, T.astype(np.float32), epochs=40, batch=128, lr=2e-3, seed=1)
+    assert losses[-1] < 0.25 * losses[0], losses[[0, -1]]
+    # deterministic given the seed
+    blob2, losses2 = bv.mlp_train(X, T.astype(np.float32), epochs=40, batch=128, lr=2e-3, seed=1)
+    np.testing.assert_array_equal(losses, losses2)
+
+
+def test_warm_start_cuts_loglik_calls(bv):
+    wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained warm-start weights committed")
+    n = 10000
+    calls = []
+    for k, (s2, beta, tau2, nu) in enumerate([(1.6, 0.12, 3e-3, 1.5), (0.7, 0.04, 2e-2, 0.5)]):
+        locs = synth.locs_uniform(n, 2, 900 + k)
+        with bv.Context() as ctx:
+            ctx.set_data(locs)
+            ctx.build_blocks(n // 10, seed=900 + k)
+            ctx.select_neighbors(100)
+            ctx.simulate(bv.theta(s2, beta, nu, tau2), synth.normal(900 + k, 20, n))
+            cold0 = bv.theta(1.0, 0.1, nu, 1e-2)
+            lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+            th_c, ll_c, ne_c = ctx.mle(cold0, lo, hi, precision=bv.BV_FP64, ftol_rel=1e-12, xtol=1e-6)
+            ctx.warmstart_load(wpath)
+            warm0 = ctx.warmstart_predict(cold0)
+            th_w, ll_w, ne_w = ctx.mle(warm0, lo, hi, precision=bv.BV_FP64, ftol_rel=1e-12, xtol=1e-6)
+        assert abs(ll_w - ll_c) <= 1e-6 * abs(ll_c), (ll_w, ll_c)
+        calls.append((ne_c, ne_w))
+    assert sum(w for _, w in calls) < sum(c for c, _ in calls), calls

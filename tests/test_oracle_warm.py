@@ -1,0 +1,81 @@
+"""Pins for the warm-start oracle (oracle/warm.py): the backpropagated gradient against
+central finite differences, GELU's derivative, and the semivariogram of a linear field
+against its direct definition."""
+import numpy as np
+
+from oracle import warm
+
+
+def _blob(seed=0, scale=0.3):
+    rng = np.random.default_rng(seed)
+    b = np.empty(warm.BLOB)
+    b[:warm.NFEAT] = rng.normal(size=warm.NFEAT)
+    b[warm.NFEAT:2 * warm.NFEAT] = rng.uniform(0.5, 2.0, warm.NFEAT)
+    b[2 * warm.NFEAT:2 * warm.NFEAT + 3] = rng.normal(size=3)
+    b[2 * warm.NFEAT + 3:2 * warm.NFEAT + 6] = rng.uniform(0.5, 2.0, 3)
+    b[2 * warm.NFEAT + 6:] = rng.normal(scale=scale, size=warm.NPARAM) / 6
+    return b
+
+
+def _batch(seed=1, B=7):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(B, warm.NFEAT))
+    T = np.column_stack([rng.normal(size=(B, 3)), rng.choice([0.5, 1.5, 2.5], B)])
+    return X, T
+
+
+def test_gradient_matches_central_differences():
+    b = _blob()
+    X, T = _batch()
+    loss, g = warm.mlp_loss_grad(b, X, T)
+    rng = np.random.default_rng(5)
+    off = 2 * warm.NFEAT + 6
+    # sample coordinates in every layer's weights and biases
+    idx = np.concatenate([rng.choice(warm.NPARAM, 40, replace=False),
+                          [0, 5120, 5120 + 127, warm.NPARAM - 1, warm.NPARAM - 7]])
+    h = 1e-6
+    for i in idx:
+        bp, bm = b.copy(), b.copy()
+        bp[off + i] += h
+        bm[off + i] -= h
+        fd = (warm.mlp_loss_grad(bp, X, T)[0] - warm.mlp_loss_grad(bm, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_gelu_derivative():
+    x = np.linspace(-6, 6, 101)
+    h = 1e-6
+    fd = (warm._gelu(x + h) - warm._gelu(x - h)) / (2 * h)
+    np.testing.assert_allclose(warm._gelu_d(x), fd, atol=1e-8)
+
+
+def test_loss_zero_at_perfect_fit():
+    b = _blob(scale=0.0)                     # zero weights: outputs are the biases (0)
+    X, T = _batch()
+    ym, ys = b[2 * warm.NFEAT:2 * warm.NFEAT + 3], b[2 * warm.NFEAT + 3:2 * warm.NFEAT + 6]
+    T[:, :3] = ym                            # standardised targets 0 -> zero regression loss
+    loss, _ = warm.mlp_loss_grad(b, X, T)
+    assert abs(loss - np.log(3.0)) < 1e-12   # uniform logits: cross-entropy log 3
+
+
+def test_variogram_of_a_linear_field():
+    # d = 1, y = c x:  (y_i - y_j)^2 / 2 = c^2 h^2 / 2, so gamma_k is that mean per bin
+    rng = np.random.default_rng(2)
+    n = 300
+    x = np.sort(rng.random(n))[:, None]
+    c = 1.7
+    y = c * x[:, 0]
+    f = warm.features(x, y, np.array([0, 100, 300]), np.array([0, 0, 50]), max_points=10000)
+    var = np.mean((y - y.mean()) ** 2)
+    sums, cnts = np.zeros(32), np.zeros(32)
+    for i in range(n):
+        for j in range(i + 1, n):
+            h = abs(x[i, 0] - x[j, 0])
+            if 0 < h <= 0.5:
+                k = min(int(np.floor(h * 64)), 31)
+                sums[k] += 0.5 * (c * h) ** 2
+                cnts[k] += 1
+    want = np.where(cnts > 0, sums / np.maximum(cnts, 1) / var, 0.0)
+    np.testing.assert_allclose(f[:32], want, rtol=1e-12)
+    assert f[33] == 150 and f[35] == 100 and f[36] == 200 and f[37] == 25
+    assert abs(f[38] - np.log(n)) < 1e-15 and f[39] == 1
