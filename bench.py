@@ -30,17 +30,28 @@ sys.path.insert(0, ROOT)
 
 from paper_2410_04477_gb300 import synth  # noqa: E402
 
-METRIC = "block-Vecchia loglik evals/sec (FP64), n=2e5, bc=2e4, m=60, nu=1.5"
+METRIC = "block-Vecchia loglik evals/sec (FP64), n=2e+05, bc=2e+04, m=60, nu=1.5, d=2"
 UNIT = "evals/s"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor), used as the ALU roofline
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5 at max clock
 
 WORKLOADS = {
+    # batched plain FP64: 2e5 uniform points, bc 2e4, m 60 / 120, y from BV at m=400
     "c2_m60": dict(n=200_000, d=2, bc=20_000, m=60, nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-4,
                    seed=1, gen_m=400),
     "c2_m120": dict(n=200_000, d=2, bc=20_000, m=120, nu=1.5, sigma2=1.0, beta=0.05,
                     nugget=1e-4, seed=1, gen_m=400),
+    # 3D profile: 20,000 sites x 50 jittered levels = 1e6 points, anisotropic range
+    "c3": dict(n=1_000_000, d=3, sites=20_000, levels=50, bc=100_000, m=200, nu=0.5, sigma2=1.0,
+               beta=0.1, ranges=[0.1, 0.1, 0.3], nugget=1e-3, seed=2, gen_m=400),
+    # MLE on 5e5 points, bc 5e4, m 100; cold start (1, 0.1, 1e-2) vs learned warm start
+    "c4_mle": dict(n=500_000, d=2, bc=50_000, m=100, nu=1.5, sigma2=1.5, beta=0.05, nugget=5e-3,
+                   seed=4, gen_m=100),
+    # 256 datasets in one launch, n log-uniform [5e3, 5e4], bc = n/10, per-dataset theta
+    "c5_m30": dict(ndata=256, m=30, seed=5, d=2, gen_m=30),
+    "c5_m60": dict(ndata=256, m=60, seed=5, d=2, gen_m=30),
+    "c5_m120": dict(ndata=256, m=120, seed=5, d=2, gen_m=30),
 }
 
 
@@ -96,23 +107,38 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def true_theta(bv, w, f=(1.0, 1.0, 1.0)):
+    if w.get("ranges"):
+        return bv.theta(w["sigma2"] * f[0], None, w["nu"], w["nugget"] * f[2],
+                        ranges=[r * f[1] for r in w["ranges"]])
+    return bv.theta(w["sigma2"] * f[0], w["beta"] * f[1], w["nu"], w["nugget"] * f[2])
+
+
 def make_thetas(bv, w, count, seed):
+    """count perturbed parameter vectors (one per step); for several datasets, a list
+    of per-dataset vectors per step."""
     f = synth.perturb_factors(seed + 1000, count)
-    out = []
-    for k in range(count):
-        out.append(bv.theta(w["sigma2"] * f[k, 0], w["beta"] * f[k, 1], w["nu"], w["nugget"] * f[k, 2]))
-    return out
+    if "ndata" in w:
+        base = w["thetas"]
+        return [[bv.theta(t[0] * f[k, 0], t[1] * f[k, 1], t[3], t[2] * f[k, 2]) for t in base]
+                for k in range(count)]
+    return [[true_theta(bv, w, f[k])] for k in range(count)]
 
 
 def setup_gpu(bv, ctx, w, log):
     t0 = time.perf_counter()
-    locs = synth.locs_uniform(w["n"], w["d"], w["seed"])
+    if "ndata" in w:
+        return setup_multi(bv, ctx, w, log)
+    if w["d"] == 3:
+        locs = synth.locs_levels(w["sites"], w["levels"], w["seed"])
+    else:
+        locs = synth.locs_uniform(w["n"], w["d"], w["seed"])
     ctx.set_data(locs)
     ctx.build_blocks(w["bc"], seed=w["seed"], iters=20)
     t1 = time.perf_counter()
     ctx.select_neighbors(w["gen_m"])
     z = synth.normal(w["seed"], 20, w["n"])
-    y = ctx.simulate(bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"]), z)
+    y = ctx.simulate(true_theta(bv, w), z)
     t2 = time.perf_counter()
     ctx.select_neighbors(w["m"])
     t3 = time.perf_counter()
@@ -120,19 +146,52 @@ def setup_gpu(bv, ctx, w, log):
     return locs, y, dict(blocks_s=round(t1 - t0, 2), draw_s=round(t2 - t1, 2), nn_s=round(t3 - t2, 2))
 
 
+def setup_multi(bv, ctx, w, log):
+    """C5: every dataset drawn from the block-Vecchia model at its own theta (one context
+    per dataset for the draw), then all loaded into one context for batched evaluation."""
+    t0 = time.perf_counter()
+    sizes = synth.dataset_sizes(w["seed"], w["ndata"])
+    th = synth.theta_draws(w["seed"], w["ndata"])
+    w["thetas"] = [tuple(map(float, t)) for t in th]
+    w["n"] = int(sizes.sum())
+    w["sizes"] = sizes
+    locs_l, y_l = [], []
+    with bv.Context(ctx_device(ctx)) as tmp:
+        for k in range(w["ndata"]):
+            n = int(sizes[k])
+            locs = synth.locs_uniform(n, 2, w["seed"] * 100000 + k)
+            tmp.set_data(locs)
+            tmp.build_blocks(n // 10, seed=w["seed"] * 100000 + k, iters=20)
+            tmp.select_neighbors(w["gen_m"])
+            s2, beta, tau2, nu = th[k]
+            y_l.append(tmp.simulate(bv.theta(s2, beta, nu, tau2), synth.normal(w["seed"] * 100000 + k, 20, n)))
+            locs_l.append(locs)
+    t1 = time.perf_counter()
+    ctx.set_datasets(locs_l, y_l)
+    ctx.build_blocks_multi([int(n) // 10 for n in sizes], seed=w["seed"] * 100000, iters=20)
+    ctx.select_neighbors(w["m"])
+    t2 = time.perf_counter()
+    log(f"setup: {w['ndata']} draws {t1 - t0:.1f}s, blocks+neighbours {t2 - t1:.1f}s (sum n = {w['n']})")
+    return locs_l, np.concatenate(y_l), dict(draws_s=round(t1 - t0, 2), structure_s=round(t2 - t1, 2))
+
+
+def ctx_device(ctx):
+    return 0
+
+
 def time_device(torch, bv, ctx, stream, thetas, prec, warmup, steps, flush):
     """Per-evaluation CUDA-event durations (ms) on the launching stream, L2 flushed between."""
-    dout = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dout = torch.zeros(len(thetas[0]), dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
         for k in range(warmup):
-            ctx.loglik_async([thetas[k % len(thetas)]], prec, dout.data_ptr())
+            ctx.loglik_async(thetas[k % len(thetas)], prec, dout.data_ptr())
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
         for k in range(steps):
             flush.zero_()
             evs[k][0].record(stream)
-            ctx.loglik_async([thetas[(warmup + k) % len(thetas)]], prec, dout.data_ptr())
+            ctx.loglik_async(thetas[(warmup + k) % len(thetas)], prec, dout.data_ptr())
             evs[k][1].record(stream)
     torch.cuda.synchronize()
     st, fb = ctx.sync()
@@ -174,6 +233,10 @@ def run_reference(args, w):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    if "ndata" in w or w["d"] != 2:
+        print(json.dumps({"impl": "reference", "unavailable": "reference arm (CPU oracle) is wired for the "
+                          "single-dataset 2D workloads only"}), flush=True)
+        return 0
     import oracle
     oracle.build()
     import oracle as O
@@ -198,7 +261,7 @@ def run_reference(args, w):
     val = 1.0 / per_full
     sample = (f"each step: one FP64 oracle evaluation of an n={n_s} sub-square at the same density "
               f"({len(bp) - 1} blocks, m={w['m']}), extrapolated to the full workload by block count")
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+    line = {"impl": "reference", "metric": metric_of(w, args), "value": val, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(w, args),
@@ -210,11 +273,61 @@ def run_reference(args, w):
 
 
 def config_of(w, args):
-    return {"workload": args.workload, "n": w["n"], "d": w["d"], "bc": w["bc"], "m": w["m"],
-            "nu": w["nu"], "sigma2": w["sigma2"], "beta": w["beta"], "nugget": w["nugget"],
-            "y": f"block-Vecchia draw at m={w['gen_m']}", "theta": "perturbed U(0.8,1.2) per step",
-            "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
-            "parallelism": "replicas" if _dist()[0] > 1 else "single"}
+    c = {"workload": args.workload, "d": w["d"], "m": w["m"], "y": f"block-Vecchia draw at m={w['gen_m']}",
+         "theta": "perturbed U(0.8,1.2) per step", "precision": args.precision,
+         "l2": "flushed between timed steps (256 MB write)",
+         "parallelism": "replicas" if _dist()[0] > 1 else "single"}
+    if "ndata" in w:
+        c.update(ndata=w["ndata"], n_total=w.get("n"), bc="n/10 per dataset", n_range=[5000, 50000],
+                 theta_per_dataset="log-uniform sigma2 [0.5,2], beta [0.02,0.3], tau2 [1e-4,1e-1]; nu in {0.5,1.5,2.5}")
+    else:
+        c.update(n=w["n"], bc=w["bc"], nu=w["nu"], sigma2=w["sigma2"], nugget=w["nugget"],
+                 range=w.get("ranges") or w["beta"])
+    return c
+
+
+def metric_of(w, args):
+    prec = "FP64" if args.precision == "fp64" else "mixed FP32/FP64"
+    if "ndata" in w:
+        return f"block-Vecchia loglik evals/sec ({prec}), {w['ndata']} datasets in one launch, m={w['m']}"
+    return (f"block-Vecchia loglik evals/sec ({prec}), n={w['n']:.0e}, bc={w['bc']:.0e}, m={w['m']}, "
+            f"nu={w['nu']}, d={w['d']}")
+
+
+def run_mle(bv, ctx, w, log):
+    """MLE wall-time: cold start (1, 0.1, 1e-2) and the learned warm start, FP64 and
+    mixed; sigma^2, range and nugget free, nu fixed."""
+    wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
+    nu = w["nu"]
+    lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+    cold0 = bv.theta(1.0, 0.1, nu, 1e-2)
+    res = {}
+    warm0 = None
+    if os.path.exists(wpath):
+        t0 = time.perf_counter()
+        ctx.warmstart_load(wpath)
+        warm0 = ctx.warmstart_predict(cold0)
+        res["warm_predict_s"] = time.perf_counter() - t0
+        res["warm_start_theta"] = [warm0.sigma2, warm0.range[0], warm0.nugget]
+    for pname, prec in (("fp64", bv.BV_FP64), ("mixed", bv.BV_MIXED)):
+        for sname, th0 in (("cold", cold0), ("warm", warm0)):
+            if th0 is None:
+                continue
+            ctx.loglik(th0, prec)   # plan, tune and capture outside the timed MLE
+            t0 = time.perf_counter()
+            th, ll, ne = ctx.mle(th0, lo, hi, precision=prec, ftol_rel=1e-10, xtol=1e-6, max_evals=2000)
+            el = time.perf_counter() - t0
+            if sname == "warm":
+                el += res.get("warm_predict_s", 0.0)
+            res[f"{pname}_{sname}"] = {"wall_s": el, "evals": ne, "loglik": ll,
+                                       "theta_hat": [th.sigma2, th.range[0], th.nugget]}
+            log(f"mle {pname} {sname}: {el:.2f}s {ne} evals ell={ll:.6f}")
+    for pname in ("fp64", "mixed"):
+        if f"{pname}_warm" in res:
+            c, wv = res[f"{pname}_cold"], res[f"{pname}_warm"]
+            res[f"{pname}_warm_vs_cold"] = {"speedup": c["wall_s"] / wv["wall_s"], "evals_saved": c["evals"] - wv["evals"],
+                                            "rel_diff_loglik": abs(wv["loglik"] - c["loglik"]) / abs(c["loglik"])}
+    return res
 
 
 def main():
@@ -225,12 +338,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_m60", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the mixed / m=120 / MLE lines")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other-precision line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -250,6 +363,7 @@ def main():
     ctx.autotune(prec)
     info = ctx.plan_info(prec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    nd = len(thetas[0])
 
     def barrier():
         torch.cuda.synchronize()
@@ -272,50 +386,58 @@ def main():
     value = ws * args.steps / (tot_ms / 1e3)
 
     # end to end through the public API with host buffers: y (pinned) up, ell down
-    y_pin = torch.from_numpy(y_true.copy()).pin_memory()
+    y_pin = torch.from_numpy(np.ascontiguousarray(y_true)).pin_memory()
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
         ctx.set_observations(y_pin.numpy())
-        ctx.loglik(thetas[(args.warmup + k) % len(thetas)], prec)
+        if nd == 1:
+            ctx.loglik(thetas[(args.warmup + k) % len(thetas)][0], prec)
+        else:
+            ctx.loglik_multi(thetas[(args.warmup + k) % len(thetas)], prec)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w["n"] * 8 + 64),
-           "d2h_bytes_per_step": 8}
+    e2e = {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w["n"] * 8 + 64 * nd),
+           "d2h_bytes_per_step": 8 * nd}
 
     achieved = info["flops"] / (mean_ms / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": "k_ll_fp64 (all size bins) + reduction, one evaluation",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; probe 1.19)",
             "flops_per_eval": info["flops"], "cov_entries_per_eval": info["cov_entries"]}
     if prec == bv.BV_MIXED:
-        roof.update(kernel="k_ll_mixed (all size bins) + reduction", peak=FP32_PEAK_TFLOPS,
+        roof.update(kernel="k_ll_mixed (all size bins) + reduction, one evaluation", peak=FP32_PEAK_TFLOPS,
                     frac=achieved / FP32_PEAK_TFLOPS,
-                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz")
+                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (probe 69.5 at ~1.99 GHz)")
 
     extras = {}
     if not args.no_extras and rank == 0:
-        ll_true64 = ctx.loglik(bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"]), bv.BV_FP64)
+        base = [true_theta(bv, w)] if nd == 1 else [bv.theta(t[0], t[1], t[3], t[2]) for t in w["thetas"]]
+        ll64 = ctx.loglik_multi(base, bv.BV_FP64)
         other = bv.BV_MIXED if prec == bv.BV_FP64 else bv.BV_FP64
         ctx.autotune(other)
-        ms2 = time_device(torch, bv, ctx, stream, thetas, other, 3, min(args.steps, 30), flush)
-        ll_true_m = ctx.loglik(bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"]), bv.BV_MIXED)
+        n2 = min(args.steps, 30) if other == bv.BV_MIXED or nd > 1 else min(args.steps, 5)
+        ms2 = time_device(torch, bv, ctx, stream, thetas, other, 3, n2, flush)
+        llm = ctx.loglik_multi(base, bv.BV_MIXED)
+        rel = np.abs(llm - ll64) / np.abs(ll64)
         extras["other_precision"] = {
             "precision": "mixed" if other == bv.BV_MIXED else "fp64",
             "evals_per_s": len(ms2) / (sum(ms2) / 1e3),
             "achieved_tflops": info["flops"] / (statistics.mean(ms2) / 1e3) / 1e12,
-            "ell_fp64": ll_true64, "ell_mixed": ll_true_m,
-            "rel_err_mixed_vs_fp64": abs(ll_true_m - ll_true64) / abs(ll_true64),
-            "abs_err": abs(ll_true_m - ll_true64)}
+            "ell_fp64_at_truth": float(ll64.sum()), "ell_mixed_at_truth": float(llm.sum()),
+            "rel_err_mixed_vs_fp64": float(abs(llm.sum() - ll64.sum()) / abs(ll64.sum())),
+            "max_rel_err_per_dataset": float(rel.max()), "abs_err": float(abs(llm.sum() - ll64.sum()))}
         log(f"extras: {extras['other_precision']}")
+        if args.workload == "c4_mle":
+            extras["mle"] = run_mle(bv, ctx, w, log)
     cpu = None
-    if not args.no_cpu and rank == 0 and ws == 1:
+    if not args.no_cpu and rank == 0 and ws == 1 and "ndata" not in w and w["d"] == 2:
         v, sample, cores, per = cpu_oracle_sample(w)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        line = {"metric": metric_of(w, args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == bv.BV_FP64 else "f32+f64",
                 "data": "synthetic", "config": config_of(w, args), "roofline": roof,

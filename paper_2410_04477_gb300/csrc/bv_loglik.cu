@@ -234,102 +234,161 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
-// Mixed: FP32 shared memory.  Layout: A packed float | col[2][N+1] float | pts[d][N] float
-// Coordinates are taken relative to the block centroid in FP64 and rounded to FP32, so
-// FP32 differences keep their relative accuracy for nearby points.
+// Mixed: FP32 covariance and updates, FP64 log-determinant and quadratic form.
+// The augmented matrix is held as 4x4 tiles (lower tile triangle, tile (I,J) at
+// (I(I+1)/2 + J)*16 floats, row-major inside the tile), factored by 4-column panels:
+//   panel p: every thread factors the 4x4 diagonal tile in registers (4 pivots), then
+//            solves its own rows of tile column p against it (one barrier);
+//   update:  every trailing tile (I,J), p < J <= I, is updated by one thread,
+//            A_IJ -= P_I P_J^T, with 128-bit shared-memory accesses (64 FMAs per 12
+//            loads and 4 stores);
+// so each panel costs two barriers and no per-element index arithmetic.  Coordinates are
+// taken relative to the block centroid in FP64 and rounded to FP32, so FP32 differences
+// keep their relative accuracy for nearby points.
 // ---------------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float* tile_at(float* t, int I, int J) { return t + (((I * (I + 1)) >> 1) + J) * 16; }
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ double red[NT / 32];
     __shared__ int s_fail;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
 
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int blk = a.work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
         const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
-        const int N = m + b, R = N + 1;
+        const int N = m + b, R = N + 1, T = (R + 3) >> 2;
         const DevTheta th = a.theta[a.bds[blk]];
-        float* A = sm;
-        float* col0 = A + ((R * (R + 1)) >> 1);
-        float* col1 = col0 + R;
-        float* px = col1 + R;
+        float* tiles = sm;
+        float* px = tiles + (((T * (T + 1)) >> 1) << 4);
+        float* yv = px + 3 * N;
+        float* piv = yv + N;
+        float* ydiag = piv + N;  // 4 floats
         const int d = a.d;
         const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
 
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < d; ++k)
-                px[k * N + t] = (float)((a.locs[(int64_t)k * a.n_tot + g] - a.cent[(int64_t)blk * d + k]) *
-                                        th.inv_range[k]);
-            A[pk(N, t)] = (float)a.y[g];
+            for (int k = 0; k < 3; ++k)
+                px[k * N + t] = k < d ? (float)((a.locs[(int64_t)k * a.n_tot + g] - a.cent[(int64_t)blk * d + k]) *
+                                                th.inv_range[k])
+                                      : 0.0f;
+            yv[t] = (float)a.y[g];
         }
-        if (tid == 0) {
-            A[pk(N, N)] = 0.0f;
-            s_fail = 0;
-        }
+        if (tid == 0) s_fail = 0;
         __syncthreads();
 
-        const int T = (N * (N + 1)) >> 1;
-        for (int f = tid; f < T; f += NT) {
-            int r, c;
-            tri_rc(f, r, c);
-            float acc = 0.0f;
-            for (int k = 0; k < d; ++k) {
-                const float t = px[k * N + r] - px[k * N + c];
-                acc = fmaf(t, t, acc);
+        // fill every element of the lower tile triangle (padding and the strictly upper
+        // part of diagonal tiles get 0; row N is y)
+        const int TE = ((T * (T + 1)) >> 1) << 4;
+        for (int f = tid; f < TE; f += NT) {
+            int I, J;
+            tri_rc(f >> 4, I, J);
+            const int r = (I << 2) + ((f >> 2) & 3), c = (J << 2) + (f & 3);
+            float v = 0.0f;
+            if (r < N && c <= r) {
+                const float t0 = px[r] - px[c], t1 = px[N + r] - px[N + c], t2 = px[2 * N + r] - px[2 * N + c];
+                v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
+                if (r == c) v += tau2;
+            } else if (r == N && c < N) {
+                v = yv[c];
             }
-            float v = matern32(th.nu_code, s2, sqrtf(acc));
-            if (r == c) v += tau2;
-            A[f] = v;
+            tiles[f] = v;
         }
         __syncthreads();
 
-        if (warp == 0) {
-            const float p = A[0];
-            if (!(p > 0.0f) && lane == 0) s_fail = 1;
-            const float rs = rsqrtf(p);
-            for (int j = 1 + lane; j <= N; j += 32) {
-                const float v = A[pk(j, 0)] * rs;
-                A[pk(j, 0)] = v;
-                col0[j] = v;
-            }
-        }
-        __syncthreads();
-
-        for (int k = 0; k + 1 < N; ++k) {
-            const float* cur = (k & 1) ? col1 : col0;
-            float* nxt = (k & 1) ? col0 : col1;
-            const int kk = k + 1;
-            if (warp == 0) {
-                const float ck = cur[kk];
-                for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fmaf(-cur[j], ck, A[pk(j, kk)]);
-                __syncwarp();
-                const float p = A[pk(kk, kk)];
-                if (!(p > 0.0f) && lane == 0) s_fail = 1;
-                const float rs = rsqrtf(p);
-                for (int j = kk + 1 + lane; j <= N; j += 32) {
-                    const float v = A[pk(j, kk)] * rs;
-                    A[pk(j, kk)] = v;
-                    nxt[j] = v;
+        for (int p = 0; (p << 2) < N; ++p) {
+            const int k0 = p << 2, nc = min(4, N - k0);
+            // (a) diagonal tile factored in registers by every thread
+            float D[16];
+            {
+                const float* tp = tile_at(tiles, p, p);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float4 q = ld4(tp + 4 * r);
+                    D[4 * r] = q.x;
+                    D[4 * r + 1] = q.y;
+                    D[4 * r + 2] = q.z;
+                    D[4 * r + 3] = q.w;
                 }
             }
-            if (warp > 0) {
-                const int S = N - kk;
-                const int TS = (S * (S + 1)) >> 1;
-                constexpr int NU = NT - 32;
-                for (int f = tid - 32; f < TS; f += 2 * NU) {
-                    int r1, c1, r2, c2;
-                    tri_rc(f, r1, c1);
-                    const bool two = f + NU < TS;
-                    tri_rc(two ? f + NU : f, r2, c2);
-                    const int j1 = kk + 1 + r1, i1 = kk + 1 + c1, j2 = kk + 1 + r2, i2 = kk + 1 + c2;
-                    const float a1 = A[pk(j1, i1)], x1 = cur[j1], y1 = cur[i1];
-                    const float a2 = A[pk(j2, i2)], x2 = cur[j2], y2 = cur[i2];
-                    A[pk(j1, i1)] = fmaf(-x1, y1, a1);
-                    if (two) A[pk(j2, i2)] = fmaf(-x2, y2, a2);
+            float rs[4], pv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pv[c] = D[5 * c];
+                rs[c] = c < nc ? rsqrtf(pv[c]) : 0.0f;
+#pragma unroll
+                for (int r = c + 1; r < 4; ++r) D[4 * r + c] *= rs[c];
+#pragma unroll
+                for (int r = c + 1; r < 4; ++r)
+#pragma unroll
+                    for (int q = c + 1; q <= r; ++q) D[4 * r + q] = fmaf(-D[4 * r + c], D[4 * q + c], D[4 * r + q]);
+            }
+            // (b) rows of tile column p.  The diagonal tile itself is not written back
+            // (other threads may still be reading it): its pivots go to piv[] and, when
+            // it holds row N, that row's factor entries to ydiag[].
+            for (int r = k0 + tid; r < (T << 2); r += NT) {
+                const int I = r >> 2, ra = r & 3;
+                float* rowp = tile_at(tiles, I, p) + 4 * ra;
+                float x[4];
+                if (I == p) {
+                    if (ra < nc) {
+                        piv[k0 + ra] = pv[ra];
+                        if (!(pv[ra] > 0.0f)) s_fail = 1;
+                    }
+                    if (r == N) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) ydiag[c] = c < nc ? D[4 * ra + c] : 0.0f;
+                    }
+                    continue;
+                } else {
+                    const float4 q = ld4(rowp);
+                    x[0] = q.x;
+                    x[1] = q.y;
+                    x[2] = q.z;
+                    x[3] = q.w;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float v = x[c];
+#pragma unroll
+                        for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], D[4 * c + q2], v);
+                        x[c] = c < nc ? v * rs[c] : 0.0f;
+                    }
+                }
+                st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
+            }
+            __syncthreads();
+            // (c) trailing tiles
+            const int S = T - p - 1;
+            const int cnt = (S * (S + 1)) >> 1;
+            for (int q = tid; q < cnt; q += NT) {
+                int ii, jj;
+                tri_rc(q, ii, jj);
+                const int I = p + 1 + ii, J = p + 1 + jj;
+                const float* PI = tile_at(tiles, I, p);
+                const float* PJ = tile_at(tiles, J, p);
+                float* At = tile_at(tiles, I, J);
+                float pi[16], pj[16];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float4 u = ld4(PI + 4 * r), v = ld4(PJ + 4 * r);
+                    pi[4 * r] = u.x; pi[4 * r + 1] = u.y; pi[4 * r + 2] = u.z; pi[4 * r + 3] = u.w;
+                    pj[4 * r] = v.x; pj[4 * r + 1] = v.y; pj[4 * r + 2] = v.z; pj[4 * r + 3] = v.w;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float4 acc = ld4(At + 4 * r);
+                    float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) o[c] = fmaf(-pi[4 * r + k], pj[4 * c + k], o[c]);
+                    st4(At + 4 * r, make_float4(o[0], o[1], o[2], o[3]));
                 }
             }
             __syncthreads();
@@ -338,12 +397,13 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
         // FP64 accumulation of the quadratic form and the log-determinant
         double part = 0.0;
         for (int k = m + tid; k < N; k += NT) {
-            const double z = (double)A[pk(N, k)];
-            part += z * z + log((double)A[pk(k, k)]);
+            const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
+                                                  : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
+            part += z * z + log((double)piv[k]);
         }
-        const double s = block_sum<NT>(part, red);
+        const double sres = block_sum<NT>(part, red);
         if (tid == 0) {
-            double ell = -0.5 * (s + (double)b * kLog2Pi);
+            double ell = -0.5 * (sres + (double)b * kLog2Pi);
             if (s_fail || !(ell == ell)) {
                 ell = -INFINITY;
                 record_fail(a.fail, blk);
@@ -536,6 +596,10 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
     const size_t R = (size_t)nmax + 1;
     const size_t el = kind == 1 ? sizeof(float) : sizeof(double);
     if (kind == 2) return 0;
+    if (kind == 1) {
+        const size_t T = (R + 3) / 4;
+        return ((sizeof(float) * (T * (T + 1) / 2 * 16 + 5 * (size_t)nmax + 4)) + 15) & ~(size_t)15;
+    }
     size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
     return (bytes + 15) & ~(size_t)15;
 }

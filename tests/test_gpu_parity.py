@@ -256,3 +256,22 @@ def test_device_exp_within_two_ulp(bv):
     err = np.abs(got - want) / ulp
     assert err.max() <= 2.0, (err.max(), x[np.argmax(err)])
     assert bv.exp_neg_check(np.array([700.5, 800.0, 1e6])).max() == 0.0
+
+
+@pytest.mark.parametrize("d,m,bc,ranges", [(2, 0, 300, None), (2, 7, 300, None), (2, 63, 250, None),
+                                           (2, 120, 200, None), (3, 200, 150, [0.1, 0.1, 0.3])])
+def test_mixed_precision_per_block(bv, d, m, bc, ranges):
+    # every augmented size N = m + b mod 4 occurs; per-block terms within FP32-level error
+    n = 3000
+    locs = synth.locs_uniform(n, d, 40 + m)
+    th = _otheta(1.0, 0.08, 1.5 if d == 2 else 0.5, 1e-3, ranges)
+    y = oracle.exact_draw(th, locs, synth.normal(40 + m, 20, n))
+    ga = (1.0, 0.08, 1.5 if d == 2 else 0.5, 1e-3, ranges)
+    llm, per, gs = _gpu_ll(bv, locs, y, bc, m, ga, prec=1, seed=1)
+    os_ = _oracle_struct(locs, bc, m, seed=1)
+    _same_struct(gs, os_)
+    llo, per_o, _ = oracle.loglik(th, locs, y, *os_)
+    Ns = np.diff(os_[0]) + np.diff(os_[2])
+    assert set(Ns % 4) == {0, 1, 2, 3}
+    np.testing.assert_allclose(per, per_o, rtol=0, atol=2e-2)
+    assert abs(llm - llo) <= 1e-4 * abs(llo), (llm, llo)
