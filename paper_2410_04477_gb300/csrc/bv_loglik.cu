@@ -235,26 +235,78 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
 
 // ---------------------------------------------------------------------------------
 // Mixed: FP32 covariance and updates, FP64 log-determinant and quadratic form.
-// The augmented matrix is held as 4x4 tiles (lower tile triangle, tile (I,J) at
-// (I(I+1)/2 + J)*16 floats, row-major inside the tile), factored by 4-column panels:
-//   panel p: every thread factors the 4x4 diagonal tile in registers (4 pivots), then
-//            solves its own rows of tile column p against it (one barrier);
-//   update:  every trailing tile (I,J), p < J <= I, is updated by one thread,
-//            A_IJ -= P_I P_J^T, with 128-bit shared-memory accesses (64 FMAs per 12
-//            loads and 4 stores);
-// so each panel costs two barriers and no per-element index arithmetic.  Coordinates are
-// taken relative to the block centroid in FP64 and rounded to FP32, so FP32 differences
-// keep their relative accuracy for nearby points.
+// The augmented matrix is held as 4x4 tiles (lower tile triangle; tile (I,J) starts at
+// (I(I+1)/2 + J) * kTS floats, row-major inside the tile; kTS = 20 pads each tile to 80
+// bytes so that eight consecutive tiles fall on distinct 16-byte bank groups), factored
+// by 4-column panels:
+//   panel p:  every thread solves its rows of tile column p against the factored 4x4
+//             diagonal tile (read from `dfac`, one barrier);
+//   update:   every trailing tile (I,J), p < J <= I, is updated by one thread,
+//             A_IJ -= P_I P_J^T with 128-bit shared-memory accesses; the thread that
+//             updates the next diagonal tile (always thread 0) factors it at once into
+//             `dfac` (look-ahead), so the pivots never sit on every thread's path.
+// Coordinates are taken relative to the block centroid in FP64 and rounded to FP32, so
+// FP32 differences keep their relative accuracy for nearby points.
 // ---------------------------------------------------------------------------------
+constexpr int kTS = 20;  // floats per stored 4x4 tile (16 + 4 padding)
+
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ float* tile_at(float* t, int I, int J) { return t + (((I * (I + 1)) >> 1) + J) * 16; }
+__device__ __forceinline__ float* tile_at(float* t, int I, int J) { return t + (((I * (I + 1)) >> 1) + J) * kTS; }
+
+// Factor the 4x4 diagonal tile at `tp` (pivot columns c < nc) into dfac:
+// dfac[0..15] = L (strictly lower part), dfac[16..19] = 1/sqrt(pivot), dfac[20..23] = pivot.
+// Writes the pivots of global columns k0.. to piv, row N's entries (if row N lies in this
+// tile) to ydiag, and raises *fail on a non-positive pivot.
+__device__ __forceinline__ void factor_diag(const float* tp, int nc, int k0, int N, float* dfac, float* piv,
+                                            float* ydiag, int* fail) {
+    float D[16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float4 q = ld4(tp + 4 * r);
+        D[4 * r] = q.x;
+        D[4 * r + 1] = q.y;
+        D[4 * r + 2] = q.z;
+        D[4 * r + 3] = q.w;
+    }
+    float rs[4], pv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        pv[c] = D[5 * c];
+        rs[c] = c < nc ? rsqrtf(pv[c]) : 0.0f;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) D[4 * r + c] *= rs[c];
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r)
+#pragma unroll
+            for (int q = c + 1; q <= r; ++q) D[4 * r + q] = fmaf(-D[4 * r + c], D[4 * q + c], D[4 * r + q]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) st4(dfac + 4 * r, make_float4(D[4 * r], D[4 * r + 1], D[4 * r + 2], D[4 * r + 3]));
+    st4(dfac + 16, make_float4(rs[0], rs[1], rs[2], rs[3]));
+    st4(dfac + 20, make_float4(pv[0], pv[1], pv[2], pv[3]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (c < nc) {
+            piv[k0 + c] = pv[c];
+            if (!(pv[c] > 0.0f)) *fail = 1;
+        }
+    const int ra = N - k0;  // row N inside this tile?
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (r == ra) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ydiag[c] = (c < nc && c < r) ? D[4 * r + c] : 0.0f;
+        }
+}
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ double red[NT / 32];
+    __shared__ __align__(16) float dfac[24];
+    __shared__ __align__(16) float ydiag[4];
     __shared__ int s_fail;
     const int tid = threadIdx.x;
 
@@ -265,105 +317,104 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
         const int N = m + b, R = N + 1, T = (R + 3) >> 2;
         const DevTheta th = a.theta[a.bds[blk]];
         float* tiles = sm;
-        float* px = tiles + (((T * (T + 1)) >> 1) << 4);
+        float* px = tiles + ((T * (T + 1)) >> 1) * kTS;
         float* yv = px + 3 * N;
         float* piv = yv + N;
-        float* ydiag = piv + N;  // 4 floats
         const int d = a.d;
         const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
+        const double ir0 = th.inv_range[0], ir1 = th.inv_range[1], ir2 = th.inv_range[2];
 
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < 3; ++k)
-                px[k * N + t] = k < d ? (float)((a.locs[(int64_t)k * a.n_tot + g] - a.cent[(int64_t)blk * d + k]) *
-                                                th.inv_range[k])
-                                      : 0.0f;
+            const double* cb = a.cent + (int64_t)blk * d;
+            px[t] = (float)((a.locs[g] - cb[0]) * ir0);
+            px[N + t] = d > 1 ? (float)((a.locs[a.n_tot + g] - cb[1]) * ir1) : 0.0f;
+            px[2 * N + t] = d > 2 ? (float)((a.locs[2 * a.n_tot + g] - cb[2]) * ir2) : 0.0f;
             yv[t] = (float)a.y[g];
         }
         if (tid == 0) s_fail = 0;
         __syncthreads();
 
-        // fill every element of the lower tile triangle (padding and the strictly upper
-        // part of diagonal tiles get 0; row N is y)
-        const int TE = ((T * (T + 1)) >> 1) << 4;
-        for (int f = tid; f < TE; f += NT) {
+        // fill: one 4x4 tile per thread (padding rows/columns and the strictly upper part
+        // of diagonal tiles get 0; row N is y)
+        const int NTL = (T * (T + 1)) >> 1;
+        for (int q = tid; q < NTL; q += NT) {
             int I, J;
-            tri_rc(f >> 4, I, J);
-            const int r = (I << 2) + ((f >> 2) & 3), c = (J << 2) + (f & 3);
-            float v = 0.0f;
-            if (r < N && c <= r) {
-                const float t0 = px[r] - px[c], t1 = px[N + r] - px[N + c], t2 = px[2 * N + r] - px[2 * N + c];
-                v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
-                if (r == c) v += tau2;
-            } else if (r == N && c < N) {
-                v = yv[c];
+            tri_rc(q, I, J);
+            float* tp = tiles + q * kTS;
+            float cx[4], cy[4], cz[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = (J << 2) + e;
+                const bool ok = c < N;
+                cx[e] = ok ? px[c] : 0.0f;
+                cy[e] = ok ? px[N + c] : 0.0f;
+                cz[e] = ok ? px[2 * N + c] : 0.0f;
             }
-            tiles[f] = v;
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int r = (I << 2) + rr;
+                float o[4];
+                if (r < N) {
+                    const float rx = px[r], ry = px[N + r], rz = px[2 * N + r];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = (J << 2) + e;
+                        const float t0 = rx - cx[e], t1 = ry - cy[e], t2 = rz - cz[e];
+                        float v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
+                        if (r == c) v += tau2;
+                        o[e] = c <= r ? v : 0.0f;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = (J << 2) + e;
+                        o[e] = (r == N && c < N) ? yv[c] : 0.0f;
+                    }
+                }
+                st4(tp + 4 * rr, make_float4(o[0], o[1], o[2], o[3]));
+            }
         }
+        __syncthreads();
+        if (tid == 0) factor_diag(tiles, min(4, N), 0, N, dfac, piv, ydiag, &s_fail);
         __syncthreads();
 
         for (int p = 0; (p << 2) < N; ++p) {
             const int k0 = p << 2, nc = min(4, N - k0);
-            // (a) diagonal tile factored in registers by every thread
-            float D[16];
+            // (a) rows of tile column p below the diagonal tile
             {
-                const float* tp = tile_at(tiles, p, p);
+                float L[16], rs[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const float4 q = ld4(tp + 4 * r);
-                    D[4 * r] = q.x;
-                    D[4 * r + 1] = q.y;
-                    D[4 * r + 2] = q.z;
-                    D[4 * r + 3] = q.w;
+                    const float4 q = ld4(dfac + 4 * r);
+                    L[4 * r] = q.x;
+                    L[4 * r + 1] = q.y;
+                    L[4 * r + 2] = q.z;
+                    L[4 * r + 3] = q.w;
                 }
-            }
-            float rs[4], pv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                pv[c] = D[5 * c];
-                rs[c] = c < nc ? rsqrtf(pv[c]) : 0.0f;
-#pragma unroll
-                for (int r = c + 1; r < 4; ++r) D[4 * r + c] *= rs[c];
-#pragma unroll
-                for (int r = c + 1; r < 4; ++r)
-#pragma unroll
-                    for (int q = c + 1; q <= r; ++q) D[4 * r + q] = fmaf(-D[4 * r + c], D[4 * q + c], D[4 * r + q]);
-            }
-            // (b) rows of tile column p.  The diagonal tile itself is not written back
-            // (other threads may still be reading it): its pivots go to piv[] and, when
-            // it holds row N, that row's factor entries to ydiag[].
-            for (int r = k0 + tid; r < (T << 2); r += NT) {
-                const int I = r >> 2, ra = r & 3;
-                float* rowp = tile_at(tiles, I, p) + 4 * ra;
-                float x[4];
-                if (I == p) {
-                    if (ra < nc) {
-                        piv[k0 + ra] = pv[ra];
-                        if (!(pv[ra] > 0.0f)) s_fail = 1;
-                    }
-                    if (r == N) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) ydiag[c] = c < nc ? D[4 * ra + c] : 0.0f;
-                    }
-                    continue;
-                } else {
+                {
+                    const float4 q = ld4(dfac + 16);
+                    rs[0] = q.x;
+                    rs[1] = q.y;
+                    rs[2] = q.z;
+                    rs[3] = q.w;
+                }
+                for (int r = k0 + 4 + tid; r < (T << 2); r += NT) {
+                    float* rowp = tile_at(tiles, r >> 2, p) + 4 * (r & 3);
                     const float4 q = ld4(rowp);
-                    x[0] = q.x;
-                    x[1] = q.y;
-                    x[2] = q.z;
-                    x[3] = q.w;
+                    float x[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         float v = x[c];
 #pragma unroll
-                        for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], D[4 * c + q2], v);
+                        for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], L[4 * c + q2], v);
                         x[c] = c < nc ? v * rs[c] : 0.0f;
                     }
+                    st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
                 }
-                st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
             }
             __syncthreads();
-            // (c) trailing tiles
+            // (b) trailing tiles; thread 0 starts with the next diagonal tile and factors it
             const int S = T - p - 1;
             const int cnt = (S * (S + 1)) >> 1;
             for (int q = tid; q < cnt; q += NT) {
@@ -382,7 +433,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    float4 acc = ld4(At + 4 * r);
+                    const float4 acc = ld4(At + 4 * r);
                     float o[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
@@ -390,6 +441,8 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
                         for (int k = 0; k < 4; ++k) o[c] = fmaf(-pi[4 * r + k], pj[4 * c + k], o[c]);
                     st4(At + 4 * r, make_float4(o[0], o[1], o[2], o[3]));
                 }
+                if (q == 0 && ((p + 1) << 2) < N)
+                    factor_diag(At, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, &s_fail);
             }
             __syncthreads();
         }
@@ -598,7 +651,7 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
     if (kind == 2) return 0;
     if (kind == 1) {
         const size_t T = (R + 3) / 4;
-        return ((sizeof(float) * (T * (T + 1) / 2 * 16 + 5 * (size_t)nmax + 4)) + 15) & ~(size_t)15;
+        return ((sizeof(float) * (T * (T + 1) / 2 * 20 + 5 * (size_t)nmax)) + 15) & ~(size_t)15;
     }
     size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
     return (bytes + 15) & ~(size_t)15;
