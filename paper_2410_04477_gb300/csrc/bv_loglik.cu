@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                 const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                 acc = fma(t, t, acc);
             }
-            double v = matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
+            // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
+            const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
+            double v = matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
         }
