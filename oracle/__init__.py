@@ -72,11 +72,10 @@ _P = ctypes.POINTER
 _d, _i64, _i32, _u64, _int = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int
 
 
-def lib():
-    global _lib
-    with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+def _bind(L):
+    """Declare the C signatures on a loaded oracle library."""
+    if True:
+        if True:
             L.or_splitmix64.restype = _u64
             L.or_splitmix64.argtypes = [_u64, _u64]
             L.or_bessel_k.restype = _d
@@ -108,8 +107,34 @@ def lib():
                                               _P(_d), _i32, _P(_i32), _P(_i64), _P(_i32)]
             L.or_num_threads.restype = _int
             L.or_num_threads.argtypes = []
-            _lib = L
+    return L
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
         return _lib
+
+
+class use_library:
+    """Tests only: route this module's calls to another build of the oracle (a copy with
+    a planted mistake), restoring the real one on exit."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        lib()
+        self.saved = _lib
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *a):
+        global _lib
+        _lib = self.saved
 
 
 def _ptr(a, ct):

@@ -525,9 +525,12 @@ int or_kmeans(const double* locs, int64_t n, int d, int64_t k, uint64_t seed, in
     /* k-means++ seeding */
     int64_t first = (int64_t)or_mulhi(or_sm64(stream, 0), (uint64_t)n);
     for (int j = 0; j < d; j++) cent[j] = locs[first * d + j];
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) D2[i] = or_d2(locs + i * d, cent, d);
     for (int64_t t = 1; t < k; t++) {
         uint64_t W = 0;
+        /* exact integer sum: the order of the additions does not matter */
+#pragma omp parallel for schedule(static) reduction(+ : W)
         for (int64_t i = 0; i < n; i++) W += (uint64_t)ldexp(D2[i], s);
         uint64_t r = or_sm64(stream, (uint64_t)t);
         int64_t pick;
@@ -542,6 +545,7 @@ int or_kmeans(const double* locs, int64_t n, int d, int64_t k, uint64_t seed, in
             }
         }
         for (int j = 0; j < d; j++) cent[t * d + j] = locs[pick * d + j];
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
             double v = or_d2(locs + i * d, cent + t * d, d);
             if (v < D2[i]) D2[i] = v;

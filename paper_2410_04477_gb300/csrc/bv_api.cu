@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -539,7 +541,8 @@ static int set_grid(bv_ctx* c, BinPlan& bp) {
     }
     const int occ = bv_occupancy(bp.kind, bp.threads, bp.smem);
     if (occ <= 0) return BV_EINTERNAL;
-    bp.grid = (int)std::min<int64_t>(bp.nwork, (int64_t)occ * c->num_sms);
+    const int64_t per_cta = bp.kind == 3 ? bp.threads / 32 : 1;  // blocks in flight per CTA
+    bp.grid = (int)std::min<int64_t>((bp.nwork + per_cta - 1) / per_cta, (int64_t)occ * c->num_sms);
     return BV_OK;
 }
 
@@ -640,21 +643,32 @@ static int autotune(bv_ctx* c, int prec) {
     BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
     for (auto& bp : c->plan[prec]) {
         if (bp.kind == 2) continue;
-        const int cands[] = {96, 160, 288, 544};
-        int best_t = bp.threads;
+        // candidates: CTA per block with 1 panel warp + 2/4/8/16 update warps; for small
+        // mixed-precision blocks also a warp per block with 2/4/8 warps per CTA
+        std::vector<std::pair<int, int>> cands;
+        for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
+        if (bp.kind == 1 && bp.nmax <= 128)
+            for (int t : {64, 128, 256}) cands.push_back({3, t});
+        int best_k = bp.kind, best_t = bp.threads;
         float best_ms = 1e30f;
-        for (int t : cands) {
+        for (auto kt : cands) {
             BinPlan trial = bp;
-            trial.threads = t;
+            trial.kind = kt.first;
+            trial.threads = kt.second;
             if (set_grid(c, trial) != BV_OK) continue;
             const float ms = time_bin(c, trial, 2);
             if (ms < best_ms) {
                 best_ms = ms;
-                best_t = t;
+                best_k = kt.first;
+                best_t = kt.second;
             }
         }
+        bp.kind = best_k;
         bp.threads = best_t;
         BV_TRY(set_grid(c, bp));
+        if (getenv("BV_LOG_PLAN"))
+            fprintf(stderr, "[bv plan] prec %d bin nmax %d nwork %d -> kind %d threads %d grid %d smem %zu (%.3f ms)\n",
+                    prec, bp.nmax, bp.nwork, bp.kind, bp.threads, bp.grid, bp.smem, best_ms);
     }
     BV_CUDA(cudaGetLastError());
     c->tuned[prec] = true;

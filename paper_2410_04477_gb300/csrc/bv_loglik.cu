@@ -302,170 +302,218 @@ __device__ __forceinline__ void factor_diag(const float* tp, int nc, int k0, int
         }
 }
 
+// Group synchronisation: a whole CTA, or one warp that owns its block.
+template <bool WARP>
+__device__ __forceinline__ void gsync() {
+    if (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+// Floats of shared memory one mixed-precision block of augmented size <= nmax needs.
+__host__ __device__ __forceinline__ int mixed_floats(int nmax) {
+    const int T = (nmax + 1 + 3) >> 2;
+    return ((((T * (T + 1)) >> 1) * kTS + 5 * nmax + 28) + 3) & ~3;
+}
+
+// One block, mixed precision, by a group of NG threads (tid in [0, NG)).  sm: the
+// group's shared region (mixed_floats(N) floats, 16-byte aligned).  Returns the group's
+// partial sum of z^2 + log pivot over the block columns in every thread (valid after the
+// caller reduces it) and sets *fail.
+template <int NG, bool WARP>
+__device__ __forceinline__ double mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
+    const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
+    const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
+    const int N = m + b, R = N + 1, T = (R + 3) >> 2;
+    const DevTheta th = a.theta[a.bds[blk]];
+    float* tiles = sm;
+    float* px = tiles + ((T * (T + 1)) >> 1) * kTS;
+    float* yv = px + 3 * N;
+    float* piv = yv + N;
+    float* dfac = sm + ((((((T * (T + 1)) >> 1) * kTS + 5 * N) + 3) & ~3));  // 16-byte aligned
+    float* ydiag = dfac + 24;
+    const int d = a.d;
+    const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
+    const double ir0 = th.inv_range[0], ir1 = th.inv_range[1], ir2 = th.inv_range[2];
+
+    for (int t = tid; t < N; t += NG) {
+        const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+        const double* cb = a.cent + (int64_t)blk * d;
+        px[t] = (float)((a.locs[g] - cb[0]) * ir0);
+        px[N + t] = d > 1 ? (float)((a.locs[a.n_tot + g] - cb[1]) * ir1) : 0.0f;
+        px[2 * N + t] = d > 2 ? (float)((a.locs[2 * a.n_tot + g] - cb[2]) * ir2) : 0.0f;
+        yv[t] = (float)a.y[g];
+    }
+    gsync<WARP>();
+
+    // fill: one 4x4 tile per thread (padding rows/columns and the strictly upper part of
+    // diagonal tiles get 0; row N is y)
+    const int NTL = (T * (T + 1)) >> 1;
+    for (int q = tid; q < NTL; q += NG) {
+        int I, J;
+        tri_rc(q, I, J);
+        float* tp = tiles + q * kTS;
+        float cx[4], cy[4], cz[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = (J << 2) + e;
+            const bool ok = c < N;
+            cx[e] = ok ? px[c] : 0.0f;
+            cy[e] = ok ? px[N + c] : 0.0f;
+            cz[e] = ok ? px[2 * N + c] : 0.0f;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = (I << 2) + rr;
+            float o[4];
+            if (r < N) {
+                const float rx = px[r], ry = px[N + r], rz = px[2 * N + r];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = (J << 2) + e;
+                    const float t0 = rx - cx[e], t1 = ry - cy[e], t2 = rz - cz[e];
+                    float v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
+                    if (r == c) v += tau2;
+                    o[e] = c <= r ? v : 0.0f;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = (J << 2) + e;
+                    o[e] = (r == N && c < N) ? yv[c] : 0.0f;
+                }
+            }
+            st4(tp + 4 * rr, make_float4(o[0], o[1], o[2], o[3]));
+        }
+    }
+    gsync<WARP>();
+    if (tid == 0) factor_diag(tiles, min(4, N), 0, N, dfac, piv, ydiag, fail);
+    gsync<WARP>();
+
+    for (int p = 0; (p << 2) < N; ++p) {
+        const int k0 = p << 2, nc = min(4, N - k0);
+        // rows of tile column p below the diagonal tile
+        {
+            float L[16], rs[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 q = ld4(dfac + 4 * r);
+                L[4 * r] = q.x;
+                L[4 * r + 1] = q.y;
+                L[4 * r + 2] = q.z;
+                L[4 * r + 3] = q.w;
+            }
+            {
+                const float4 q = ld4(dfac + 16);
+                rs[0] = q.x;
+                rs[1] = q.y;
+                rs[2] = q.z;
+                rs[3] = q.w;
+            }
+            for (int r = k0 + 4 + tid; r < (T << 2); r += NG) {
+                float* rowp = tile_at(tiles, r >> 2, p) + 4 * (r & 3);
+                const float4 q = ld4(rowp);
+                float x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v = x[c];
+#pragma unroll
+                    for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], L[4 * c + q2], v);
+                    x[c] = c < nc ? v * rs[c] : 0.0f;
+                }
+                st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
+            }
+        }
+        gsync<WARP>();
+        // trailing tiles; thread 0 starts with the next diagonal tile and factors it
+        const int S = T - p - 1;
+        const int cnt = (S * (S + 1)) >> 1;
+        for (int q = tid; q < cnt; q += NG) {
+            int ii, jj;
+            tri_rc(q, ii, jj);
+            const int I = p + 1 + ii, J = p + 1 + jj;
+            const float* PI = tile_at(tiles, I, p);
+            const float* PJ = tile_at(tiles, J, p);
+            float* At = tile_at(tiles, I, J);
+            float pi[16], pj[16];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 u = ld4(PI + 4 * r), v = ld4(PJ + 4 * r);
+                pi[4 * r] = u.x; pi[4 * r + 1] = u.y; pi[4 * r + 2] = u.z; pi[4 * r + 3] = u.w;
+                pj[4 * r] = v.x; pj[4 * r + 1] = v.y; pj[4 * r + 2] = v.z; pj[4 * r + 3] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 acc = ld4(At + 4 * r);
+                float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) o[c] = fmaf(-pi[4 * r + k], pj[4 * c + k], o[c]);
+                st4(At + 4 * r, make_float4(o[0], o[1], o[2], o[3]));
+            }
+            if (q == 0 && ((p + 1) << 2) < N)
+                factor_diag(At, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, fail);
+        }
+        gsync<WARP>();
+    }
+
+    // quadratic form and log-determinant terms of the block columns, in FP64
+    double part = 0.0;
+    for (int k = m + tid; k < N; k += NG) {
+        const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
+                                              : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
+        part += z * z + log((double)piv[k]);
+    }
+    return part;
+}
+
+__device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, int failed) {
+    double ell = -0.5 * (s + (double)b * kLog2Pi);
+    if (failed || !(ell == ell)) {
+        ell = -INFINITY;
+        record_fail(a.fail, blk);
+    }
+    a.ell_blk[blk] = ell;
+}
+
+// CTA per block.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ double red[NT / 32];
-    __shared__ __align__(16) float dfac[24];
-    __shared__ __align__(16) float ydiag[4];
     __shared__ int s_fail;
     const int tid = threadIdx.x;
-
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int blk = a.work[w];
-        const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
-        const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
-        const int N = m + b, R = N + 1, T = (R + 3) >> 2;
-        const DevTheta th = a.theta[a.bds[blk]];
-        float* tiles = sm;
-        float* px = tiles + ((T * (T + 1)) >> 1) * kTS;
-        float* yv = px + 3 * N;
-        float* piv = yv + N;
-        const int d = a.d;
-        const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
-        const double ir0 = th.inv_range[0], ir1 = th.inv_range[1], ir2 = th.inv_range[2];
-
-        for (int t = tid; t < N; t += NT) {
-            const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            const double* cb = a.cent + (int64_t)blk * d;
-            px[t] = (float)((a.locs[g] - cb[0]) * ir0);
-            px[N + t] = d > 1 ? (float)((a.locs[a.n_tot + g] - cb[1]) * ir1) : 0.0f;
-            px[2 * N + t] = d > 2 ? (float)((a.locs[2 * a.n_tot + g] - cb[2]) * ir2) : 0.0f;
-            yv[t] = (float)a.y[g];
-        }
         if (tid == 0) s_fail = 0;
         __syncthreads();
-
-        // fill: one 4x4 tile per thread (padding rows/columns and the strictly upper part
-        // of diagonal tiles get 0; row N is y)
-        const int NTL = (T * (T + 1)) >> 1;
-        for (int q = tid; q < NTL; q += NT) {
-            int I, J;
-            tri_rc(q, I, J);
-            float* tp = tiles + q * kTS;
-            float cx[4], cy[4], cz[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = (J << 2) + e;
-                const bool ok = c < N;
-                cx[e] = ok ? px[c] : 0.0f;
-                cy[e] = ok ? px[N + c] : 0.0f;
-                cz[e] = ok ? px[2 * N + c] : 0.0f;
-            }
-#pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
-                const int r = (I << 2) + rr;
-                float o[4];
-                if (r < N) {
-                    const float rx = px[r], ry = px[N + r], rz = px[2 * N + r];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = (J << 2) + e;
-                        const float t0 = rx - cx[e], t1 = ry - cy[e], t2 = rz - cz[e];
-                        float v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
-                        if (r == c) v += tau2;
-                        o[e] = c <= r ? v : 0.0f;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = (J << 2) + e;
-                        o[e] = (r == N && c < N) ? yv[c] : 0.0f;
-                    }
-                }
-                st4(tp + 4 * rr, make_float4(o[0], o[1], o[2], o[3]));
-            }
-        }
-        __syncthreads();
-        if (tid == 0) factor_diag(tiles, min(4, N), 0, N, dfac, piv, ydiag, &s_fail);
-        __syncthreads();
-
-        for (int p = 0; (p << 2) < N; ++p) {
-            const int k0 = p << 2, nc = min(4, N - k0);
-            // (a) rows of tile column p below the diagonal tile
-            {
-                float L[16], rs[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float4 q = ld4(dfac + 4 * r);
-                    L[4 * r] = q.x;
-                    L[4 * r + 1] = q.y;
-                    L[4 * r + 2] = q.z;
-                    L[4 * r + 3] = q.w;
-                }
-                {
-                    const float4 q = ld4(dfac + 16);
-                    rs[0] = q.x;
-                    rs[1] = q.y;
-                    rs[2] = q.z;
-                    rs[3] = q.w;
-                }
-                for (int r = k0 + 4 + tid; r < (T << 2); r += NT) {
-                    float* rowp = tile_at(tiles, r >> 2, p) + 4 * (r & 3);
-                    const float4 q = ld4(rowp);
-                    float x[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        float v = x[c];
-#pragma unroll
-                        for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], L[4 * c + q2], v);
-                        x[c] = c < nc ? v * rs[c] : 0.0f;
-                    }
-                    st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
-                }
-            }
-            __syncthreads();
-            // (b) trailing tiles; thread 0 starts with the next diagonal tile and factors it
-            const int S = T - p - 1;
-            const int cnt = (S * (S + 1)) >> 1;
-            for (int q = tid; q < cnt; q += NT) {
-                int ii, jj;
-                tri_rc(q, ii, jj);
-                const int I = p + 1 + ii, J = p + 1 + jj;
-                const float* PI = tile_at(tiles, I, p);
-                const float* PJ = tile_at(tiles, J, p);
-                float* At = tile_at(tiles, I, J);
-                float pi[16], pj[16];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float4 u = ld4(PI + 4 * r), v = ld4(PJ + 4 * r);
-                    pi[4 * r] = u.x; pi[4 * r + 1] = u.y; pi[4 * r + 2] = u.z; pi[4 * r + 3] = u.w;
-                    pj[4 * r] = v.x; pj[4 * r + 1] = v.y; pj[4 * r + 2] = v.z; pj[4 * r + 3] = v.w;
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float4 acc = ld4(At + 4 * r);
-                    float o[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) o[c] = fmaf(-pi[4 * r + k], pj[4 * c + k], o[c]);
-                    st4(At + 4 * r, make_float4(o[0], o[1], o[2], o[3]));
-                }
-                if (q == 0 && ((p + 1) << 2) < N)
-                    factor_diag(At, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, &s_fail);
-            }
-            __syncthreads();
-        }
-
-        // FP64 accumulation of the quadratic form and the log-determinant
-        double part = 0.0;
-        for (int k = m + tid; k < N; k += NT) {
-            const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
-                                                  : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
-            part += z * z + log((double)piv[k]);
-        }
+        const double part = mixed_block<NT, false>(a, blk, sm, tid, &s_fail);
         const double sres = block_sum<NT>(part, red);
-        if (tid == 0) {
-            double ell = -0.5 * (sres + (double)b * kLog2Pi);
-            if (s_fail || !(ell == ell)) {
-                ell = -INFINITY;
-                record_fail(a.fail, blk);
-            }
-            a.ell_blk[blk] = ell;
-        }
+        if (tid == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, s_fail);
         __syncthreads();
+    }
+}
+
+// Warp per block: each of the NT/32 warps of a CTA factors its own blocks with warp
+// synchronisation only (small blocks, where CTA-wide barriers dominate).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int WPB = NT / 32;
+    __shared__ int s_fail[WPB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* sm = reinterpret_cast<float*>(smraw) + (size_t)warp * region_floats;
+    for (int w = blockIdx.x * WPB + warp; w < a.nwork; w += gridDim.x * WPB) {
+        const int blk = a.work[w];
+        if (lane == 0) s_fail[warp] = 0;
+        __syncwarp();
+        double part = mixed_block<32, true>(a, blk, sm, lane, &s_fail[warp]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        __syncwarp();
+        if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part, s_fail[warp]);
+        __syncwarp();
     }
 }
 
@@ -628,6 +676,8 @@ cudaError_t set_smem_cap() {
     cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ll_mixed<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_mixed_w<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     return e;
 }
 
@@ -639,6 +689,7 @@ cudaError_t launch_kind(int kind, int grid, size_t smem, const LLArgs& a, cudaSt
     }
     if (kind == 0) k_ll_fp64<NT><<<grid, NT, smem, s>>>(a);
     else if (kind == 1) k_ll_mixed<NT><<<grid, NT, smem, s>>>(a);
+    else if (kind == 3) k_ll_mixed_w<NT><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
     else k_ll_large<NT><<<grid, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -651,10 +702,8 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
     const size_t R = (size_t)nmax + 1;
     const size_t el = kind == 1 ? sizeof(float) : sizeof(double);
     if (kind == 2) return 0;
-    if (kind == 1) {
-        const size_t T = (R + 3) / 4;
-        return ((sizeof(float) * (T * (T + 1) / 2 * 20 + 5 * (size_t)nmax)) + 15) & ~(size_t)15;
-    }
+    if (kind == 1) return sizeof(float) * (size_t)mixed_floats(nmax);
+    if (kind == 3) return sizeof(float) * (size_t)mixed_floats(nmax) * (size_t)(threads / 32);
     size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
     return (bytes + 15) & ~(size_t)15;
 }
@@ -675,6 +724,8 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     a.work = bp.d_work;
     a.nwork = bp.nwork;
     switch (bp.threads) {
+        case 64: return launch_kind<64>(bp.kind, bp.grid, bp.smem, a, s);
+        case 128: return launch_kind<128>(bp.kind, bp.grid, bp.smem, a, s);
         case 96: return launch_kind<96>(bp.kind, bp.grid, bp.smem, a, s);
         case 160: return launch_kind<160>(bp.kind, bp.grid, bp.smem, a, s);
         case 288: return launch_kind<288>(bp.kind, bp.grid, bp.smem, a, s);
@@ -710,11 +761,13 @@ int bv_occupancy(int kind, int threads, size_t smem) {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT>, NT, smem);  \
             else if (kind == 1)                                                               \
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT>, NT, smem); \
+            else if (kind == 3)                                                               \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed_w<NT>, NT, smem); \
             else                                                                              \
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
         }                                                                                     \
     }
-    BV_OCC(96) BV_OCC(160) BV_OCC(288) BV_OCC(544) BV_OCC(256)
+    BV_OCC(64) BV_OCC(128) BV_OCC(96) BV_OCC(160) BV_OCC(288) BV_OCC(544) BV_OCC(256)
 #undef BV_OCC
     if (e != cudaSuccess) return 0;
     return nb;

@@ -1,0 +1,142 @@
+"""The pins catch plausible mistakes: each test compiles a copy of the oracle with one
+planted mistake (the real source is untouched) and checks that at least one pin fails."""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+from tests import _ref
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "bv_oracle.c")
+
+MUTANTS = {
+    "nugget dropped": ("if (same) c += th->nugget;", "if (same) c += 0.0 * th->nugget;"),
+    "Schur complement sign": ("Slk[j * b + k] -= s;", "Slk[j * b + k] += s;"),
+    "log-det factor 2 missing": ("dl *= 2.0;", "dl *= 1.0;"),
+    "nu = 3/2 closed form": ("return (1.0 + x) * exp(-x);", "return (1.0 + 0.5 * x) * exp(-x);"),
+    "conditional mean sign": ("mu[j] = s;", "mu[j] = -s;"),
+    "y' from the block instead of the neighbours": ("for (int64_t j = 0; j < m; j++) col[j] = y[nn[j]];",
+                                                    "for (int64_t j = 0; j < m; j++) col[j] = y[blk[j % b]];"),
+    "2 pi term counts one extra point": ("ell = -0.5 * (u + dl + (double)b * log(2.0 * M_PI));",
+                                         "ell = -0.5 * (u + dl + (double)(b + 1) * log(2.0 * M_PI));"),
+    "neighbour ties to the highest index": ("return a.d2 < b.d2 || (a.d2 == b.d2 && a.idx < b.idx);",
+                                            "return a.d2 < b.d2 || (a.d2 == b.d2 && a.idx > b.idx);"),
+    "candidates include the block's first point": ("for (int64_t p = 0; p < block_ptr[i]; p++) {",
+                                                   "for (int64_t p = 0; p <= block_ptr[i] && p < n; p++) {"),
+    "K-means ties to the highest centre": ("if (t < best) { best = t; bi = (int32_t)c; }",
+                                           "if (t <= best) { best = t; bi = (int32_t)c; }"),
+    "centroid without the 2^-q scaling": ("cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q);",
+                                          "cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q + 1);"),
+}
+
+
+def _build(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, old
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new, 1))
+    so = str(tmp_path / "libmut.so")
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                    "-o", so, str(path), "-lm"], check=True)
+    return so
+
+
+def _pin_matern():
+    x = np.logspace(-3, 1, 50)
+    return all(np.allclose(oracle.matern_corr(nu, x), _ref.matern_kv(nu, x), rtol=1e-12)
+               for nu in (0.5, 1.5, 2.5))
+
+
+def _setup():
+    n = 240
+    locs = synth.locs_uniform(n, 2, 3)
+    S = _ref.full_cov(locs, 1.2, 0.1, 1.5, 1e-2)
+    y = np.linalg.cholesky(S) @ synth.normal(3, 20, n)
+    return n, locs, S, y, oracle.theta(1.2, 0.1, 1.5, 1e-2)
+
+
+def _pin_one_block():
+    n, locs, S, y, th = _setup()
+    ll1, _, _ = oracle.loglik(th, locs, y, np.array([0, n]), np.arange(n, dtype=np.int32),
+                              np.array([0, 0]), np.zeros(0, np.int32), check=False)
+    return abs(ll1 - _ref.exact_loglik(S, y)) < 1e-9 * abs(ll1)
+
+
+def _pin_dense():
+    n, locs, S, y, th = _setup()
+    bp, pi, ce = oracle.build_blocks(locs, 24, seed=2)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 12)
+    ll, per, st = oracle.loglik(th, locs, y, bp, pi, nnp, nni, check=False)
+    P, ldP, _, _ = _ref.bv_dense_precision(S, bp, pi, nnp, nni)
+    return st == 0 and abs(ll - _ref.loglik_from_precision(P, ldP, y)) < 1e-9 * abs(ll)
+
+
+def _lattice():
+    g = np.arange(10) / 10.0
+    return np.array([(a, b) for a in g for b in g])
+
+
+def _pin_neighbours():
+    lat = _lattice()
+    lbp, lpi, lce = oracle.build_blocks(lat, 20, seed=1, iters=5)
+    lnp, lni = oracle.select_neighbors(lat, lbp, lpi, lce, 9)
+    for i in range(len(lbp) - 1):
+        cand = lpi[:lbp[i]].astype(np.int64)
+        if len(cand) == 0:
+            continue
+        diff = lat[cand] - lce[i]
+        d2 = diff[:, 0] * diff[:, 0] + diff[:, 1] * diff[:, 1]
+        want = cand[np.lexsort((cand, d2))][:min(9, len(cand))]
+        if not np.array_equal(lni[lnp[i]:lnp[i + 1]], want):
+            return False
+    return True
+
+
+def _pin_centroids():
+    lat = _lattice()
+    lbp, lpi, lce = oracle.build_blocks(lat, 20, seed=1, iters=5)
+    return all(np.allclose(lce[i], lat[lpi[lbp[i]:lbp[i + 1]]].mean(axis=0), atol=1e-12)
+               for i in range(len(lbp) - 1))
+
+
+def _pin_kmeans_tie():
+    # three collinear points; with the two seeded centres at the ends (iters = 0) the
+    # middle point is exactly equidistant and must go to the lower centre index
+    x = np.array([[0.0], [2.0], [1.0]])
+    for seed in range(400):
+        lab, cen = oracle.kmeans(x, 2, seed=seed, iters=0)
+        if sorted(cen[:, 0].tolist()) == [0.0, 2.0]:
+            return lab[2] == 0 and lab[0] == int(np.argmin(np.abs(cen[:, 0] - 0.0)))
+    raise AssertionError("no seed puts the centres at both ends")
+
+
+PINS = {"matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
+        "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
+        "K-means exact tie": _pin_kmeans_tie}
+
+
+def _pins():
+    """Reduced versions of the pins in test_oracle_*.py; a pin that raises has failed."""
+    out = {}
+    for name, f in PINS.items():
+        try:
+            out[name] = bool(f())
+        except Exception as e:  # noqa: BLE001 -- a crash is a caught mistake
+            out[name] = False
+    return out
+
+
+def test_real_oracle_passes_the_reduced_pins():
+    res = _pins()
+    assert all(res.values()), res
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    with oracle.use_library(_build(tmp_path, old, new)):
+        res = _pins()
+    assert not all(res.values()), f"mistake '{name}' passed every pin: {res}"
