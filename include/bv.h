@@ -252,7 +252,10 @@ int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_the
  *            min(n, max_points) points (point j kept when floor(r_j n / 2^64) < max_points,
  *            r_j = SplitMix64 draw j of stream seed);
  *   [32] log var(y); [33..36] block size mean, std, min, max; [37] mean conditioning
- *   size m_i; [38] log n; [39] d.
+ *   size m_i; [38] nearest-neighbour semivariance: mean over subsample points i of
+ *   (y_i - y_nn(i))^2 / 2, divided by var(y), nn(i) the nearest other subsample point
+ *   (squared distance without fused multiply-add, lowest index on ties); [39] 64 x the
+ *   mean nearest-neighbour distance (in semivariogram-bin units).
  * Blocks and neighbours must exist.  out[ndatasets x BV_NFEAT] (host).  Synchronous. */
 #define BV_NFEAT 40
 int bv_features(bv_ctx* ctx, int32_t max_points, uint64_t seed, float* out);

@@ -2,7 +2,8 @@
 non-learned heuristic is to start from a cheaper fit, Sec. 2.3).
 
 TEST INFRASTRUCTURE (see oracle/__init__.py).  Plain, slow definitions:
-  features()     the 40 summary features of one dataset (semivariogram + structure stats)
+  features()     the 40 summary features of one dataset (semivariogram, structure
+                 statistics, nearest-neighbour semivariance and distance)
   mlp_forward()  the MLP 40 -> 128 -> 128 -> 128 -> 6 with exact-erf GELU
   mlp_loss_grad()  the training loss and its gradient by explicit backpropagation
 """
@@ -21,8 +22,8 @@ BLOB = NPARAM + 2 * NFEAT + 6
 
 def features(locs, y, block_ptr, nn_ptr, max_points=10000, seed=0):
     """Semivariogram gamma_k / var(y) in 32 bins of width 1/64 on (0, 0.5] over a seeded
-    subsample, then log var(y), block-size mean/std/min/max, mean conditioning size,
-    log n, d."""
+    subsample, then log var(y), block-size mean/std/min/max, mean conditioning size, the
+    nearest-neighbour semivariance / var(y) and 64 x the mean nearest-neighbour distance."""
     locs = np.asarray(locs, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     n, d = locs.shape
@@ -55,8 +56,20 @@ def features(locs, y, block_ptr, nn_ptr, max_points=10000, seed=0):
     f[32] = np.log(var)
     f[33], f[34], f[35], f[36] = bs.mean(), bs.std(), bs.min(), bs.max()
     f[37] = ms.mean()
-    f[38] = np.log(n)
-    f[39] = d
+    # nearest other subsample point (squared distance summed left to right, lowest index
+    # on ties): semivariance and distance at the smallest lag
+    g_nn, d_nn = 0.0, 0.0
+    for a in range(P):
+        diff = X - X[a]
+        d2 = diff[:, 0] * diff[:, 0]
+        for k in range(1, d):
+            d2 = d2 + diff[:, k] * diff[:, k]
+        d2[a] = np.inf
+        j = int(np.argmin(d2))
+        g_nn += 0.5 * (V[a] - V[j]) ** 2
+        d_nn += np.sqrt(d2[j])
+    f[38] = g_nn / P / var
+    f[39] = 64.0 * d_nn / P
     return f
 
 

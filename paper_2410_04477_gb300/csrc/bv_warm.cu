@@ -98,6 +98,63 @@ __global__ void __launch_bounds__(kVT) k_variogram(const double* __restrict__ xs
     }
 }
 
+// Nearest neighbour of every subsample point (exact FP64 squared distance without
+// contraction; ties to the lowest index), in three passes over all ordered pairs:
+// the minimum distance, then the lowest index attaining it, then the semivariance term.
+// pass 1 (which = 0): best[i] = min_j d2 bits; pass 2 (which = 1): arg[i] = min j with
+// d2 == best[i].  One thread per i, j streamed through shared memory.
+__global__ void __launch_bounds__(kVT) k_nn_pass(const double* __restrict__ xs, const double* __restrict__ ys_,
+                                                 const double* __restrict__ zs, int d, int64_t P, int which,
+                                                 unsigned long long* __restrict__ best,
+                                                 unsigned long long* __restrict__ arg) {
+    __shared__ double tx[kVT], ty[kVT], tz[kVT];
+    const int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x;
+    const bool live = i < P;
+    double xi = 0, yi = 0, zi = 0;
+    if (live) {
+        xi = xs[i];
+        yi = d > 1 ? ys_[i] : 0.0;
+        zi = d > 2 ? zs[i] : 0.0;
+    }
+    unsigned long long bi = ~0ull, ai = ~0ull;
+    const unsigned long long target = (live && which == 1) ? best[i] : 0ull;
+    for (int64_t j0 = 0; j0 < P; j0 += kVT) {
+        __syncthreads();
+        if (j0 + threadIdx.x < P) {
+            tx[threadIdx.x] = xs[j0 + threadIdx.x];
+            ty[threadIdx.x] = d > 1 ? ys_[j0 + threadIdx.x] : 0.0;
+            tz[threadIdx.x] = d > 2 ? zs[j0 + threadIdx.x] : 0.0;
+        }
+        __syncthreads();
+        if (!live) continue;
+        const int jn = (int)min((int64_t)kVT, P - j0);
+        for (int t = 0; t < jn; ++t) {
+            const int64_t j = j0 + t;
+            if (j == i) continue;
+            const double dx = __dsub_rn(xi, tx[t]);
+            double d2 = __dmul_rn(dx, dx);
+            if (d > 1) {
+                const double dy = __dsub_rn(yi, ty[t]);
+                d2 = __dadd_rn(d2, __dmul_rn(dy, dy));
+            }
+            if (d > 2) {
+                const double dz = __dsub_rn(zi, tz[t]);
+                d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+            }
+            const unsigned long long kb = (unsigned long long)__double_as_longlong(d2);
+            if (which == 0) {
+                if (kb < bi) bi = kb;
+            } else if (kb == target && (unsigned long long)j < ai) {
+                ai = (unsigned long long)j;
+            }
+        }
+    }
+    if (live) {
+        if (which == 0) best[i] = bi;
+        else arg[i] = ai;
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // MLP kernels (FP32).  Activations are row-major [batch][features].
 // ---------------------------------------------------------------------------------
@@ -353,6 +410,33 @@ extern "C" int bv_features(bv_ctx* c, int32_t max_points, uint64_t seed, float* 
         BV_CUDA(cudaMemcpyAsync(hc.data(), pcnt, sizeof(unsigned long long) * ntile * kBins, cudaMemcpyDeviceToHost,
                                 c->stream));
         BV_CUDA(cudaStreamSynchronize(c->stream));
+        // nearest neighbour inside the subsample: semivariance and distance at the
+        // smallest lag the data offer (these carry the nugget)
+        double nn_gamma = 0.0, nn_dist = 0.0;
+        if (P >= 2) {
+            unsigned long long *dbest = nullptr, *darg = nullptr;
+            BV_CUDA(cudaMalloc(&dbest, sizeof(unsigned long long) * P));
+            BV_CUDA(cudaMalloc(&darg, sizeof(unsigned long long) * P));
+            const unsigned g = (unsigned)((P + kVT - 1) / kVT);
+            k_nn_pass<<<g, kVT, 0, c->stream>>>(dsoa, dsoa + P, dsoa + 2 * P, d, P, 0, dbest, darg);
+            k_nn_pass<<<g, kVT, 0, c->stream>>>(dsoa, dsoa + P, dsoa + 2 * P, d, P, 1, dbest, darg);
+            BV_CUDA(cudaGetLastError());
+            std::vector<unsigned long long> hb(P), ha(P);
+            BV_CUDA(cudaMemcpyAsync(hb.data(), dbest, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, c->stream));
+            BV_CUDA(cudaMemcpyAsync(ha.data(), darg, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, c->stream));
+            BV_CUDA(cudaStreamSynchronize(c->stream));
+            cudaFree(dbest);
+            cudaFree(darg);
+            for (int64_t q = 0; q < P; ++q) {
+                double d2;
+                memcpy(&d2, &hb[q], sizeof(d2));
+                const double dv = soa[(size_t)3 * P + q] - soa[(size_t)3 * P + (int64_t)ha[q]];
+                nn_gamma += 0.5 * dv * dv;
+                nn_dist += sqrt(d2);
+            }
+            nn_gamma /= (double)P;
+            nn_dist /= (double)P;
+        }
         cudaFree(dsoa);
         cudaFree(psum);
         cudaFree(pcnt);
@@ -395,8 +479,8 @@ extern "C" int bv_features(bv_ctx* c, int32_t max_points, uint64_t seed, float* 
         f[35] = (float)mn;
         f[36] = (float)mx;
         f[37] = (float)(mm / nbk);
-        f[38] = (float)log((double)n);
-        f[39] = (float)d;
+        f[38] = (float)(nn_gamma / var);
+        f[39] = (float)(64.0 * nn_dist);
     }
     return BV_OK;
 }
@@ -457,7 +541,10 @@ extern "C" int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t e
         }
         const double sd = sqrt(q / (double)n);
         blob[k] = (float)m;
-        blob[BV_NFEAT + k] = (float)(sd > 1e-12 ? sd : 1.0);
+        // a feature constant over the training set carries no information: a huge scale
+        // maps it to 0 for every input, so an unseen value cannot push the network out of
+        // its training distribution
+        blob[BV_NFEAT + k] = (float)(sd > 1e-6 * (fabs(m) + 1.0) ? sd : 1e30);
     }
     for (int k = 0; k < 3; ++k) {
         double m = 0.0, q = 0.0;

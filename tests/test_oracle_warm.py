@@ -78,4 +78,13 @@ def test_variogram_of_a_linear_field():
     want = np.where(cnts > 0, sums / np.maximum(cnts, 1) / var, 0.0)
     np.testing.assert_allclose(f[:32], want, rtol=1e-12)
     assert f[33] == 150 and f[35] == 100 and f[36] == 200 and f[37] == 25
-    assert abs(f[38] - np.log(n)) < 1e-15 and f[39] == 1
+    # nearest neighbour on a sorted line: the closer of the two adjacent points
+    xs = x[:, 0]
+    g_nn = d_nn = 0.0
+    for i in range(n):
+        cand = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        j = min(cand, key=lambda jj: ((xs[i] - xs[jj]) ** 2, jj))
+        g_nn += 0.5 * (c * (xs[i] - xs[j])) ** 2
+        d_nn += abs(xs[i] - xs[j])
+    assert abs(f[38] - g_nn / n / var) <= 1e-12 * f[38]
+    assert abs(f[39] - 64 * d_nn / n) <= 1e-12 * f[39]
