@@ -327,16 +327,17 @@ def run_mle(bv, ctx, w, log):
         warm0 = ctx.warmstart_predict(cold0)
         res["warm_predict_s"] = time.perf_counter() - t0
         res["warm_start_theta"] = [warm0.sigma2, warm0.range[0], warm0.nugget]
-    # initial simplex scale: 0.5 in log-parameters from the fixed cold start; 0.2 (about the
-    # network's validation RMSE of log sigma^2 and log beta) from the learned warm start
+    # initial simplex scale: 0.5 in log-parameters from the fixed cold start; from the
+    # learned warm start its validation RMSE (0.2 for log sigma^2 and log beta, 0.75 for
+    # log tau^2, weights/warmstart.json)
     for pname, prec in (("fp64", bv.BV_FP64), ("mixed", bv.BV_MIXED)):
-        for sname, th0, step in (("cold", cold0, 0.5), ("warm", warm0, 0.2)):
+        for sname, th0, step, stepn in (("cold", cold0, 0.5, 0.5), ("warm", warm0, 0.2, 0.75)):
             if th0 is None:
                 continue
             ctx.loglik(th0, prec)   # plan, tune and capture outside the timed MLE
             t0 = time.perf_counter()
             th, ll, ne = ctx.mle(th0, lo, hi, precision=prec, ftol_rel=1e-10, xtol=1e-5, max_evals=2000,
-                                 init_step=step)
+                                 init_step=step, init_step_nugget=stepn)
             el = time.perf_counter() - t0
             if sname == "warm":
                 el += res.get("warm_predict_s", 0.0)

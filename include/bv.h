@@ -146,6 +146,15 @@ int bv_get_neighbors(bv_ctx* ctx, int64_t* nn_ptr, int32_t* nn_idx);
 int bv_loglik(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_loglik,
               double* out_per_block);
 
+/* The two terms of ell for dataset 0: ell = -(quad + logdet + n log 2 pi) / 2, with
+ * quad = y^T Sigma~^{-1} y = sum_i u_i and logdet = log |Sigma~| = sum_i d_i (Algorithm 1's
+ * u_i and d_i summed over blocks).  Because every block's conditional covariance scales
+ * with sigma^2 while its kriging weights do not, quad at sigma^2 = 1 gives the profile
+ * estimate sigma^2 = quad / n for a fixed range and nugget-to-sigma^2 ratio (used by
+ * bv_mle).  Any output pointer but out_loglik may be NULL.  Synchronous. */
+int bv_loglik_terms(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_loglik,
+                    double* out_quad, double* out_logdet);
+
 /* All datasets at once: thetas[ndatasets] (host), out_loglik[ndatasets] (host).
  * Synchronous. */
 int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
@@ -228,11 +237,18 @@ typedef struct bv_mle_opts {
     double ftol_rel;     /* stop when the simplex's ell spread < ftol_rel * |ell|      */
     double xtol;         /* ... and its log-parameter spread < xtol                     */
     double init_step;    /* initial simplex step in log-parameter units (e.g. 0.5)     */
+    double init_step_nugget; /* initial step of the nugget's coordinate, log tau^2 or,
+                                with sigma^2 profiled, log(tau^2 / sigma^2) (0: same as
+                                init_step); the nugget is the least identified parameter,
+                                so a start point can be much surer of sigma^2 and beta */
 } bv_mle_opts;
 
 /* Maximise ell over log(sigma^2), log(beta), log(tau^2) (free_mask selects) inside the
  * box [lo, hi] by a bounded Nelder-Mead search (derivative-free, as the paper's BOBYQA,
- * Sec. 3.2).  theta0: start point.  Outputs: theta_hat, loglik_hat, n_evals.
+ * Sec. 3.2).  When sigma^2 is free and the nugget is free or zero, sigma^2 is profiled
+ * out: the search runs over log beta and log(tau^2 / sigma^2) and sigma^2 takes its
+ * closed-form maximiser Q / n (bv_loglik_terms) clamped to the box.  theta0: start
+ * point.  Outputs: theta_hat, loglik_hat (the FP64 ell at theta_hat), n_evals.
  * Synchronous (one device evaluation per optimizer step). */
 int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,

@@ -35,7 +35,7 @@ class bv_theta(ctypes.Structure):
 class bv_mle_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_evals", ctypes.c_int32),
                 ("ftol_rel", ctypes.c_double), ("xtol", ctypes.c_double),
-                ("init_step", ctypes.c_double)]
+                ("init_step", ctypes.c_double), ("init_step_nugget", ctypes.c_double)]
 
 
 def theta(sigma2=1.0, beta=0.1, nu=0.5, nugget=0.0, ranges=None) -> bv_theta:
@@ -79,6 +79,7 @@ _SIGS = {
     "bv_get_blocks": (_int, [_vp, _P(_i64), _P(_i32), _P(_d)]),
     "bv_get_neighbors": (_int, [_vp, _P(_i64), _P(_i32)]),
     "bv_loglik": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d)]),
+    "bv_loglik_terms": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
     "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
@@ -303,6 +304,13 @@ class Context:
             return out.value, per, st
         return out.value
 
+    def loglik_terms(self, th: bv_theta, precision=BV_FP64):
+        """(ell, quad, logdet) with ell = -(quad + logdet + n log 2 pi) / 2."""
+        l, q, d = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(_lib.bv_loglik_terms(self.h, ctypes.byref(th), precision, ctypes.byref(l), ctypes.byref(q),
+                                    ctypes.byref(d)), "bv_loglik_terms")
+        return l.value, q.value, d.value
+
     def loglik_multi(self, thetas, precision=BV_FP64, allow_notpd=False):
         arr = (bv_theta * len(thetas))(*thetas)
         out = np.empty(len(thetas), np.float64)
@@ -339,8 +347,8 @@ class Context:
 
     def mle(self, th0: bv_theta, lo: bv_theta, hi: bv_theta,
             free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
-            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5):
-        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step)
+            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0):
+        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget)
         out = bv_theta()
         ll = ctypes.c_double(0.0)
         ne = ctypes.c_int32(0)

@@ -77,6 +77,7 @@ static void free_blocks(bv_ctx* c) {
     dfree(c->d_bds);
     dfree(c->d_ds_blk_off);
     dfree(c->d_ell_blk);
+    dfree(c->d_u_blk);
     c->h_bptr.clear();
     c->h_pidx.clear();
     c->h_bds.clear();
@@ -90,6 +91,9 @@ static void free_data(bv_ctx* c) {
     dfree(c->d_locs);
     dfree(c->d_y);
     dfree(c->d_out);
+    dfree(c->d_quad);
+    if (c->h_quad) cudaFreeHost(c->h_quad);
+    c->h_quad = nullptr;
     dfree(c->d_theta);
     if (c->h_out) cudaFreeHost(c->h_out);
     c->h_out = nullptr;
@@ -185,6 +189,8 @@ extern "C" int bv_set_datasets(bv_ctx* c, int32_t ndata, const int64_t* n_per, c
     BV_CUDA(cudaMalloc(&c->d_locs, sizeof(double) * n_tot * d));
     BV_CUDA(cudaMalloc(&c->d_y, sizeof(double) * n_tot));
     BV_CUDA(cudaMalloc(&c->d_out, sizeof(double) * ndata));
+    BV_CUDA(cudaMalloc(&c->d_quad, sizeof(double) * ndata));
+    BV_CUDA(cudaMallocHost(&c->h_quad, sizeof(double) * ndata));
     BV_CUDA(cudaMalloc(&c->d_theta, sizeof(DevTheta) * ndata));
     BV_CUDA(cudaMallocHost(&c->h_out, sizeof(double) * ndata));
     c->h_theta.assign(ndata, DevTheta{});
@@ -230,6 +236,7 @@ static int upload_blocks(bv_ctx* c, const std::vector<double>& cent) {
     BV_CUDA(cudaMalloc(&c->d_bds, sizeof(int32_t) * nb));
     BV_CUDA(cudaMalloc(&c->d_ds_blk_off, sizeof(int64_t) * (c->ndata + 1)));
     BV_CUDA(cudaMalloc(&c->d_ell_blk, sizeof(double) * nb));
+    BV_CUDA(cudaMalloc(&c->d_u_blk, sizeof(double) * nb));
     BV_CUDA(cudaMemcpyAsync(c->d_bptr, c->h_bptr.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
                             c->stream));
     BV_CUDA(cudaMemcpyAsync(c->d_pidx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot, cudaMemcpyHostToDevice,
@@ -526,6 +533,7 @@ static LLArgs make_args(bv_ctx* c) {
     a.work = nullptr;
     a.nwork = 0;
     a.ell_blk = c->d_ell_blk;
+    a.u_blk = c->d_u_blk;
     a.fail = c->d_fail;
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
@@ -717,7 +725,7 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
     }
     for (size_t i = 0; i < nb; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
-    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_ds_blk_off, c->ndata, c->d_fail, c->d_bds, c->d_out, c->stream));
+    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->d_out, c->d_quad, c->stream));
     return BV_OK;
 }
 
@@ -763,6 +771,7 @@ static int prepare_eval(bv_ctx* c, const bv_theta* thetas, int32_t prec) {
 
 static int finish_sync(bv_ctx* c, double* out, int nout) {
     BV_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaMemcpyAsync(c->h_quad, c->d_quad, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
     BV_CUDA(cudaMemcpyAsync(c->h_fail, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     BV_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < nout; ++k) out[k] = c->h_out[k];
@@ -820,4 +829,17 @@ extern "C" int bv_plan_info(bv_ctx* c, int32_t prec, int32_t* launches, int32_t*
     if (flops) *flops = f;
     if (entries) *entries = e;
     return BV_OK;
+}
+
+extern "C" int bv_loglik_terms(bv_ctx* c, const bv_theta* theta, int32_t prec, double* out_loglik, double* out_quad,
+                               double* out_logdet) {
+    if (!c || !out_loglik) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    BV_TRY(prepare_eval(c, theta, prec));
+    BV_TRY(bv_enqueue_loglik(c, prec, nullptr, true));
+    const int st = finish_sync(c, out_loglik, 1);
+    const double q = c->h_quad[0];
+    if (out_quad) *out_quad = q;
+    if (out_logdet) *out_logdet = -2.0 * c->h_out[0] - q - (double)c->n_tot * 1.8378770664093454835606594728112;
+    return st;
 }

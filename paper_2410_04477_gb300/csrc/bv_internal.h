@@ -73,6 +73,7 @@ struct LLArgs {
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
     double* ell_blk;         // per-block conditional log-likelihood (output)
+    double* u_blk;           // per-block quadratic form u_i = v_i^T v_i (output)
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
     double* ws;              // global workspace (large-block path)
     int64_t ws_stride;       // doubles per workspace slot
@@ -100,9 +101,8 @@ int bv_occupancy(int kind, int threads, size_t smem);
 // Largest augmented size the global-memory path accepts (packed indices stay in int32).
 #define BV_LARGE_MAX_N 30000
 cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a, cudaStream_t s);
-cudaError_t bv_launch_reduce(const double* ell_blk, const int64_t* ds_blk_off, int32_t ndata,
-                             const unsigned long long* fail, const int32_t* bds, double* out,
-                             cudaStream_t s);
+cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_blk_off,
+                             int32_t ndata, double* out, double* out_quad, cudaStream_t s);
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
 
 // K-means and neighbour search (bv_kmeans.cu, bv_nn.cu).
@@ -173,6 +173,9 @@ struct bv_ctx {
 
     // evaluation state
     double* d_ell_blk = nullptr;
+    double* d_u_blk = nullptr;        // per-block quadratic forms
+    double* d_quad = nullptr;         // ndata: sum of the quadratic forms
+    double* h_quad = nullptr;         // pinned, ndata
     unsigned long long* d_fail = nullptr;
     double* d_out = nullptr;          // ndata
     double* h_out = nullptr;          // pinned, ndata

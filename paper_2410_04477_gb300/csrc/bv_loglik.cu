@@ -217,12 +217,14 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         }
 
         // u + d over the block columns
-        double part = 0.0;
+        double part = 0.0, partu = 0.0;
         for (int k = m + tid; k < N; k += NT) {
             const double z = A[pk(N, k)];
+            partu += z * z;
             part += z * z + log(A[pk(k, k)]);
         }
         const double s = block_sum<NT>(part, red);
+        const double su = block_sum<NT>(partu, red);
         if (tid == 0) {
             double ell = -0.5 * (s + (double)b * kLog2Pi);
             if (s_fail || !(ell == ell)) {
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                 record_fail(a.fail, blk);
             }
             a.ell_blk[blk] = ell;
+            a.u_blk[blk] = su;
         }
         __syncthreads();
     }
@@ -320,7 +323,7 @@ __host__ __device__ __forceinline__ int mixed_floats(int nmax) {
 // partial sum of z^2 + log pivot over the block columns in every thread (valid after the
 // caller reduces it) and sets *fail.
 template <int NG, bool WARP>
-__device__ __forceinline__ double mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
+__device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
     const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
     const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
     const int N = m + b, R = N + 1, T = (R + 3) >> 2;
@@ -458,22 +461,24 @@ __device__ __forceinline__ double mixed_block(const LLArgs& a, int blk, float* s
     }
 
     // quadratic form and log-determinant terms of the block columns, in FP64
-    double part = 0.0;
+    double part = 0.0, partu = 0.0;
     for (int k = m + tid; k < N; k += NG) {
         const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
                                               : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
+        partu += z * z;
         part += z * z + log((double)piv[k]);
     }
-    return part;
+    return make_double2(part, partu);
 }
 
-__device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, int failed) {
+__device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, double su, int failed) {
     double ell = -0.5 * (s + (double)b * kLog2Pi);
     if (failed || !(ell == ell)) {
         ell = -INFINITY;
         record_fail(a.fail, blk);
     }
     a.ell_blk[blk] = ell;
+    a.u_blk[blk] = su;
 }
 
 // CTA per block.
@@ -488,9 +493,10 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
         const int blk = a.work[w];
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        const double part = mixed_block<NT, false>(a, blk, sm, tid, &s_fail);
-        const double sres = block_sum<NT>(part, red);
-        if (tid == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, s_fail);
+        const double2 part = mixed_block<NT, false>(a, blk, sm, tid, &s_fail);
+        const double sres = block_sum<NT>(part.x, red);
+        const double sresu = block_sum<NT>(part.y, red);
+        if (tid == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, sresu, s_fail);
         __syncthreads();
     }
 }
@@ -508,11 +514,14 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
         const int blk = a.work[w];
         if (lane == 0) s_fail[warp] = 0;
         __syncwarp();
-        double part = mixed_block<32, true>(a, blk, sm, lane, &s_fail[warp]);
+        double2 part = mixed_block<32, true>(a, blk, sm, lane, &s_fail[warp]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+        }
         __syncwarp();
-        if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part, s_fail[warp]);
+        if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part.x, part.y, s_fail[warp]);
         __syncwarp();
     }
 }
@@ -604,12 +613,14 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
             }
             __syncthreads();
         }
-        double part = 0.0;
+        double part = 0.0, partu = 0.0;
         for (int k = m + tid; k < N; k += NT) {
             const double z = A[pk(N, k)];
+            partu += z * z;
             part += z * z + log(A[pk(k, k)]);
         }
         const double s = block_sum<NT>(part, red);
+        const double su = block_sum<NT>(partu, red);
         if (tid == 0) {
             double ell = -0.5 * (s + (double)b * kLog2Pi);
             if (s_fail || !(ell == ell)) {
@@ -617,6 +628,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
                 record_fail(a.fail, blk);
             }
             a.ell_blk[blk] = ell;
+            a.u_blk[blk] = su;
         }
         __syncthreads();
     }
@@ -626,35 +638,44 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
 // Deterministic per-dataset sum of the per-block terms (fixed thread->block map, Neumaier
 // compensation per thread, fixed-order combination).
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reduce(const double* ell_blk, const int64_t* ds_off,
-                                                double* out) {
-    __shared__ double ss[256], sc[256];
-    const int ds = blockIdx.x, tid = threadIdx.x;
-    const int64_t lo = ds_off[ds], hi = ds_off[ds + 1];
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+// Fixed-order compensated sums of a per-block array over one dataset's blocks.
+__device__ double dataset_sum(const double* v, int64_t lo, int64_t hi, double* ss, double* sc) {
+    const int tid = threadIdx.x;
     double s = 0.0, c = 0.0;
-    for (int64_t i = lo + tid; i < hi; i += 256) {
-        const double x = ell_blk[i];
-        const double t = s + x;
-        if (fabs(s) >= fabs(x)) c += (s - t) + x;
-        else c += (x - t) + s;
-        s = t;
-    }
+    for (int64_t i = lo + tid; i < hi; i += 256) neumaier_add(s, c, v[i]);
     ss[tid] = s;
     sc[tid] = c;
     __syncthreads();
+    double r = 0.0;
     if (tid == 0) {
         double S = 0.0, C = 0.0;
         for (int i = 0; i < 256; ++i) {
-            const double x = ss[i];
-            const double t = S + x;
-            if (fabs(S) >= fabs(x)) C += (S - t) + x;
-            else C += (x - t) + S;
-            S = t;
+            neumaier_add(S, C, ss[i]);
             C += sc[i];
         }
-        double r = S + C;
-        if (!(r == r)) r = -INFINITY;
-        out[ds] = r;
+        r = S + C;
+    }
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_off,
+                                                double* out, double* out_quad) {
+    __shared__ double ss[256], sc[256];
+    const int ds = blockIdx.x;
+    const int64_t lo = ds_off[ds], hi = ds_off[ds + 1];
+    const double l = dataset_sum(ell_blk, lo, hi, ss, sc);
+    const double q = dataset_sum(u_blk, lo, hi, ss, sc);
+    if (threadIdx.x == 0) {
+        out[ds] = (l == l) ? l : -INFINITY;
+        out_quad[ds] = q;
     }
 }
 
@@ -735,12 +756,9 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     }
 }
 
-cudaError_t bv_launch_reduce(const double* ell_blk, const int64_t* ds_blk_off, int32_t ndata,
-                             const unsigned long long* fail, const int32_t* bds, double* out,
-                             cudaStream_t s) {
-    (void)fail;
-    (void)bds;
-    k_reduce<<<ndata, 256, 0, s>>>(ell_blk, ds_blk_off, out);
+cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_blk_off,
+                             int32_t ndata, double* out, double* out_quad, cudaStream_t s) {
+    k_reduce<<<ndata, 256, 0, s>>>(ell_blk, u_blk, ds_blk_off, out, out_quad);
     return cudaGetLastError();
 }
 

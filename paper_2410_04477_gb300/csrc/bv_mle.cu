@@ -3,14 +3,24 @@
 // The paper estimates theta with the derivative-free BOBYQA optimiser (Sec. 3.2); this
 // library uses the derivative-free Nelder-Mead simplex method (Nelder and Mead 1965) with
 // the standard coefficients (reflection 1, expansion 2, contraction 1/2, shrink 1/2).
-// Coordinates: log(sigma^2 / beta^(2 nu)), log beta, log tau^2 (the free ones).  For the
-// Matern model sigma^2 and beta are poorly identified separately but their combination
-// sigma^2 / beta^(2 nu) is well identified, so the likelihood surface has a long ridge in
-// (log sigma^2, log beta) that this change of variables straightens.  Points outside the
-// box [lo, hi] score -inf.  After convergence the simplex is rebuilt once around the best
-// point and the search resumed (a standard guard against premature collapse).  Every
-// objective value is one device evaluation of ell (bv_loglik); a non-positive-definite
-// point also scores -inf and is rejected.  With BV_MIXED the search runs in mixed
+//
+// Profile likelihood.  Write the covariance as sigma^2 (R_beta + eta I) with eta =
+// tau^2 / sigma^2.  Every block's kriging weights depend on (beta, eta) only and its
+// conditional covariance is sigma^2 times that at sigma^2 = 1, so with Q and D the
+// quadratic form and log-determinant of Eq. 4 at sigma^2 = 1,
+//     ell(sigma^2, beta, eta) = -(Q / sigma^2 + D + n log sigma^2 + n log 2 pi) / 2,
+// which is concave in log sigma^2 with its maximum at sigma^2 = Q / n.  When sigma^2 is
+// free (and the nugget is free or zero) the search therefore runs over (log beta,
+// log eta) only, each point costing one evaluation at sigma^2 = 1 that returns Q and ell
+// (bv_loglik_terms), and sigma^2 is set in closed form: Q / n clamped to the part of the
+// box that keeps sigma^2 and tau^2 = eta sigma^2 inside [lo, hi].  Otherwise the search
+// runs over log(sigma^2 / beta^(2 nu)), log beta, log tau^2 (the free ones); for the
+// Matern model sigma^2 and beta are poorly identified separately but that combination is
+// well identified, so the change of variables straightens the ridge of the surface.
+//
+// Points outside the box score -inf, and so does a non-positive-definite point.  After
+// convergence the simplex is rebuilt once around the best point and the search resumed
+// (a standard guard against premature collapse).  With BV_MIXED the search runs in mixed
 // precision and is finished by a short FP64 search from its optimum, so the returned
 // estimate and ell are FP64.
 #include <math.h>
@@ -31,7 +41,45 @@ struct Space {
     int dim;
     double lo[3], hi[3];  // log-box of sigma^2, range, nugget (in that order, all three)
     double two_nu;
+    bool profile;         // sigma^2 profiled out; coordinates (log beta, log eta)
+    double n;             // number of observations
 };
+
+// Profile coordinates x -> the sigma^2 = 1 point (range, eta) it stands for.
+bool to_unit_theta(const Space& S, const double* x, bv_theta* t, double* leta) {
+    *t = S.base;
+    int k = 0;
+    double lbeta = log(S.base.range[0]);
+    *leta = -INFINITY;  // eta = 0 when the nugget is fixed at zero
+    if (S.mask & BV_FREE_RANGE) lbeta = x[k++];
+    if (S.mask & BV_FREE_NUGGET) *leta = x[k++];
+    if (lbeta < S.lo[1] || lbeta > S.hi[1]) return false;
+    t->sigma2 = 1.0;
+    if (S.mask & BV_FREE_RANGE) {
+        const double f = exp(lbeta) / S.base.range[0];
+        for (int j = 0; j < 3; ++j) t->range[j] = S.base.range[j] * f;
+    }
+    t->nugget = (S.mask & BV_FREE_NUGGET) ? exp(*leta) : 0.0;
+    return true;
+}
+
+// The profile maximiser of ell over sigma^2 inside the box, given Q and log eta: Q / n,
+// or, in logs, clamped to [lo, hi] of sigma^2 intersected with that of tau^2 - log eta.
+bool profile_sigma2(const Space& S, double Q, double leta, double* s2, double* lsig) {
+    double a = S.lo[0], b = S.hi[0];
+    if (S.mask & BV_FREE_NUGGET) {
+        a = std::max(a, S.lo[2] - leta);
+        b = std::min(b, S.hi[2] - leta);
+    }
+    if (!(a <= b) || !(Q > 0.0)) return false;
+    *s2 = Q / S.n;
+    *lsig = log(*s2);
+    if (*lsig < a || *lsig > b) {
+        *lsig = std::min(b, std::max(a, *lsig));
+        *s2 = exp(*lsig);
+    }
+    return true;
+}
 
 // Internal coordinates x -> theta.  x holds, for the free parameters in order:
 // u = log sigma^2 - 2 nu log beta (if sigma^2 free), log beta (if range free), log tau^2.
@@ -47,9 +95,11 @@ bool to_theta(const Space& S, const double* x, bv_theta* t) {
     if (fs) lsig = u + S.two_nu * lbeta;
     if (lsig < S.lo[0] || lsig > S.hi[0] || lbeta < S.lo[1] || lbeta > S.hi[1] || ltau < S.lo[2] || ltau > S.hi[2])
         return false;
-    t->sigma2 = exp(lsig);
-    const double f = exp(lbeta) / S.base.range[0];
-    for (int j = 0; j < 3; ++j) t->range[j] = S.base.range[j] * f;
+    if (fs) t->sigma2 = exp(lsig);
+    if (fr) {
+        const double f = exp(lbeta) / S.base.range[0];
+        for (int j = 0; j < 3; ++j) t->range[j] = S.base.range[j] * f;
+    }
     if (fn) t->nugget = exp(ltau);
     return true;
 }
@@ -57,28 +107,71 @@ bool to_theta(const Space& S, const double* x, bv_theta* t) {
 void from_theta(const Space& S, const bv_theta& t, double* x) {
     int k = 0;
     const double lb = log(t.range[0]);
+    if (S.profile) {
+        if (S.mask & BV_FREE_RANGE) x[k++] = lb;
+        if (S.mask & BV_FREE_NUGGET) x[k++] = log(t.nugget) - log(t.sigma2);
+        return;
+    }
     if (S.mask & BV_FREE_SIGMA2) x[k++] = log(t.sigma2) - S.two_nu * lb;
     if (S.mask & BV_FREE_RANGE) x[k++] = lb;
     if (S.mask & BV_FREE_NUGGET) x[k++] = log(t.nugget);
 }
 
-// One Nelder-Mead search from x0 with initial step `step`; returns the best point and
-// value (of f = -ell) and adds the evaluations used to *evals.
-int nelder_mead(bv_ctx* c, const Space& S, int prec, std::vector<double> x0, double step, double ftol, double xtol,
-                int max_evals, int* evals, std::vector<double>* xbest, double* fbest) {
-    const int n = S.dim;
+// The objective f = -ell at internal coordinates x, one device evaluation per call.
+// Remembers the best full theta it has scored (reset() between precisions).
+struct Objective {
+    bv_ctx* c;
+    const Space* S;
+    int prec = BV_FP64;
+    int evals = 0;
     int hard_error = BV_OK;
-    auto f = [&](const std::vector<double>& x) -> double {
+    double fbest = INFINITY;
+    bv_theta tbest{};
+
+    void reset(int p) {
+        prec = p;
+        fbest = INFINITY;
+    }
+    double operator()(const std::vector<double>& x) {
         bv_theta t;
-        if (!to_theta(S, x.data(), &t)) return INFINITY;
         double ll = -INFINITY;
-        ++*evals;
-        const int st = bv_loglik(c, &t, prec, &ll, nullptr);
-        if (st != BV_OK && st != BV_ENOTPD) hard_error = st;
-        return (st == BV_OK && std::isfinite(ll)) ? -ll : INFINITY;
-    };
+        if (S->profile) {
+            double leta, Q = 0.0;
+            if (!to_unit_theta(*S, x.data(), &t, &leta)) return INFINITY;
+            ++evals;
+            const int st = bv_loglik_terms(c, &t, prec, &ll, &Q, nullptr);
+            if (st != BV_OK && st != BV_ENOTPD) hard_error = st;
+            double s2, lsig;
+            if (st != BV_OK || !std::isfinite(ll) || !profile_sigma2(*S, Q, leta, &s2, &lsig)) return INFINITY;
+            // ell at sigma^2 from ell at 1:  + (Q - Q / sigma^2 - n log sigma^2) / 2
+            ll += 0.5 * (Q - Q / s2 - S->n * lsig);
+            t.sigma2 = s2;
+            if (S->mask & BV_FREE_NUGGET) t.nugget = exp(leta + lsig);
+        } else {
+            if (!to_theta(*S, x.data(), &t)) return INFINITY;
+            ++evals;
+            const int st = bv_loglik(c, &t, prec, &ll, nullptr);
+            if (st != BV_OK && st != BV_ENOTPD) hard_error = st;
+            if (st != BV_OK || !std::isfinite(ll)) return INFINITY;
+        }
+        if (-ll < fbest) {
+            fbest = -ll;
+            tbest = t;
+        }
+        return -ll;
+    }
+};
+
+// One Nelder-Mead search from x0 with initial step `step` (`step_last` for a free
+// nugget's coordinate, the last one); returns the best point and value of f.
+int nelder_mead(Objective& f, const Space& S, std::vector<double> x0, double step, double step_last,
+                double ftol, double xtol, int max_evals, std::vector<double>* xbest, double* fbest) {
+    const int n = S.dim;
+    int& hard_error = f.hard_error;
+    int* evals = &f.evals;
     std::vector<std::vector<double>> X(n + 1, x0);
-    for (int j = 0; j < n; ++j) X[j + 1][j] += step;
+    // the nugget, when free, is the last coordinate and may take its own step
+    for (int j = 0; j < n; ++j) X[j + 1][j] += (j == n - 1 && (S.mask & BV_FREE_NUGGET)) ? step_last : step;
     std::vector<double> F(n + 1);
     for (int j = 0; j <= n; ++j) {
         F[j] = f(X[j]);
@@ -190,24 +283,41 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
     }
     if (free_mask & BV_FREE_NUGGET) t0.nugget = std::min(his[2], std::max(los[2], t0.nugget));
     S.base = t0;
+    S.n = (double)c->n_tot;
+    S.profile = (free_mask & BV_FREE_SIGMA2) && ((free_mask & BV_FREE_NUGGET) || t0.nugget == 0.0);
+    if (S.profile) --S.dim;
     std::vector<double> x(S.dim), xb;
     from_theta(S, t0, x.data());
-    int evals = 0;
+    Objective obj{c, &S};
     double fb = INFINITY;
     const int prec = opts->precision;
-    // search, then one restart around the optimum (smaller step)
-    BV_TRY(nelder_mead(c, S, prec, x, opts->init_step, opts->ftol_rel, opts->xtol, opts->max_evals, &evals, &xb, &fb));
-    BV_TRY(nelder_mead(c, S, prec, xb, std::max(opts->init_step * 0.1, 20.0 * opts->xtol), opts->ftol_rel, opts->xtol,
-                       opts->max_evals, &evals, &xb, &fb));
-    if (prec == BV_MIXED && std::isfinite(fb)) {
-        // FP64 finish from the mixed-precision optimum
-        BV_TRY(nelder_mead(c, S, BV_FP64, xb, std::max(opts->init_step * 0.02, 20.0 * opts->xtol), opts->ftol_rel,
-                           opts->xtol, opts->max_evals, &evals, &xb, &fb));
+    if (S.dim == 0) {
+        // only sigma^2 free (nugget zero): the closed form is the estimate
+        obj.reset(BV_FP64);
+        fb = obj(x);
+        BV_TRY(obj.hard_error);
+    } else {
+        // search, then one restart around the optimum (smaller step)
+        obj.reset(prec);
+        const double s0 = opts->init_step, sn = opts->init_step_nugget > 0.0 ? opts->init_step_nugget : s0;
+        const double s1 = std::max(s0 * 0.1, 20.0 * opts->xtol);
+        BV_TRY(nelder_mead(obj, S, x, s0, sn, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+        BV_TRY(nelder_mead(obj, S, xb, s1, s1, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+        if (prec == BV_MIXED && std::isfinite(fb)) {
+            // FP64 finish from the mixed-precision optimum
+            obj.reset(BV_FP64);
+            const double s2 = std::max(s0 * 0.02, 20.0 * opts->xtol);
+            BV_TRY(nelder_mead(obj, S, xb, s2, s2, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+        }
     }
-    bv_theta th;
-    if (!to_theta(S, xb.data(), &th)) return BV_EINTERNAL;
-    *theta_hat = th;
-    if (loglik_hat) *loglik_hat = -fb;
-    if (n_evals) *n_evals = evals;
-    return std::isfinite(fb) ? BV_OK : BV_ENOTPD;
+    if (!std::isfinite(obj.fbest)) {
+        *theta_hat = t0;
+        if (loglik_hat) *loglik_hat = -INFINITY;
+        if (n_evals) *n_evals = obj.evals;
+        return BV_ENOTPD;
+    }
+    *theta_hat = obj.tbest;
+    if (loglik_hat) *loglik_hat = -obj.fbest;
+    if (n_evals) *n_evals = obj.evals;
+    return BV_OK;
 }

@@ -1,0 +1,124 @@
+"""GPU maximum likelihood (Sec. 3.2) and the two terms of ell it profiles with: the
+quadratic form against the oracle, the returned ell against the oracle at the returned
+theta, the closed-form sigma^2 = Q / n, and local optimality of the estimate."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bv():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2410_04477_gb300 import bv as _bv
+    return _bv
+
+
+def _problem(n=3000, nu=1.5, s2=1.4, beta=0.06, tau2=5e-3, seed=31, bc=300, m=40):
+    locs = synth.locs_uniform(n, 2, seed)
+    y = oracle.exact_draw(oracle.theta(s2, beta, nu, tau2), locs, synth.normal(seed, 20, n))
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+    return locs, y, (bp, pi, nnp, nni), bc, m, seed
+
+
+def _ctx(bv, locs, y, bc, m, seed, ostruct):
+    ctx = bv.Context()
+    ctx.set_data(locs, y)
+    g = ctx.build_blocks(bc, seed=seed, iters=20) + ctx.select_neighbors(m)
+    for a, b in zip(g, ostruct):
+        np.testing.assert_array_equal(a, b)
+    return ctx
+
+
+def _oracle_ell(th, locs, y, st):
+    return oracle.loglik(oracle.theta(th.sigma2, th.range[0], th.nu, th.nugget), locs, y, *st)[0]
+
+
+def test_loglik_terms_match_oracle(bv):
+    locs, y, st, bc, m, seed = _problem()
+    n = len(y)
+    with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
+        th = bv.theta(1.1, 0.05, 1.5, 4e-3)
+        ll, Q, D = ctx.loglik_terms(th)
+        assert ll == ctx.loglik(th)
+    l1 = oracle.loglik(oracle.theta(1.1, 0.05, 1.5, 4e-3), locs, y, *st)[0]
+    l2 = oracle.loglik(oracle.theta(2.2, 0.05, 1.5, 8e-3), locs, y, *st)[0]
+    Q_o = 2.0 * (n * np.log(2.0) - 2.0 * (l1 - l2))   # l1 - l2 = -(Q - Q/2 - n log 2) / 2
+    assert abs(ll - l1) <= 1e-10 * abs(l1)
+    assert abs(Q - Q_o) <= 1e-8 * Q_o, (Q, Q_o)
+    assert ll == pytest.approx(-0.5 * (Q + D + n * np.log(2 * np.pi)), rel=1e-13)
+
+
+@pytest.mark.parametrize("prec_name", ["BV_FP64", "BV_MIXED"])
+def test_profile_mle_is_a_stationary_maximum(bv, prec_name):
+    locs, y, st, bc, m, seed = _problem()
+    n = len(y)
+    nu = 1.5
+    lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+    with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
+        th, ll, ne = ctx.mle(bv.theta(1.0, 0.1, nu, 1e-2), lo, hi, precision=getattr(bv, prec_name),
+                             ftol_rel=1e-13, xtol=1e-7)
+        assert 0 < ne < 2000
+        # the returned ell is the FP64 ell at the returned theta
+        assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)
+        # sigma^2 is the closed-form profile maximiser Q / n at (beta, tau^2 / sigma^2)
+        _, Q1, _ = ctx.loglik_terms(bv.theta(1.0, th.range[0], nu, th.nugget / th.sigma2))
+        assert th.sigma2 == pytest.approx(Q1 / n, rel=1e-12)
+        # a small move of any log-parameter lowers ell
+        for k in range(3):
+            for sgn in (-1, 1):
+                v = [th.sigma2, th.range[0], th.nugget]
+                v[k] *= np.exp(sgn * 1e-3)
+                assert ctx.loglik(bv.theta(v[0], v[1], nu, v[2])) < ll
+    assert abs(ll - _oracle_ell(th, locs, y, st)) <= 1e-10 * abs(ll)
+
+
+def test_profile_mle_paths_without_a_free_nugget(bv):
+    locs, y, st, bc, m, seed = _problem(tau2=0.0, nu=0.5, beta=0.1, n=2000, bc=200, m=30, seed=32)
+    n = len(y)
+    nu = 0.5
+    lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+    with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
+        # sigma^2 alone, nugget zero: closed form, one evaluation
+        th, ll, ne = ctx.mle(bv.theta(1.0, 0.1, nu, 0.0), lo, hi, free_mask=bv.BV_FREE_SIGMA2)
+        assert ne == 1
+        _, Q1, _ = ctx.loglik_terms(bv.theta(1.0, 0.1, nu, 0.0))
+        assert th.sigma2 == pytest.approx(Q1 / n, rel=1e-14) and th.range[0] == 0.1 and th.nugget == 0.0
+        assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)
+        # sigma^2 and range, nugget zero: a one-dimensional search
+        th, ll, ne = ctx.mle(bv.theta(1.0, 0.2, nu, 0.0), lo, hi,
+                             free_mask=bv.BV_FREE_SIGMA2 | bv.BV_FREE_RANGE, ftol_rel=1e-13, xtol=1e-7)
+        assert th.nugget == 0.0
+        for k in range(2):
+            for sgn in (-1, 1):
+                v = [th.sigma2, th.range[0]]
+                v[k] *= np.exp(sgn * 1e-3)
+                assert ctx.loglik(bv.theta(v[0], v[1], nu, 0.0)) < ll
+        # nugget fixed away from zero: no profiling, the direct search over sigma^2 and beta
+        th2, ll2, _ = ctx.mle(bv.theta(1.0, 0.2, nu, 1e-3), lo, hi,
+                              free_mask=bv.BV_FREE_SIGMA2 | bv.BV_FREE_RANGE, ftol_rel=1e-13, xtol=1e-7)
+        assert th2.nugget == 1e-3
+        for k in range(2):
+            for sgn in (-1, 1):
+                v = [th2.sigma2, th2.range[0]]
+                v[k] *= np.exp(sgn * 1e-3)
+                assert ctx.loglik(bv.theta(v[0], v[1], nu, 1e-3)) < ll2
+    assert abs(ll - _oracle_ell(th, locs, y, st)) <= 1e-10 * abs(ll)
+
+
+def test_profile_respects_the_box(bv):
+    # an upper bound on sigma^2 below Q / n: the estimate sits on the bound
+    locs, y, st, bc, m, seed = _problem(n=2000, bc=200, m=30, seed=33)
+    nu = 1.5
+    with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
+        lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(0.5, 3.0, nu, 10.0)
+        th, ll, _ = ctx.mle(bv.theta(0.3, 0.1, nu, 1e-2), lo, hi, ftol_rel=1e-12, xtol=1e-7)
+        assert th.sigma2 <= 0.5 * (1 + 1e-12)
+        assert 1e-6 * (1 - 1e-12) <= th.nugget <= 10.0 * (1 + 1e-12)
+        assert 0.001 <= th.range[0] <= 3.0
+        assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)

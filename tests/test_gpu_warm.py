@@ -99,9 +99,10 @@ def test_warm_start_cuts_loglik_calls(bv):
             th_c, ll_c, ne_c = ctx.mle(cold0, lo, hi, precision=bv.BV_FP64, ftol_rel=1e-12, xtol=1e-6)
             ctx.warmstart_load(wpath)
             warm0 = ctx.warmstart_predict(cold0)
-            # the warm start's simplex scale is its validated uncertainty (about 0.2 in log units)
+            # the warm start's simplex scale is its validated uncertainty (RMSE about 0.2 for
+            # log sigma^2 and log beta, 0.75 for log tau^2)
             th_w, ll_w, ne_w = ctx.mle(warm0, lo, hi, precision=bv.BV_FP64, ftol_rel=1e-12, xtol=1e-6,
-                                       init_step=0.2)
+                                       init_step=0.2, init_step_nugget=0.75)
         assert abs(ll_w - ll_c) <= 1e-6 * abs(ll_c), (ll_w, ll_c)
         calls.append((ne_c, ne_w))
     assert sum(w for _, w in calls) < sum(c for c, _ in calls), calls

@@ -126,6 +126,27 @@ def test_scaling_identity():
     assert l2 == pytest.approx(l1 - 0.5 * len(y) * np.log(c), rel=1e-12)
 
 
+def test_profile_form_in_sigma2():
+    # Scaling sigma^2 and tau^2 together by s leaves every kriging weight unchanged and
+    # scales every conditional covariance by s, so ell(s) = a - Q / (2 s) - (n / 2) log s
+    # for constants a, Q: two evaluations fix a and Q, a third must follow, and the
+    # maximiser over s is Q / n.
+    locs, th, S, y, (bp, pi, nnp, nni) = _setup(n=300, seed=10)
+    n = len(y)
+
+    def ell(s):
+        return oracle.loglik(oracle.theta(1.3 * s, 0.1, 1.5, 1e-2 * s), locs, y, bp, pi, nnp, nni)[0]
+
+    l1, l2 = ell(1.0), ell(2.0)
+    Q = 2.0 * (2.0 * (l2 - l1) + n * np.log(2.0))   # from l1 - l2 = -(Q - Q/2 - n log 2) / 2
+    a = l1 + 0.5 * Q
+    for s in (0.3, 5.0):
+        assert ell(s) == pytest.approx(a - Q / (2 * s) - 0.5 * n * np.log(s), rel=1e-12)
+    s_hat = Q / n
+    for f in (0.999, 1.001):
+        assert ell(s_hat * f) < ell(s_hat)
+
+
 def test_order_within_sets_is_immaterial():
     locs, th, S, y, (bp, pi, nnp, nni) = _setup(n=300, seed=9)
     l1, _, _ = oracle.loglik(th, locs, y, bp, pi, nnp, nni)
