@@ -18,13 +18,19 @@
 // Matern model sigma^2 and beta are poorly identified separately but that combination is
 // well identified, so the change of variables straightens the ridge of the surface.
 //
-// Points outside the box score -inf, and so does a non-positive-definite point.  After
-// convergence the simplex is rebuilt once around the best point and the search resumed
-// (a standard guard against premature collapse).  With BV_MIXED the search runs in mixed
-// precision and is finished by a short FP64 search from its optimum, so the returned
-// estimate and ell are FP64.
+// Points outside the box score -inf, and so does a non-positive-definite point.  The
+// search runs in two stages.  A coarse Nelder-Mead search (in the requested precision)
+// stops at a simplex of diameter 1e-3 in log-parameters; the simplex is then rebuilt once
+// around the best point and the search resumed (a standard guard against premature
+// collapse).  An FP64 Newton polish on a central-difference quadratic model then takes
+// the estimate to the caller's xtol in a few evaluations; where the model is not convex
+// or a step fails to improve (e.g. an optimum on the box boundary), an FP64 Nelder-Mead
+// search with the caller's tolerances finishes instead.  The returned estimate is the
+// best FP64-scored point, and ell is its FP64 value.
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -127,6 +133,7 @@ struct Objective {
     int hard_error = BV_OK;
     double fbest = INFINITY;
     bv_theta tbest{};
+    std::vector<double> xbest;
 
     void reset(int p) {
         prec = p;
@@ -157,6 +164,7 @@ struct Objective {
         if (-ll < fbest) {
             fbest = -ll;
             tbest = t;
+            xbest = x;
         }
         return -ll;
     }
@@ -244,6 +252,86 @@ int nelder_mead(Objective& f, const Space& S, std::vector<double> x0, double ste
     return BV_OK;
 }
 
+// Cholesky solve of the n x n (n <= 3) system H p = -g; false unless H is positive definite.
+bool newton_step(std::vector<double> H, const std::vector<double>& g, int n, std::vector<double>* p) {
+    for (int j = 0; j < n; ++j) {
+        for (int k = 0; k < j; ++k) H[j * n + j] -= H[j * n + k] * H[j * n + k];
+        if (!(H[j * n + j] > 0.0)) return false;
+        H[j * n + j] = sqrt(H[j * n + j]);
+        for (int i = j + 1; i < n; ++i) {
+            for (int k = 0; k < j; ++k) H[i * n + j] -= H[i * n + k] * H[j * n + k];
+            H[i * n + j] /= H[j * n + j];
+        }
+    }
+    std::vector<double> w(n);
+    for (int i = 0; i < n; ++i) {
+        double v = -g[i];
+        for (int k = 0; k < i; ++k) v -= H[i * n + k] * w[k];
+        w[i] = v / H[i * n + i];
+    }
+    p->assign(n, 0.0);
+    for (int i = n - 1; i >= 0; --i) {
+        double v = w[i];
+        for (int k = i + 1; k < n; ++k) v -= H[k * n + i] * (*p)[k];
+        (*p)[i] = v / H[i * n + i];
+    }
+    return true;
+}
+
+// Newton polish of f from x (f(x) = fx) on a central-difference quadratic model with
+// step h: gradient and Hessian from 1 + 2n + n(n-1)/2 evaluations, a Newton step (at
+// most 0.1 in the sup norm), repeated while it improves f.  True when the last step was
+// within xtol or the model's predicted decrease g^T H^-1 g / 2 was within ftol |f| (the
+// rounding floor of f bounds how well a weakly identified direction can be resolved);
+// false when the model was not convex, a point left the box, a step did not improve f,
+// or the iterations ran out (the caller then falls back to Nelder-Mead).
+bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double* fx, double h, double xtol,
+                   double ftol, int max_evals) {
+    const int n = S.dim;
+    std::vector<double> H(n * n), g(n), fp(n), fm(n), p, y;
+    for (int it = 0; it < 4; ++it) {
+        if (f.evals + 2 + n * (n + 3) / 2 > max_evals) return false;
+        for (int i = 0; i < n; ++i) {
+            y = *x;
+            y[i] += h;
+            fp[i] = f(y);
+            y[i] = (*x)[i] - h;
+            fm[i] = f(y);
+            if (f.hard_error || !std::isfinite(fp[i]) || !std::isfinite(fm[i])) return false;
+            g[i] = (fp[i] - fm[i]) / (2.0 * h);
+            H[i * n + i] = (fp[i] - 2.0 * *fx + fm[i]) / (h * h);
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                y = *x;
+                y[i] += h;
+                y[j] += h;
+                const double fij = f(y);
+                if (f.hard_error || !std::isfinite(fij)) return false;
+                H[i * n + j] = H[j * n + i] = (fij - fp[i] - fp[j] + *fx) / (h * h);
+            }
+        if (!newton_step(H, g, n, &p)) return false;
+        double len = 0.0, pred = 0.0;
+        for (int i = 0; i < n; ++i) {
+            len = std::max(len, fabs(p[i]));
+            pred -= 0.5 * g[i] * p[i];
+        }
+        const double sc = len > 0.1 ? 0.1 / len : 1.0;
+        y = *x;
+        for (int i = 0; i < n; ++i) y[i] += sc * p[i];
+        const double fy = f(y);
+        if (f.hard_error) return false;
+        const bool improved = fy < *fx;
+        if (improved) {
+            *x = y;
+            *fx = fy;
+        }
+        if (len <= xtol || pred <= ftol * fabs(*fx)) return true;
+        if (!improved) return false;
+    }
+    return false;
+}
+
 }  // namespace
 
 extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
@@ -297,17 +385,45 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
         fb = obj(x);
         BV_TRY(obj.hard_error);
     } else {
-        // search, then one restart around the optimum (smaller step)
-        obj.reset(prec);
+        // Coarse search: Nelder-Mead to a simplex of diameter 1e-3 and relative ell spread
+        // 1e-7 (in mixed precision no tighter than ten times its measured error at the
+        // start point), restarted once around the optimum; then, in FP64, a Newton polish
+        // to xtol, or, if that fails, the Nelder-Mead search and restart to the caller's
+        // tolerances.
         const double s0 = opts->init_step, sn = opts->init_step_nugget > 0.0 ? opts->init_step_nugget : s0;
-        const double s1 = std::max(s0 * 0.1, 20.0 * opts->xtol);
-        BV_TRY(nelder_mead(obj, S, x, s0, sn, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
-        BV_TRY(nelder_mead(obj, S, xb, s1, s1, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
-        if (prec == BV_MIXED && std::isfinite(fb)) {
-            // FP64 finish from the mixed-precision optimum
+        double ftol_c = std::max(opts->ftol_rel, 1e-7);
+        const double xtol_c = std::max(opts->xtol, 1e-3);
+        if (prec == BV_MIXED) {
             obj.reset(BV_FP64);
-            const double s2 = std::max(s0 * 0.02, 20.0 * opts->xtol);
-            BV_TRY(nelder_mead(obj, S, xb, s2, s2, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+            const double f64 = obj(x);
+            BV_TRY(obj.hard_error);
+            obj.reset(BV_MIXED);
+            const double f32 = obj(x);
+            BV_TRY(obj.hard_error);
+            const double err = (std::isfinite(f64) && std::isfinite(f32)) ? fabs(f32 - f64) / fabs(f64) : 1e-6;
+            ftol_c = std::max(ftol_c, 10.0 * err);
+        }
+        obj.reset(prec);
+        BV_TRY(nelder_mead(obj, S, x, s0, sn, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
+        const double s1 = std::max(s0 * 0.1, 20.0 * xtol_c);
+        BV_TRY(nelder_mead(obj, S, xb, s1, s1, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
+        if (std::isfinite(fb)) {
+            obj.reset(BV_FP64);
+            fb = obj(xb);
+            BV_TRY(obj.hard_error);
+            const int coarse = obj.evals;
+            bool done = std::isfinite(fb) && newton_polish(obj, S, &xb, &fb, 1e-3, opts->xtol, opts->ftol_rel, opts->max_evals);
+            BV_TRY(obj.hard_error);
+            if (getenv("BV_LOG_MLE"))
+                fprintf(stderr, "bv_mle: coarse search %d evals, Newton polish %s after %d\n", coarse,
+                        done ? "converged" : "fell back", obj.evals - coarse);
+            if (!done) {
+                xb = obj.xbest;
+                const double s2 = std::max(s0 * 0.02, 20.0 * opts->xtol);
+                BV_TRY(nelder_mead(obj, S, xb, s2, s2, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+                const double s3 = std::max(s0 * 0.01, 20.0 * opts->xtol);
+                BV_TRY(nelder_mead(obj, S, xb, s3, s3, opts->ftol_rel, opts->xtol, opts->max_evals, &xb, &fb));
+            }
         }
     }
     if (!std::isfinite(obj.fbest)) {
