@@ -122,3 +122,28 @@ def test_profile_respects_the_box(bv):
         assert 1e-6 * (1 - 1e-12) <= th.nugget <= 10.0 * (1 + 1e-12)
         assert 0.001 <= th.range[0] <= 3.0
         assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)
+
+
+def test_mle_with_all_earlier_points_is_the_exact_mle(bv):
+    # With m >= n every conditioning set holds all earlier points, so the block-Vecchia
+    # likelihood is the exact one (Eq. 2-3) and its maximiser is the exact MLE; here that
+    # is found independently by SciPy's Nelder-Mead on the oracle's Eq. 1.
+    from scipy.optimize import minimize
+    n, nu = 400, 1.5
+    locs = synth.locs_uniform(n, 2, 34)
+    y = oracle.exact_draw(oracle.theta(1.2, 0.08, nu, 2e-2), locs, synth.normal(34, 20, n))
+
+    def negll(x):
+        return -oracle.exact_loglik(oracle.theta(*np.exp(x[:2]), nu, np.exp(x[2])), locs, y)
+
+    r = minimize(negll, np.log([1.0, 0.1, 1e-2]), method="Nelder-Mead",
+                 options=dict(xatol=1e-9, fatol=1e-12, maxiter=4000, maxfev=4000))
+    r = minimize(negll, r.x, method="Nelder-Mead", options=dict(xatol=1e-10, fatol=1e-13, maxfev=4000))
+    lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(40, seed=34)
+        ctx.select_neighbors(10**5)
+        th, ll, _ = ctx.mle(bv.theta(1.0, 0.1, nu, 1e-2), lo, hi, ftol_rel=1e-13, xtol=1e-8)
+    assert abs(ll + r.fun) <= 1e-10 * abs(r.fun), (ll, -r.fun)
+    np.testing.assert_allclose([np.log(th.sigma2), np.log(th.range[0]), np.log(th.nugget)], r.x, atol=2e-3)
