@@ -12,6 +12,9 @@ What each function follows (details in the C source):
   block_loglik / loglik   Algorithm 1 (batched steps, literally) and Eq. 4
   exact_loglik            Eq. 1
   exact_draw / bv_draw    input generators: exact GP draw, block-Vecchia draw (Eq. 4)
+  build_pred_blocks / select_pred_neighbors / predict
+                          Sec. 2.4 + Algorithm 2 (prediction)
+  csim_normal / cond_sim  Sec. 2.4 univariate conditional simulation; PICP (Sec. 3.2)
 """
 from __future__ import annotations
 
@@ -105,6 +108,24 @@ def _bind(L):
             L.or_select_neighbors.restype = _int
             L.or_select_neighbors.argtypes = [_P(_d), _i64, _int, _i64, _P(_i64), _P(_i32),
                                               _P(_d), _i32, _P(_i32), _P(_i64), _P(_i32)]
+            L.or_build_pred_blocks.restype = _i64
+            L.or_build_pred_blocks.argtypes = [_P(_d), _i64, _int, _i64, _u64, _int, _P(_i64),
+                                               _P(_i32), _P(_d)]
+            L.or_select_pred_neighbors.restype = _int
+            L.or_select_pred_neighbors.argtypes = [_P(_d), _i64, _int, _i64, _P(_d), _i32,
+                                                   _P(_i64), _P(_i32)]
+            L.or_predict_block.restype = _int
+            L.or_predict_block.argtypes = [_P(Theta), _P(_d), _P(_d), _int, _P(_i32), _i64,
+                                           _P(_d), _P(_i32), _i64, _P(_d), _P(_d)]
+            L.or_predict.restype = _int
+            L.or_predict.argtypes = [_P(Theta), _P(_d), _P(_d), _i64, _int, _P(_d), _i64,
+                                     _P(_i64), _P(_i32), _P(_i64), _P(_i32), _P(_d), _P(_d),
+                                     _P(_d)]
+            L.or_csim_normal.restype = _d
+            L.or_csim_normal.argtypes = [_u64, _u64]
+            L.or_cond_sim.restype = _int
+            L.or_cond_sim.argtypes = [_P(_d), _P(_d), _i64, _i32, _u64, _d, _P(_d), _P(_d),
+                                      _P(_d), _P(_i64)]
             L.or_num_threads.restype = _int
             L.or_num_threads.argtypes = []
     return L
@@ -289,3 +310,89 @@ def bv_draw(th: Theta, locs, block_ptr, point_idx, nn_ptr, nn_idx, z):
     if st:
         raise OracleError(st, "bv_draw")
     return y
+
+
+def build_pred_blocks(locs_star, bc, seed, iters=20):
+    """Algorithm 2 clustering of the new locations: (block_ptr, point_idx, centroids),
+    blocks in cluster-index order."""
+    ls = _c(locs_star, np.float64)
+    n, d = ls.shape
+    bp = np.empty(bc + 1, np.int64)
+    pi = np.empty(n, np.int32)
+    ce = np.empty((bc, d), np.float64)
+    nb = lib().or_build_pred_blocks(_ptr(ls, _d), n, d, bc, seed, iters, _ptr(bp, _i64),
+                                    _ptr(pi, _i32), _ptr(ce, _d))
+    if nb < 0:
+        raise OracleError(-nb, "build_pred_blocks")
+    return bp[:nb + 1].copy(), pi, ce[:nb].copy()
+
+
+def select_pred_neighbors(locs, centroids, m):
+    """The min(m, n) observations nearest to each prediction block's centroid."""
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    ce = _c(centroids, np.float64).reshape(-1, d)
+    bc = ce.shape[0]
+    nnp = np.empty(bc + 1, np.int64)
+    mi = min(int(m), n)
+    nni = np.empty(max(bc * mi, 1), np.int32)
+    st = lib().or_select_pred_neighbors(_ptr(locs, _d), n, d, bc, _ptr(ce, _d), int(m),
+                                        _ptr(nnp, _i64), _ptr(nni, _i32))
+    if st:
+        raise OracleError(st, "select_pred_neighbors")
+    return nnp, nni[:int(nnp[-1])].copy()
+
+
+def predict_block(th: Theta, locs, y, nn, locs_star, blk):
+    """One block of Algorithm 2: (mean[b], Sigma_B[b x b])."""
+    locs, y, ls = _c(locs, np.float64), _c(y, np.float64), _c(locs_star, np.float64)
+    m = len(nn)
+    nn = _c(nn, np.int32) if m else np.zeros(1, np.int32)
+    blk = _c(blk, np.int32)
+    b = blk.size
+    mean = np.empty(b)
+    cov = np.empty((b, b))
+    st = lib().or_predict_block(ctypes.byref(th), _ptr(locs, _d), _ptr(y, _d), locs.shape[1],
+                                _ptr(nn, _i32), m, _ptr(ls, _d), _ptr(blk, _i32), b,
+                                _ptr(mean, _d), _ptr(cov, _d))
+    if st:
+        raise OracleError(st, "predict_block")
+    return mean, cov
+
+
+def predict(th: Theta, locs, y, locs_star, block_ptr, point_idx, nn_ptr, nn_idx, packed_cov=False):
+    """Algorithm 2: (mean[n*], var[n*], packed per-block Sigma_B or None)."""
+    locs, y, ls = _c(locs, np.float64), _c(y, np.float64), _c(locs_star, np.float64)
+    n, d = locs.shape
+    bp, pi = _c(block_ptr, np.int64), _c(point_idx, np.int32)
+    nnp = _c(nn_ptr, np.int64)
+    nni = _c(nn_idx, np.int32) if len(nn_idx) else np.zeros(1, np.int32)
+    ns = ls.shape[0]
+    mean, var = np.empty(ns), np.empty(ns)
+    b = np.diff(bp)
+    cov = np.empty(max(int(np.sum(b * (b + 1) // 2)), 1)) if packed_cov else None
+    st = lib().or_predict(ctypes.byref(th), _ptr(locs, _d), _ptr(y, _d), n, d, _ptr(ls, _d),
+                          bp.size - 1, _ptr(bp, _i64), _ptr(pi, _i32), _ptr(nnp, _i64),
+                          _ptr(nni, _i32), _ptr(mean, _d), _ptr(var, _d), _ptr(cov, _d))
+    if st:
+        raise OracleError(st, "predict")
+    return mean, var, cov
+
+
+def csim_normal(seed: int, counter: int) -> float:
+    """Standard normal number `counter` of the conditional-simulation stream."""
+    return float(lib().or_csim_normal(seed, counter))
+
+
+def cond_sim(mean, var, rounds, seed, z_crit, y_true=None):
+    """Univariate conditional simulation: (lower[n*], upper[n*], covered count)."""
+    mean, var = _c(mean, np.float64), _c(var, np.float64)
+    yt = _c(y_true, np.float64) if y_true is not None else None
+    ns = mean.size
+    lo, up = np.empty(ns), np.empty(ns)
+    cov = np.zeros(1, np.int64)
+    st = lib().or_cond_sim(_ptr(mean, _d), _ptr(var, _d), ns, int(rounds), seed, float(z_crit),
+                           _ptr(yt, _d), _ptr(lo, _d), _ptr(up, _d), _ptr(cov, _i64))
+    if st:
+        raise OracleError(st, "cond_sim")
+    return lo, up, int(cov[0])

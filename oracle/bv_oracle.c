@@ -19,6 +19,9 @@
  *     (POTRF, TRSM, TRSV, GEMM, GEMV, elementwise update, POTRF, TRSV, dot, log-det)
  *     and the final sum.
  *   - Exact GP log-likelihood, Eq. 1, by a dense Cholesky.
+ *   - Prediction (Sec. 2.4, Algorithm 2): blocks of the new locations, their nearest
+ *     observations, conditional means and covariances; univariate conditional
+ *     simulation and the prediction interval coverage (Sec. 3.2).
  *   - Input generators built from the same definitions: an exact GP draw and the
  *     block-Vecchia draw (Eq. 4 read generatively).
  *
@@ -697,6 +700,248 @@ int or_select_neighbors(const double* locs, int64_t n, int d, int64_t bc,
         free(h);
     }
     return fail;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Prediction (Sec. 2.4 "Block Vecchia Prediction", Algorithm 2).
+ *
+ * Clustering g: the new locations S* are split into blocks by the same K-means as
+ * Algorithm 1 (same seeding, iterations and exact-integer conventions).  Algorithm 2 has
+ * no block permutation (prediction blocks do not condition on one another), so blocks
+ * keep cluster-index order, empty clusters dropped, members ascending, and the centroid
+ * is the exact-integer mean of the members.
+ * ---------------------------------------------------------------------------------- */
+int64_t or_build_pred_blocks(const double* locs_star, int64_t n_star, int d, int64_t bc,
+                             uint64_t seed, int iters, int64_t* block_ptr, int32_t* point_idx,
+                             double* centroids) {
+    int32_t* label = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_star);
+    double* cent = (double*)malloc(sizeof(double) * (size_t)(bc * d));
+    int64_t* counts = (int64_t*)calloc((size_t)bc, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)bc + 1, sizeof(int64_t));
+    int64_t* blk_of = (int64_t*)malloc(sizeof(int64_t) * (size_t)bc);
+    if (!label || !cent || !counts || !fill || !blk_of) {
+        free(label); free(cent); free(counts); free(fill); free(blk_of);
+        return -OR_ENOMEM;
+    }
+    int st = or_kmeans(locs_star, n_star, d, bc, seed, iters, label, cent);
+    if (st != OR_OK) { free(label); free(cent); free(counts); free(fill); free(blk_of); return -st; }
+    int s = 0, q = 0;
+    or_kmeans_scales(locs_star, n_star, d, &s, &q);
+    or_update(locs_star, n_star, d, label, bc, q, cent, counts);
+    int64_t nb = 0;
+    block_ptr[0] = 0;
+    for (int64_t c = 0; c < bc; c++) {
+        blk_of[c] = -1;
+        if (counts[c] == 0) continue;
+        blk_of[c] = nb;
+        block_ptr[nb + 1] = block_ptr[nb] + counts[c];
+        for (int j = 0; j < d; j++) centroids[nb * d + j] = cent[c * d + j];
+        nb++;
+    }
+    for (int64_t i = 0; i < n_star; i++) {
+        int64_t p = blk_of[label[i]];
+        point_idx[block_ptr[p] + fill[p]++] = (int32_t)i;
+    }
+    free(label); free(cent); free(counts); free(fill); free(blk_of);
+    return nb;
+}
+
+/* Algorithm 2 "Nearest neighbors": for prediction block i the candidates are all n
+ * observations; the query is the block centroid; key (D2, index) as in Algorithm 1; the
+ * conditioning set is the min(m, n) smallest keys in ascending key order. */
+int or_select_pred_neighbors(const double* locs, int64_t n, int d, int64_t bc,
+                             const double* centroids, int32_t m, int64_t* nn_ptr,
+                             int32_t* nn_idx) {
+    if (m < 0) return OR_EINVAL;
+    const int64_t mi = m < n ? m : n;
+    nn_ptr[0] = 0;
+    for (int64_t i = 0; i < bc; i++) nn_ptr[i + 1] = nn_ptr[i] + mi;
+    if (!nn_idx || mi == 0) return OR_OK;
+    int fail = OR_OK;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < bc; i++) {
+        or_key* h = (or_key*)malloc(sizeof(or_key) * (size_t)mi);
+        if (!h) { fail = OR_ENOMEM; continue; }
+        int64_t sz = 0;
+        const double* qc = centroids + i * d;
+        for (int64_t j = 0; j < n; j++) {
+            or_key key;
+            key.idx = (int32_t)j;
+            key.d2 = or_d2(qc, locs + j * d, d);
+            if (sz < mi) {
+                h[sz] = key;
+                or_heap_sift_up(h, sz);
+                sz++;
+            } else if (or_key_less(key, h[0])) {
+                h[0] = key;
+                or_heap_sift_down(h, sz, 0);
+            }
+        }
+        qsort(h, (size_t)sz, sizeof(or_key), or_key_cmp);
+        for (int64_t t = 0; t < sz; t++) nn_idx[nn_ptr[i] + t] = h[t].idx;
+        free(h);
+    }
+    return fail;
+}
+
+/* Solve Sigma x = b with the Cholesky factor L of Sigma (forward, then backward
+ * substitution with L^T). */
+static void or_chol_solve(const double* L, int64_t n, const double* b, double* x) {
+    for (int64_t i = 0; i < n; i++) {
+        double t = b[i];
+        for (int64_t k = 0; k < i; k++) t -= L[i * n + k] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; i--) {
+        double t = x[i];
+        for (int64_t k = i + 1; k < n; k++) t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+}
+
+/* One prediction block, literally Algorithm 2:
+ *   Sigma^con = cov(S_NN, S_NN), Sigma^cross = cov(S_NN, S_B*) (m x b), Sigma^lk =
+ *   cov(S_B*, S_B*) with the nugget on the diagonal (a new location is its own point and
+ *   is never the same point as an observation);
+ *   mu = Sigma^cross^T (Sigma^con)^{-1} y_NN;
+ *   Sigma_B = Sigma^lk - Sigma^cross^T (Sigma^con)^{-1} Sigma^cross.
+ * mean[b] and cov[b x b] (row-major) are outputs. */
+int or_predict_block(const or_theta* th, const double* locs, const double* y, int d,
+                     const int32_t* nn, int64_t m, const double* locs_star, const int32_t* blk,
+                     int64_t b, double* mean, double* cov) {
+    double* Scon = (double*)calloc((size_t)(m * m + 1), sizeof(double));
+    double* Scross = (double*)calloc((size_t)(m * b + 1), sizeof(double));
+    double* W = (double*)calloc((size_t)(m * b + 1), sizeof(double));
+    double* rhs = (double*)calloc((size_t)(m + 1), sizeof(double));
+    double* x = (double*)calloc((size_t)(m + 1), sizeof(double));
+    int st = OR_OK;
+    if (!Scon || !Scross || !W || !rhs || !x) { st = OR_ENOMEM; goto done; }
+    for (int64_t j = 0; j < b; j++)
+        for (int64_t k = 0; k < b; k++)
+            cov[j * b + k] = or_cov(th, d, locs_star + (int64_t)blk[j] * d,
+                                    locs_star + (int64_t)blk[k] * d, blk[j] == blk[k]);
+    for (int64_t j = 0; j < b; j++) mean[j] = 0.0;
+    if (m == 0) goto done;
+    for (int64_t j = 0; j < m; j++)
+        for (int64_t k = 0; k < m; k++)
+            Scon[j * m + k] = or_cov(th, d, locs + (int64_t)nn[j] * d, locs + (int64_t)nn[k] * d,
+                                     nn[j] == nn[k]);
+    for (int64_t j = 0; j < m; j++)
+        for (int64_t k = 0; k < b; k++)
+            Scross[j * b + k] = or_cov(th, d, locs + (int64_t)nn[j] * d,
+                                       locs_star + (int64_t)blk[k] * d, 0);
+    if (or_potrf(Scon, m) != OR_OK) { st = OR_ENOTPD; goto done; }
+    /* (Sigma^con)^{-1} y_NN, then mu = Sigma^cross^T times it */
+    for (int64_t j = 0; j < m; j++) rhs[j] = y[nn[j]];
+    or_chol_solve(Scon, m, rhs, x);
+    for (int64_t k = 0; k < b; k++) {
+        double t = 0.0;
+        for (int64_t j = 0; j < m; j++) t += Scross[j * b + k] * x[j];
+        mean[k] = t;
+    }
+    /* W = (Sigma^con)^{-1} Sigma^cross, column by column; Sigma_B = Sigma^lk - Sigma^cross^T W */
+    for (int64_t k = 0; k < b; k++) {
+        for (int64_t j = 0; j < m; j++) rhs[j] = Scross[j * b + k];
+        or_chol_solve(Scon, m, rhs, x);
+        for (int64_t j = 0; j < m; j++) W[j * b + k] = x[j];
+    }
+    for (int64_t r = 0; r < b; r++)
+        for (int64_t c = 0; c < b; c++) {
+            double t = 0.0;
+            for (int64_t j = 0; j < m; j++) t += Scross[j * b + r] * W[j * b + c];
+            cov[r * b + c] -= t;
+        }
+done:
+    free(Scon); free(Scross); free(W); free(rhs); free(x);
+    return st;
+}
+
+/* Algorithm 2 over all blocks: mean[n_star] and var[n_star] (the diagonal of the block's
+ * Sigma_B) by new-location index; cov_packed (optional) receives each block's Sigma_B
+ * lower triangle, row by row, blocks in order (sum_i b_i (b_i + 1) / 2 entries). */
+int or_predict(const or_theta* th, const double* locs, const double* y, int64_t n, int d,
+               const double* locs_star, int64_t bc, const int64_t* block_ptr,
+               const int32_t* point_idx, const int64_t* nn_ptr, const int32_t* nn_idx,
+               double* mean, double* var, double* cov_packed) {
+    (void)n;
+    if (!or_theta_valid(th, d)) return OR_EINVAL;
+    int fail = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < bc; i++) {
+        const int64_t b = block_ptr[i + 1] - block_ptr[i];
+        const int32_t* blk = point_idx + block_ptr[i];
+        double* mu = (double*)malloc(sizeof(double) * (size_t)(b + 1));
+        double* C = (double*)malloc(sizeof(double) * (size_t)(b * b + 1));
+        int st = (mu && C) ? or_predict_block(th, locs, y, d, nn_idx + nn_ptr[i], nn_ptr[i + 1] - nn_ptr[i],
+                                              locs_star, blk, b, mu, C)
+                           : OR_ENOMEM;
+        if (st == OR_OK) {
+            for (int64_t j = 0; j < b; j++) {
+                mean[blk[j]] = mu[j];
+                var[blk[j]] = C[j * b + j];
+            }
+            if (cov_packed) {
+                int64_t off = 0;
+                /* packed offset: sum over earlier blocks of b_k (b_k + 1) / 2 */
+                for (int64_t k = 0; k < i; k++) {
+                    const int64_t bk = block_ptr[k + 1] - block_ptr[k];
+                    off += bk * (bk + 1) / 2;
+                }
+                for (int64_t r = 0; r < b; r++)
+                    for (int64_t c = 0; c <= r; c++) cov_packed[off + r * (r + 1) / 2 + c] = C[r * b + c];
+            }
+        } else {
+#pragma omp critical
+            if (fail == OR_OK) fail = st;
+        }
+        free(mu); free(C);
+    }
+    return fail;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Univariate conditional simulation and the prediction interval (Sec. 2.4, last
+ * paragraph; PICP of Sec. 3.2).  For new location i, draw r = 0 .. R-1 is
+ * y_ir = mean_i + sqrt(var_i) z_ir with z_ir standard normal by the Box-Muller transform
+ * (Box and Muller 1958) of two SplitMix64 uniforms:
+ *   c = i R + r, u1 = 1 - (x_{2c} >> 11) 2^-53, u2 = (x_{2c+1} >> 11) 2^-53,
+ *   z = sqrt(-2 ln u1) cos(2 pi u2),   x_k = draw k of stream seed ^ "condsim_".
+ * The sample mean and the sample variance (divisor R - 1) of the draws give the interval
+ * [mean~ - z_crit sd~, mean~ + z_crit sd~]; covered counts the held-out values inside it.
+ * ---------------------------------------------------------------------------------- */
+#define OR_STREAM_CSIM(seed) ((seed) ^ 0x636f6e6473696d5fULL) /* "condsim_" */
+
+double or_csim_normal(uint64_t seed, uint64_t c) {
+    const uint64_t st = OR_STREAM_CSIM(seed);
+    const double u1 = 1.0 - (double)(or_sm64(st, 2 * c) >> 11) * 0x1p-53;
+    const double u2 = (double)(or_sm64(st, 2 * c + 1) >> 11) * 0x1p-53;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+int or_cond_sim(const double* mean, const double* var, int64_t n_star, int32_t rounds,
+                uint64_t seed, double z_crit, const double* y_true, double* lower, double* upper,
+                int64_t* covered) {
+    if (rounds < 2 || n_star < 0) return OR_EINVAL;
+    int64_t cov_count = 0;
+#pragma omp parallel for schedule(static) reduction(+ : cov_count)
+    for (int64_t i = 0; i < n_star; i++) {
+        const double sd = sqrt(var[i] > 0.0 ? var[i] : 0.0);
+        double sum = 0.0;
+        for (int32_t r = 0; r < rounds; r++)
+            sum += mean[i] + sd * or_csim_normal(seed, (uint64_t)i * (uint64_t)rounds + (uint64_t)r);
+        const double mt = sum / (double)rounds;
+        double ss = 0.0;
+        for (int32_t r = 0; r < rounds; r++) {
+            const double e = mean[i] + sd * or_csim_normal(seed, (uint64_t)i * (uint64_t)rounds + (uint64_t)r) - mt;
+            ss += e * e;
+        }
+        const double st = sqrt(ss / (double)(rounds - 1));
+        lower[i] = mt - z_crit * st;
+        upper[i] = mt + z_crit * st;
+        if (y_true && y_true[i] >= lower[i] && y_true[i] <= upper[i]) cov_count++;
+    }
+    if (covered) *covered = cov_count;
+    return OR_OK;
 }
 
 int or_num_threads(void) {

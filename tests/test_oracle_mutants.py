@@ -30,6 +30,14 @@ MUTANTS = {
                                            "if (t <= best) { best = t; bi = (int32_t)c; }"),
     "centroid without the 2^-q scaling": ("cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q);",
                                           "cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q + 1);"),
+    "prediction cross-covariance with the nugget": (
+        "locs_star + (int64_t)blk[k] * d, 0);", "locs_star + (int64_t)blk[k] * d, 1);"),
+    "prediction covariance plus the correction": ("cov[r * b + c] -= t;", "cov[r * b + c] += t;"),
+    "backward substitution skipped": ("for (int64_t i = n - 1; i >= 0; i--) {\n        double t = x[i];",
+                                      "for (int64_t i = n - 1; i >= n; i--) {\n        double t = x[i];"),
+    "prediction neighbour keys shifted by one index": (
+        "key.idx = (int32_t)j;", "key.idx = (int32_t)(j > 0 ? j - 1 : 0);"),
+    "Box-Muller radius without the factor 2": ("sqrt(-2.0 * log(u1))", "sqrt(-1.0 * log(u1))"),
 }
 
 
@@ -113,7 +121,37 @@ def _pin_kmeans_tie():
     raise AssertionError("no seed puts the centres at both ends")
 
 
-PINS = {"matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
+def _pin_kriging():
+    n, locs, S, y, th = _setup()
+    lo, ls = locs[:200], locs[200:]
+    bp, pi, ce = oracle.build_pred_blocks(ls, 4, seed=5)
+    nnp, nni = oracle.select_pred_neighbors(lo, ce, 10**6)
+    mean, var, _ = oracle.predict(th, lo, y[:200], ls, bp, pi, nnp, nni)
+    Syy, Sxy = S[:200, :200], S[200:, :200]
+    kc = S[200:, 200:] - Sxy @ np.linalg.solve(Syy, Sxy.T)
+    return (np.allclose(mean, Sxy @ np.linalg.solve(Syy, y[:200]), rtol=1e-8, atol=1e-9)
+            and np.allclose(var, np.diag(kc), rtol=1e-8, atol=1e-10))
+
+
+def _pin_pred_neighbours():
+    lat = _lattice()
+    ce = np.array([[0.33, 0.71], [0.95, 0.95], [0.0, 0.0]])
+    nnp, nni = oracle.select_pred_neighbors(lat, ce, 7)
+    for i, c in enumerate(ce):
+        d2 = ((lat - c) ** 2).sum(axis=1)
+        if not np.array_equal(nni[nnp[i]:nnp[i + 1]], np.lexsort((np.arange(len(lat)), d2))[:7]):
+            return False
+    return True
+
+
+def _pin_csim_normal():
+    from scipy import stats
+    z = np.array([oracle.csim_normal(9, c) for c in range(20000)])
+    return stats.kstest(z, "norm").pvalue > 1e-3
+
+
+PINS = {"kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
+        "conditional-simulation normals": _pin_csim_normal, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
         "K-means exact tie": _pin_kmeans_tie}
 
