@@ -254,6 +254,54 @@ int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_the
            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
            double* loglik_hat, int32_t* n_evals);
 
+/* ---- prediction (Sec. 2.4, Algorithm 2) ----------------------------------------- */
+
+/* New locations S* (n_star x d, row-major, host; d as set by bv_set_data) and optionally
+ * the held-out values there (host, n_star, may be NULL), against which bv_cond_sim
+ * counts coverage.  Copied in; replaces any earlier prediction set.  Needs one dataset. */
+int bv_set_pred_locations(bv_ctx* ctx, const double* locs_star, const double* y_true, int64_t n_star);
+
+/* Algorithm 2 "Clustering": K-means blocks of S* with the conventions of
+ * bv_build_blocks (seeding, iterations, exact-integer centroids), empty clusters dropped,
+ * blocks in cluster-index order (no permutation: prediction blocks do not condition on
+ * one another), members ascending.  Outputs as bv_build_blocks (indices into S*). */
+int bv_build_pred_blocks(bv_ctx* ctx, int64_t bc, uint64_t seed, int32_t lloyd_iters,
+                         int64_t* block_ptr, int32_t* point_idx, int64_t* bc_eff);
+
+/* Algorithm 2 "Nearest neighbors": for each prediction block the min(m, n) observations
+ * nearest to its centroid, key (squared distance, index) as bv_select_neighbors, from ALL
+ * n observations.  min(m, n) <= 4000.  Outputs (may be NULL): nn_ptr[nb+1], nn_idx. */
+int bv_select_pred_neighbors(bv_ctx* ctx, int32_t m, int64_t* nn_ptr, int32_t* nn_idx);
+
+/* n_star, prediction blocks, conditioning entries, packed covariance entries
+ * (sum_i b_i (b_i + 1) / 2); any pointer may be NULL. */
+int bv_get_pred_sizes(bv_ctx* ctx, int64_t* n_star, int64_t* nblk, int64_t* n_nn, int64_t* n_cov);
+
+/* Conditional means mu = Sigma^cross (Sigma^con)^-1 y_NN and covariances Sigma_B =
+ * Sigma^lk - Sigma^cross (Sigma^con)^-1 Sigma^cross^T of every prediction block, in FP64
+ * (Algorithm 2), with the observations of bv_set_data and the nugget on the diagonal of
+ * Sigma^lk (a new location is its own point).  Host outputs, each may be NULL (results
+ * stay on the device for bv_cond_sim): mean[n_star] and var[n_star] (diag Sigma_B) by
+ * new-location index; cov_packed[n_cov]: each block's Sigma_B lower triangle row by row,
+ * blocks in order.  BV_ENOTPD if a Sigma^con is not positive definite (its block's
+ * outputs are NaN).  Synchronous. */
+int bv_predict(bv_ctx* ctx, const bv_theta* theta, double* mean, double* var, double* cov_packed);
+
+/* Univariate conditional simulation from the last bv_predict (Sec. 2.4): for each new
+ * location `rounds` draws mean + sqrt(var) z, z standard normal by Box-Muller of two
+ * SplitMix64 uniforms (stream seed ^ 0x636f6e6473696d5f, draw pair c = j * rounds + r:
+ * u1 = 1 - (x_2c >> 11) 2^-53, u2 = (x_2c+1 >> 11) 2^-53, z = sqrt(-2 ln u1) cos(2 pi u2));
+ * the interval is sample mean -/+ z_crit * sample sd (divisor rounds - 1).  Outputs
+ * (host, may be NULL): lower[n_star], upper[n_star], covered = number of held-out values
+ * inside their interval (PICP = covered / n_star; -1 without held-out values).
+ * rounds >= 2.  Synchronous. */
+int bv_cond_sim(bv_ctx* ctx, int32_t rounds, uint64_t seed, double z_crit, double* lower,
+                double* upper, int64_t* covered);
+
+/* Algorithmic work of one bv_predict: flops of the partial factorisations and covariance
+ * evaluations. */
+int bv_pred_plan_info(bv_ctx* ctx, double* flops, double* cov_evals);
+
 /* ---- learned warm start --------------------------------------------------------- */
 
 /* The paper suggests warm-starting the estimation from a cheaper fit (Sec. 2.3: estimate

@@ -91,6 +91,13 @@ _SIGS = {
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
                       _P(bv_theta), _P(_d), _P(_i32)]),
+    "bv_set_pred_locations": (_int, [_vp, _P(_d), _P(_d), _i64]),
+    "bv_build_pred_blocks": (_int, [_vp, _i64, _u64, _i32, _P(_i64), _P(_i32), _P(_i64)]),
+    "bv_select_pred_neighbors": (_int, [_vp, _i32, _P(_i64), _P(_i32)]),
+    "bv_get_pred_sizes": (_int, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]),
+    "bv_predict": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d), _P(_d)]),
+    "bv_cond_sim": (_int, [_vp, _i32, _u64, _d, _P(_d), _P(_d), _P(_i64)]),
+    "bv_pred_plan_info": (_int, [_vp, _P(_d), _P(_d)]),
     "bv_features": (_int, [_vp, _i32, _u64, _P(_f)]),
     "bv_mlp_train": (_int, [_P(_f), _P(_f), _i64, _i32, _i32, _f, _u64, _P(_f), _P(_f)]),
     "bv_mlp_forward": (_int, [_P(_f), _P(_f), _i64, _P(_f)]),
@@ -303,6 +310,60 @@ class Context:
         if per_block:
             return out.value, per, st
         return out.value
+
+    # ---- prediction (Algorithm 2) ----
+    def set_pred_locations(self, locs_star, y_true=None):
+        ls = _arr(locs_star, np.float64)
+        yt = _arr(y_true, np.float64) if y_true is not None else None
+        _check(_lib.bv_set_pred_locations(self.h, _p(ls, _d), _p(yt, _d), ls.shape[0]), "bv_set_pred_locations")
+        self.n_star = ls.shape[0]
+
+    def build_pred_blocks(self, bc, seed=0, iters=20):
+        bp = np.empty(bc + 1, np.int64)
+        pi = np.empty(self.n_star, np.int32)
+        nb = ctypes.c_int64(0)
+        _check(_lib.bv_build_pred_blocks(self.h, bc, seed, iters, _p(bp, _i64), _p(pi, _i32), ctypes.byref(nb)),
+               "bv_build_pred_blocks")
+        return bp[:nb.value + 1].copy(), pi
+
+    def pred_sizes(self):
+        v = [ctypes.c_int64(0) for _ in range(4)]
+        _check(_lib.bv_get_pred_sizes(self.h, *[ctypes.byref(x) for x in v]), "bv_get_pred_sizes")
+        return tuple(x.value for x in v)
+
+    def select_pred_neighbors(self, m):
+        _check(_lib.bv_select_pred_neighbors(self.h, int(m), None, None), "bv_select_pred_neighbors")
+        _, nb, nn, _ = self.pred_sizes()
+        nnp = np.empty(nb + 1, np.int64)
+        nni = np.empty(max(nn, 1), np.int32)
+        _check(_lib.bv_select_pred_neighbors(self.h, int(m), _p(nnp, _i64), _p(nni, _i32)),
+               "bv_select_pred_neighbors")
+        return nnp, nni[:nn].copy()
+
+    def predict(self, th: bv_theta, want=("mean", "var"), packed_cov=False, allow_notpd=False):
+        """(mean, var, packed covariance or None); want=() keeps results on the device."""
+        ns, _, _, ncov = self.pred_sizes()
+        mean = np.empty(ns) if "mean" in want else None
+        var = np.empty(ns) if "var" in want else None
+        cov = np.empty(max(ncov, 1)) if packed_cov else None
+        _check(_lib.bv_predict(self.h, ctypes.byref(th), _p(mean, _d), _p(var, _d), _p(cov, _d)), "bv_predict",
+               allow=(BV_ENOTPD,) if allow_notpd else ())
+        return mean, var, (cov[:ncov] if cov is not None else None)
+
+    def cond_sim(self, rounds=1000, seed=0, z_crit=1.959963984540054, bounds=True):
+        """(lower, upper, covered); covered is -1 without held-out values."""
+        ns = self.pred_sizes()[0]
+        lo = np.empty(ns) if bounds else None
+        up = np.empty(ns) if bounds else None
+        cov = ctypes.c_int64(0)
+        _check(_lib.bv_cond_sim(self.h, int(rounds), seed, float(z_crit), _p(lo, _d), _p(up, _d),
+                                ctypes.byref(cov)), "bv_cond_sim")
+        return lo, up, cov.value
+
+    def pred_plan_info(self):
+        f, e = ctypes.c_double(0), ctypes.c_double(0)
+        _check(_lib.bv_pred_plan_info(self.h, ctypes.byref(f), ctypes.byref(e)), "bv_pred_plan_info")
+        return f.value, e.value
 
     def loglik_terms(self, th: bv_theta, precision=BV_FP64):
         """(ell, quad, logdet) with ell = -(quad + logdet + n log 2 pi) / 2."""

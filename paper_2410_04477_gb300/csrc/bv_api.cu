@@ -87,6 +87,7 @@ static void free_blocks(bv_ctx* c) {
 }
 
 static void free_data(bv_ctx* c) {
+    bv_pred_free(c);
     free_blocks(c);
     dfree(c->d_locs);
     dfree(c->d_y);

@@ -119,6 +119,9 @@ int bv_select_neighbors_device(const double* d_locs_soa, int64_t n_tot, int d,
                                const int64_t* h_nptr, int64_t* d_nptr, int32_t* d_nidx,
                                double amax, cudaStream_t s);
 
+int bv_select_pred_neighbors_device(const double* d_locs, int64_t n_tot, int d, const double* d_qcent, int64_t nq,
+                                    const int64_t* d_nptr, int32_t* d_nidx, double amax, cudaStream_t s);
+
 // Block-Vecchia sampler (bv_sim.cu).
 int bv_simulate_device(bv_ctx* ctx, const DevTheta& th, const double* d_z, double* d_y);
 
@@ -131,6 +134,7 @@ __host__ __device__ inline uint64_t bv_sm64(uint64_t stream, uint64_t counter) {
 }
 #define BV_STREAM_KPP(seed) ((seed) ^ 0x6b6d65616e732b2bull)
 #define BV_STREAM_ZETA(seed) ((seed) ^ 0x7a6574615f6f7264ull)
+#define BV_STREAM_CSIM(seed) ((seed) ^ 0x636f6e6473696d5full)
 
 // ------------------------------------------------------------------------------------
 // The context
@@ -198,7 +202,13 @@ struct bv_ctx {
     // warm start
     std::vector<float> mlp_w;
     bool have_mlp = false;
+
+    // prediction (bv_pred.cu)
+    struct PredState* pred = nullptr;
 };
+
+// prediction state teardown (bv_pred.cu); also called when the observations change
+void bv_pred_free(bv_ctx* ctx);
 
 // helpers in bv_api.cu
 int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* out);

@@ -2,7 +2,8 @@
 // neighbors").
 //
 // Definition (fixed by this library, identical to the plain brute-force rule): for the
-// block at position i of the order, the candidates are all points of blocks 0..i-1; the
+// block at position i of the order, the candidates are all points of blocks 0..i-1 (for a
+// prediction block, Algorithm 2: all observations); the
 // query is the block centroid c_i; the key of candidate j is (D2(c_i, s_j), j), D2 being
 // the squared distance summed left to right without fused multiply-add; the conditioning
 // set is the m_i smallest keys, ascending.  Positive doubles order like their bit
@@ -122,8 +123,9 @@ __device__ int find_bin(const unsigned int* hist, int nb, unsigned int need, uns
 struct NNArgs {
     const float* xs32;    // [d][P_all] FP32 coordinates in block order, from `base`
     const double* xs64;   // [d][P_all] FP64 coordinates in block order, from `base`
-    const int32_t* pord;  // point index in block order (slice)
+    const int32_t* pord;  // point index in block order (slice); null: candidate p is point base + p
     int64_t P_all;
+    int64_t fixed_P;      // >= 0: every query ranks the first fixed_P candidates (prediction)
     int d;
     const int64_t* bptr;  // global block ptr
     int64_t base;         // bptr[blk_begin]
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(kNT) k_select(NNArgs a) {
     unsigned int* scan = hist + 4096;                                         // kNT
     __shared__ int s_cnt;
     const int64_t blk = a.blk_begin + blockIdx.x;
-    const int64_t P = a.bptr[blk] - a.base;
+    const int64_t P = a.fixed_P >= 0 ? a.fixed_P : a.bptr[blk] - a.base;
+    auto gidx = [&](int64_t p) -> int { return a.pord ? a.pord[a.base + p] : (int)(a.base + p); };
     const int64_t out0 = a.nptr[blk];
     const int mi = (int)(a.nptr[blk + 1] - out0);
     if (mi == 0) return;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kNT) k_select(NNArgs a) {
     if (P <= kCap) {
         for (int64_t p = threadIdx.x; p < P; p += kNT) {
             key[p] = k64(p);
-            idx[p] = a.pord[a.base + p];
+            idx[p] = gidx(p);
         }
         count = (int)P;
     } else {
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kNT) k_select(NNArgs a) {
                 const int slot = atomicAdd(&s_cnt, 1);
                 if (slot < kCap) {
                     key[slot] = k64(p);
-                    idx[slot] = a.pord[a.base + p];
+                    idx[slot] = gidx(p);
                 }
             }
         }
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kNT) k_select(NNArgs a) {
                 for (int64_t p = threadIdx.x; p < P; p += kNT) {
                     if (!(d32(p) <= thr)) continue;
                     const unsigned long long kk = k64(p);
-                    const unsigned int ii = (unsigned)a.pord[a.base + p];
+                    const unsigned int ii = (unsigned)gidx(p);
                     if ((kk & pmask) != pk || (ii & pimask) != pidx) continue;
                     const unsigned int digit = pass < 8 ? (unsigned)(kk >> (56 - 8 * pass)) & 255u
                                                         : (ii >> (24 - 8 * (pass - 8))) & 255u;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kNT) k_select(NNArgs a) {
             for (int64_t p = threadIdx.x; p < P; p += kNT) {
                 if (!(d32(p) <= thr)) continue;
                 const unsigned long long kk = k64(p);
-                const int ii = a.pord[a.base + p];
+                const int ii = gidx(p);
                 if (!key_less(pk, (int)pidx, kk, ii)) {
                     const int slot = atomicAdd(&s_cnt, 1);
                     if (slot < kCap) {
@@ -285,7 +288,7 @@ __global__ void k_gather_order(const double* __restrict__ locs, int64_t n_tot, i
                                float* __restrict__ xs32, double* __restrict__ xs64) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= P_all) return;
-    const int64_t g = pidx[base + p];
+    const int64_t g = pidx ? pidx[base + p] : base + p;
     for (int k = 0; k < d; ++k) {
         const double v = locs[(int64_t)k * n_tot + g];
         xs64[(int64_t)k * P_all + p] = v;
@@ -325,6 +328,7 @@ int bv_select_neighbors_device(const double* d_locs, int64_t n_tot, int d, const
     a.xs64 = xs64;
     a.pord = d_pidx;
     a.P_all = P_all;
+    a.fixed_P = -1;
     a.d = d;
     a.bptr = d_bptr;
     a.base = base;
@@ -338,6 +342,47 @@ int bv_select_neighbors_device(const double* d_locs, int64_t n_tot, int d, const
                         sizeof(unsigned int) * (4096 + kNT);
     BV_CUDA(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t nq = blk_end - blk_begin;
+    k_select<<<(unsigned)nq, kNT, smem, s>>>(a);
+    BV_CUDA(cudaGetLastError());
+    BV_CUDA(cudaFreeAsync(xs32, s));
+    BV_CUDA(cudaFreeAsync(xs64, s));
+    BV_CUDA(cudaFreeAsync(ovf, s));
+    return BV_OK;
+}
+
+// Prediction (Algorithm 2): the conditioning set of query q (centroid d_qcent[q]) is the
+// m_q = d_nptr[q+1] - d_nptr[q] smallest keys among ALL n_tot observations.
+int bv_select_pred_neighbors_device(const double* d_locs, int64_t n_tot, int d, const double* d_qcent, int64_t nq,
+                                    const int64_t* d_nptr, int32_t* d_nidx, double amax, cudaStream_t s) {
+    if (nq <= 0 || n_tot <= 0) return BV_OK;
+    float* xs32 = nullptr;
+    double* xs64 = nullptr;
+    int* ovf = nullptr;
+    BV_CUDA(cudaMallocAsync(&xs32, sizeof(float) * n_tot * 3, s));
+    BV_CUDA(cudaMallocAsync(&xs64, sizeof(double) * n_tot * 3, s));
+    BV_CUDA(cudaMallocAsync(&ovf, sizeof(int), s));
+    BV_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+    BV_CUDA(cudaMemsetAsync(xs32, 0, sizeof(float) * n_tot * 3, s));
+    BV_CUDA(cudaMemsetAsync(xs64, 0, sizeof(double) * n_tot * 3, s));
+    k_gather_order<<<(unsigned)((n_tot + 255) / 256), 256, 0, s>>>(d_locs, n_tot, d, nullptr, 0, n_tot, xs32, xs64);
+    BV_CUDA(cudaGetLastError());
+    NNArgs a;
+    a.xs32 = xs32;
+    a.xs64 = xs64;
+    a.pord = nullptr;
+    a.P_all = n_tot;
+    a.fixed_P = n_tot;
+    a.d = d;
+    a.bptr = nullptr;
+    a.base = 0;
+    a.blk_begin = 0;
+    a.cent = d_qcent;
+    a.nptr = d_nptr;
+    a.nidx = d_nidx;
+    a.amax = (float)amax;
+    a.overflow_count = ovf;
+    const size_t smem = sizeof(unsigned long long) * kCap + sizeof(int) * kCap + sizeof(unsigned int) * (4096 + kNT);
+    BV_CUDA(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_select<<<(unsigned)nq, kNT, smem, s>>>(a);
     BV_CUDA(cudaGetLastError());
     BV_CUDA(cudaFreeAsync(xs32, s));
