@@ -52,6 +52,13 @@ WORKLOADS = {
     "c5_m30": dict(ndata=256, m=30, seed=5, d=2, gen_m=30),
     "c5_m60": dict(ndata=256, m=60, seed=5, d=2, gen_m=30),
     "c5_m120": dict(ndata=256, m=120, seed=5, d=2, gen_m=30),
+    # prediction (Algorithm 2) + 1,000-round univariate conditional simulation and PICP:
+    # the paper's shape (n = 20,000 in the unit square, 10% held out, 200 prediction
+    # blocks) and a 10x larger one with the same 1:10 block-to-location ratio
+    "pred_20k": dict(kind="pred", n=20_000, d=2, bc=2_000, gen_m=200, pred_bc=200, m=60, rounds=1000,
+                     nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-2, seed=6),
+    "pred_2e5": dict(kind="pred", n=200_000, d=2, bc=20_000, gen_m=200, pred_bc=2_000, m=120, rounds=1000,
+                     nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-2, seed=7),
 }
 
 
@@ -352,6 +359,178 @@ def run_mle(bv, ctx, w, log):
     return res
 
 
+def pred_split(w):
+    """Locations and the held-out mask (10%: SplitMix64 draw mod 10 == 0)."""
+    locs = synth.locs_uniform(w["n"], w["d"], w["seed"])
+    r = synth.splitmix64(synth.stream(w["seed"], 9), np.arange(w["n"], dtype=np.uint64))
+    return locs, (r % np.uint64(10)) == np.uint64(0)
+
+
+def pred_metric(w):
+    return (f"block-Vecchia prediction + {w['rounds']}-round conditional simulation, new locations/sec (FP64), "
+            f"n={w['n']:.0e}, n*={w['n'] // 10:.0e}, pred bc={w['pred_bc']}, m={w['m']}, nu={w['nu']}")
+
+
+def pred_config(w, args):
+    return {"workload": args.workload, "n": w["n"], "held_out": "10% (SplitMix64 mod 10)", "pred_bc": w["pred_bc"],
+            "m": w["m"], "rounds": w["rounds"], "d": w["d"], "nu": w["nu"],
+            "theta": [w["sigma2"], w["beta"], w["nugget"]], "y": f"block-Vecchia draw at m={w['gen_m']}",
+            "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replicas" if _dist()[0] > 1 else "single"}
+
+
+def pred_oracle_sample(w, locs, y, hold, seconds=10.0):
+    """The oracle's Algorithm 2 + conditional simulation on the first prediction blocks of
+    the same workload (oracle blocks and neighbours), repeated for about `seconds`;
+    returns new locations/s, the sample description and the thread count."""
+    import oracle
+    lo, yo, ls, yt = locs[~hold], y[~hold], locs[hold], y[hold]
+    th = oracle.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+    bp, pi, ce = oracle.build_pred_blocks(ls, w["pred_bc"], seed=w["seed"])
+    k = min(len(bp) - 1, 20)
+    nnp, nni = oracle.select_pred_neighbors(lo, ce[:k], w["m"])
+    sel = pi[:bp[k]]
+    sub_ls, sub_yt = ls[sel], yt[sel]
+    sub_bp, sub_pi = bp[:k + 1], np.arange(bp[k], dtype=np.int32)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        mean, var, _ = oracle.predict(th, lo, yo, sub_ls, sub_bp, sub_pi, nnp, nni)
+        oracle.cond_sim(mean, var, w["rounds"], reps, 1.959963984540054, sub_yt)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 100:
+            break
+    return (reps * len(sel) / el, f"{reps} x (Algorithm 2 + {w['rounds']}-round conditional simulation) on the "
+            f"first {k} prediction blocks ({len(sel)} new locations) of the same workload", oracle.num_threads())
+
+
+def run_pred(args, w, log):
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        # data from the oracle's own block-Vecchia draw on a 20,000-point copy at the same density
+        n_s = min(w["n"], 20_000)
+        wl = dict(w, n=n_s, pred_bc=max(1, w["pred_bc"] * n_s // w["n"]))
+        locs, hold = pred_split(wl)
+        th = oracle.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+        bp, pi, ce = oracle.build_blocks(locs, n_s // 10, seed=w["seed"])
+        nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 30)
+        y = oracle.bv_draw(th, locs, bp, pi, nnp, nni, synth.normal(w["seed"], 20, n_s))
+        vals = []
+        for k in range(args.warmup + args.steps):
+            v, sample, cores = pred_oracle_sample(wl, locs, y, hold, seconds=2.0)
+            if k >= args.warmup:
+                vals.append(v)
+        val = statistics.mean(vals)
+        line = {"impl": "reference", "metric": pred_metric(w), "value": val, "unit": "predictions/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": (w["n"] // 10) / val * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": pred_config(w, args),
+                "cpu_baseline": {"value": val, "unit": "predictions/s", "cores": cores, "kind": "oracle",
+                                 "sample": "each step: " + sample + " (data: oracle block-Vecchia draw at m=30, "
+                                 f"n={n_s})"},
+                "e2e": {"value": val, "unit": "predictions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2410_04477_gb300 import bv
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    locs, hold = pred_split(w)
+    th = bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+    with bv.Context(local, stream.cuda_stream) as gen:
+        gen.set_data(locs)
+        gen.build_blocks(w["bc"], seed=w["seed"])
+        gen.select_neighbors(w["gen_m"])
+        y = gen.simulate(th, synth.normal(w["seed"], 20, w["n"]))
+    ctx = bv.Context(local, stream.cuda_stream)
+    ctx.set_data(locs[~hold], y[~hold])
+    ctx.set_pred_locations(locs[hold], y[hold])
+    ctx.build_pred_blocks(w["pred_bc"], seed=w["seed"])
+    ctx.select_pred_neighbors(w["m"])
+    flops, cov_evals = ctx.pred_plan_info()
+    n_star = int(hold.sum())
+    log(f"setup {time.perf_counter() - t0:.1f}s: n_obs={int((~hold).sum())} n*={n_star}")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step(k, timing):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ctx.predict(th, want=())
+        e[1].record(stream)
+        _, _, cov = ctx.cond_sim(w["rounds"], seed=k, bounds=False)
+        e[2].record(stream)
+        if timing is not None:
+            timing.append((e, cov))
+
+    for k in range(args.warmup):
+        step(k, None)
+    barrier()
+    clk = Clocks(local)
+    rec = []
+    for k in range(args.steps):
+        step(args.warmup + k, rec)
+    barrier()
+    clocks = clk.stop()
+    pred_ms = [a[0].elapsed_time(a[1]) for a, _ in rec]
+    sim_ms = [a[1].elapsed_time(a[2]) for a, _ in rec]
+    tot_ms = max_over_ranks(float(sum(pred_ms) + sum(sim_ms)))
+    value = ws * args.steps * n_star / (tot_ms / 1e3)
+    picp = [c / n_star for _, c in rec]
+    # end to end through the public API with host buffers: observations up, means,
+    # variances and interval bounds down
+    y_pin = torch.from_numpy(np.ascontiguousarray(y[~hold])).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ctx.set_observations(y_pin.numpy())
+        ctx.predict(th)
+        ctx.cond_sim(w["rounds"], seed=k)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": ws * args.steps * n_star / e2e_s, "unit": "predictions/s",
+           "h2d_bytes_per_step": int((~hold).sum()) * 8, "d2h_bytes_per_step": n_star * 8 * 4 + 16}
+    mean_pred = statistics.mean(pred_ms) / 1e3
+    achieved = flops / mean_pred / 1e12
+    roof = {"bound": "alu", "kernel": "k_pred (one launch: covariance + partial augmented Cholesky of every "
+            "prediction block)", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; probe 1.19)",
+            "flops_per_launch": flops, "cov_entries_per_launch": cov_evals}
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        v, sample, cores = pred_oracle_sample(w, locs, y, hold)
+        cpu = {"value": v, "unit": "predictions/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {"metric": pred_metric(w), "value": value, "unit": "predictions/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": pred_config(w, args), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * args.steps,
+                "extras": {"predict_ms": statistics.mean(pred_ms), "cond_sim_ms": statistics.mean(sim_ms),
+                           "picp_mean": statistics.mean(picp), "picp_min": min(picp), "picp_max": max(picp)}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,6 +545,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     w = dict(WORKLOADS[args.workload])
+    if w.get("kind") == "pred":
+        log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
+        return run_pred(args, w, log)
     if args.impl == "reference":
         return run_reference(args, w)
 

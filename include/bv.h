@@ -288,10 +288,11 @@ int bv_get_pred_sizes(bv_ctx* ctx, int64_t* n_star, int64_t* nblk, int64_t* n_nn
 int bv_predict(bv_ctx* ctx, const bv_theta* theta, double* mean, double* var, double* cov_packed);
 
 /* Univariate conditional simulation from the last bv_predict (Sec. 2.4): for each new
- * location `rounds` draws mean + sqrt(var) z, z standard normal by Box-Muller of two
- * SplitMix64 uniforms (stream seed ^ 0x636f6e6473696d5f, draw pair c = j * rounds + r:
- * u1 = 1 - (x_2c >> 11) 2^-53, u2 = (x_2c+1 >> 11) 2^-53, z = sqrt(-2 ln u1) cos(2 pi u2));
- * the interval is sample mean -/+ z_crit * sample sd (divisor rounds - 1).  Outputs
+ * location j `rounds` draws mean + sqrt(var) z, z standard normal by Box-Muller, two per
+ * pair of SplitMix64 uniforms (stream seed ^ 0x636f6e6473696d5f; pair k of location j uses
+ * draws 2c and 2c+1, c = j * ceil(rounds/2) + k: u1 = 1 - (x_2c >> 11) 2^-53,
+ * u2 = (x_2c+1 >> 11) 2^-53, z_2k = sqrt(-2 ln u1) cos(2 pi u2), z_2k+1 = the same with
+ * sin); the interval is sample mean -/+ z_crit * sample sd (divisor rounds - 1).  Outputs
  * (host, may be NULL): lower[n_star], upper[n_star], covered = number of held-out values
  * inside their interval (PICP = covered / n_star; -1 without held-out values).
  * rounds >= 2.  Synchronous. */

@@ -122,7 +122,7 @@ def _bind(L):
                                      _P(_i64), _P(_i32), _P(_i64), _P(_i32), _P(_d), _P(_d),
                                      _P(_d)]
             L.or_csim_normal.restype = _d
-            L.or_csim_normal.argtypes = [_u64, _u64]
+            L.or_csim_normal.argtypes = [_u64, _i64, _i32, _i32]
             L.or_cond_sim.restype = _int
             L.or_cond_sim.argtypes = [_P(_d), _P(_d), _i64, _i32, _u64, _d, _P(_d), _P(_d),
                                       _P(_d), _P(_i64)]
@@ -379,9 +379,9 @@ def predict(th: Theta, locs, y, locs_star, block_ptr, point_idx, nn_ptr, nn_idx,
     return mean, var, cov
 
 
-def csim_normal(seed: int, counter: int) -> float:
-    """Standard normal number `counter` of the conditional-simulation stream."""
-    return float(lib().or_csim_normal(seed, counter))
+def csim_normal(seed: int, j: int, rounds: int, r: int) -> float:
+    """Standard normal number r of new location j when each location takes `rounds`."""
+    return float(lib().or_csim_normal(seed, j, rounds, r))
 
 
 def cond_sim(mean, var, rounds, seed, z_crit, y_true=None):

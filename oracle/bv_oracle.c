@@ -901,21 +901,27 @@ int or_predict(const or_theta* th, const double* locs, const double* y, int64_t 
 
 /* ------------------------------------------------------------------------------------
  * Univariate conditional simulation and the prediction interval (Sec. 2.4, last
- * paragraph; PICP of Sec. 3.2).  For new location i, draw r = 0 .. R-1 is
- * y_ir = mean_i + sqrt(var_i) z_ir with z_ir standard normal by the Box-Muller transform
- * (Box and Muller 1958) of two SplitMix64 uniforms:
- *   c = i R + r, u1 = 1 - (x_{2c} >> 11) 2^-53, u2 = (x_{2c+1} >> 11) 2^-53,
- *   z = sqrt(-2 ln u1) cos(2 pi u2),   x_k = draw k of stream seed ^ "condsim_".
- * The sample mean and the sample variance (divisor R - 1) of the draws give the interval
- * [mean~ - z_crit sd~, mean~ + z_crit sd~]; covered counts the held-out values inside it.
+ * paragraph; PICP of Sec. 3.2).  For new location j, draw r = 0 .. R-1 is
+ * y_jr = mean_j + sqrt(var_j) z_jr with z_jr standard normal by the Box-Muller transform
+ * (Box and Muller 1958), which turns two uniforms into two independent normals: pair
+ * k = 0 .. ceil(R/2)-1 of location j uses c = j ceil(R/2) + k,
+ *   u1 = 1 - (x_{2c} >> 11) 2^-53, u2 = (x_{2c+1} >> 11) 2^-53, rho = sqrt(-2 ln u1),
+ *   z_{j,2k} = rho cos(2 pi u2),  z_{j,2k+1} = rho sin(2 pi u2)  (dropped when 2k+1 = R),
+ * x_i = draw i of the SplitMix64 stream seed ^ "condsim_".  The sample mean and the sample
+ * variance (divisor R - 1) of the y_jr give the interval [mean~ - z_crit sd~,
+ * mean~ + z_crit sd~]; covered counts the held-out values inside it.
  * ---------------------------------------------------------------------------------- */
 #define OR_STREAM_CSIM(seed) ((seed) ^ 0x636f6e6473696d5fULL) /* "condsim_" */
 
-double or_csim_normal(uint64_t seed, uint64_t c) {
+/* Normal number r of location j (pairs as above). */
+double or_csim_normal(uint64_t seed, int64_t j, int32_t rounds, int32_t r) {
     const uint64_t st = OR_STREAM_CSIM(seed);
+    const uint64_t half = ((uint64_t)rounds + 1) / 2;
+    const uint64_t c = (uint64_t)j * half + (uint64_t)(r / 2);
     const double u1 = 1.0 - (double)(or_sm64(st, 2 * c) >> 11) * 0x1p-53;
     const double u2 = (double)(or_sm64(st, 2 * c + 1) >> 11) * 0x1p-53;
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    const double rho = sqrt(-2.0 * log(u1));
+    return (r % 2 == 0) ? rho * cos(2.0 * M_PI * u2) : rho * sin(2.0 * M_PI * u2);
 }
 
 int or_cond_sim(const double* mean, const double* var, int64_t n_star, int32_t rounds,
@@ -928,11 +934,11 @@ int or_cond_sim(const double* mean, const double* var, int64_t n_star, int32_t r
         const double sd = sqrt(var[i] > 0.0 ? var[i] : 0.0);
         double sum = 0.0;
         for (int32_t r = 0; r < rounds; r++)
-            sum += mean[i] + sd * or_csim_normal(seed, (uint64_t)i * (uint64_t)rounds + (uint64_t)r);
+            sum += mean[i] + sd * or_csim_normal(seed, i, rounds, r);
         const double mt = sum / (double)rounds;
         double ss = 0.0;
         for (int32_t r = 0; r < rounds; r++) {
-            const double e = mean[i] + sd * or_csim_normal(seed, (uint64_t)i * (uint64_t)rounds + (uint64_t)r) - mt;
+            const double e = mean[i] + sd * or_csim_normal(seed, i, rounds, r) - mt;
             ss += e * e;
         }
         const double st = sqrt(ss / (double)(rounds - 1));

@@ -18,9 +18,9 @@
 //
 // Conditional simulation (the paper's univariate scheme): draw r of new location j is
 // mu_j + sigma_j z_jr with z_jr standard normal by the Box-Muller transform (Box and
-// Muller 1958) of two SplitMix64 uniforms; the sample mean and sample standard deviation
-// (divisor R - 1) of the R draws give the interval mean~ -/+ z_crit sd~, and the PICP is
-// the fraction of held-out values inside it.
+// Muller 1958), two normals per pair of SplitMix64 uniforms; the sample mean and sample
+// standard deviation (divisor R - 1) of the R draws give the interval mean~ -/+ z_crit sd~,
+// and the PICP is the fraction of held-out values inside it.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "bv_device.cuh"
 #include "bv_internal.h"
 
 struct PredState {
@@ -63,7 +64,6 @@ struct PredState {
 
 namespace {
 
-constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr int kPredNT = 256;
 constexpr size_t kPredSmemCap = 227 * 1024 - 1024;
 
@@ -99,15 +99,6 @@ void free_blocks(PredState* p) {
     p->have_blocks = false;
 }
 
-__device__ __forceinline__ int64_t pk(int64_t r, int64_t c) { return ((r * (r + 1)) >> 1) + c; }
-
-__device__ __forceinline__ double matern(int nu, double sigma2, double x) {
-    const double e = exp(-x);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
-    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
-}
-
 struct PredArgs {
     const double* locs;    // observations, SoA d x n_obs
     int64_t n_obs;
@@ -121,6 +112,7 @@ struct PredArgs {
     const int32_t* nidx;
     const int64_t* coff;   // null: no packed covariance output
     DevTheta th;
+    ExpConsts ex;
     double* mean;
     double* var;
     double* cov;
@@ -131,57 +123,108 @@ struct PredArgs {
     unsigned long long* fail;
 };
 
-// Doubles of one block's storage: the packed (N+1)-row triangle and d x N coordinates.
-__host__ __device__ inline int64_t pred_doubles(int64_t N) { return (N + 1) * (N + 2) / 2 + 3 * N; }
+// Doubles of one block's storage: the packed (N+1)-row triangle, two column buffers of
+// N+1 and d x N coordinates (d <= 3).
+__host__ __device__ inline int64_t pred_doubles(int64_t N) { return (N + 1) * (N + 2) / 2 + 2 * (N + 1) + 3 * N; }
 
+// One CTA per prediction block (grid-stride).  Gather, covariance into the packed
+// triangle (flat index, table-driven exponential), then the first m columns eliminated
+// right-looking with look-ahead: warp 0 finishes column k+1 (update by column k, pivot,
+// scale into a column buffer) while the other warps apply column k to the rest of the
+// trailing triangle, one barrier per column; a last pass applies column m-1 everywhere.
 __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
-    constexpr int NT = kPredNT, NW = NT / 32;
+    constexpr int NT = kPredNT, NU = NT - 32;
     extern __shared__ __align__(16) double sm[];
+    __shared__ double etab[32];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
+    const DevTheta th = a.th;
+    const int d = a.d;
     for (int64_t blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
         const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
-        const int N = m + b;
+        const int N = m + b, R = N + 1;
         double* A = N <= a.smem_n ? sm : a.ws + (int64_t)blockIdx.x * a.ws_stride;
-        double* px = A + pk(N + 1, 0);
-        for (int t = tid; t < N; t += NT)
-            for (int k = 0; k < a.d; ++k)
-                px[k * N + t] = t < m ? a.locs[(int64_t)k * a.n_obs + a.nidx[n0 + t]]
-                                      : a.plocs[(int64_t)k * a.n_star + a.pidx[b0 + (t - m)]];
-        if (tid == 0) s_fail = 0;
+        double* col0 = A + pk(R, 0);
+        double* col1 = col0 + R;
+        double* px = col1 + R;
+        for (int t = tid; t < N; t += NT) {
+            const bool obs = t < m;
+            const int64_t g = obs ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+            for (int k = 0; k < d; ++k)
+                px[k * N + t] = obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g];
+            A[pk(N, t)] = obs ? a.y[g] : 0.0;  // data row: [y_NN, 0]
+        }
+        if (tid == 0) {
+            A[pk(N, N)] = 0.0;
+            s_fail = 0;
+        }
         __syncthreads();
-        // covariance rows 0..N-1 (nugget on the diagonal: each row is its own point) and
-        // the data row N = [y_NN, 0]
-        for (int r = warp; r < N; r += NW)
-            for (int c = lane; c <= r; c += 32) {
-                double acc = 0.0;
-                for (int k = 0; k < a.d; ++k) {
-                    const double t = (px[k * N + r] - px[k * N + c]) * a.th.inv_range[k];
-                    acc = fma(t, t, acc);
-                }
-                double v = matern(a.th.nu_code, a.th.sigma2, sqrt(acc));
-                if (r == c) v += a.th.nugget;
-                A[pk(r, c)] = v;
+        // covariance rows 0..N-1 (Eq. 5; nugget on the diagonal: every row is its own point)
+        const int T = (N * (N + 1)) >> 1;
+        for (int f = tid; f < T; f += NT) {
+            int r, c;
+            tri_rc(f, r, c);
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                acc = fma(t, t, acc);
             }
-        for (int c = tid; c <= N; c += NT) A[pk(N, c)] = c < m ? a.y[a.nidx[n0 + c]] : 0.0;
+            const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
+            double v = matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
+            if (r == c) v += th.nugget;
+            A[f] = v;
+        }
         __syncthreads();
-        // right-looking elimination of the m conditioning columns
-        for (int k = 0; k < m; ++k) {
+        if (m > 0) {
             if (warp == 0) {
-                const double p = A[pk(k, k)];
-                const bool ok = p > 0.0;
-                if (!ok && lane == 0) s_fail = 1;
-                const double l = ok ? sqrt(p) : 1.0;
-                const double rl = 1.0 / l;
-                for (int j = k + 1 + lane; j <= N; j += 32) A[pk(j, k)] *= rl;
-                if (lane == 0) A[pk(k, k)] = l;
+                const double p = A[0];
+                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                const double rs = rsqrt(p);
+                for (int j = 1 + lane; j <= N; j += 32) {
+                    const double v = A[pk(j, 0)] * rs;
+                    A[pk(j, 0)] = v;
+                    col0[j] = v;
+                }
             }
             __syncthreads();
-            for (int j = k + 1 + warp; j <= N; j += NW) {
-                const double cj = A[pk(j, k)];
-                double* Aj = A + pk(j, 0);
-                for (int i = k + 1 + lane; i <= j; i += 32) Aj[i] = fma(-cj, A[pk(i, k)], Aj[i]);
+            for (int k = 0; k + 1 < m; ++k) {
+                const double* cur = (k & 1) ? col1 : col0;
+                double* nxt = (k & 1) ? col0 : col1;
+                const int kk = k + 1;
+                if (warp == 0) {
+                    const double ck = cur[kk];
+                    for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
+                    __syncwarp();
+                    const double p = A[pk(kk, kk)];
+                    if (!(p > 0.0) && lane == 0) s_fail = 1;
+                    const double rs = rsqrt(p);
+                    for (int j = kk + 1 + lane; j <= N; j += 32) {
+                        const double v = A[pk(j, kk)] * rs;
+                        A[pk(j, kk)] = v;
+                        nxt[j] = v;
+                    }
+                } else {
+                    const int S = N - kk, TS = (S * (S + 1)) >> 1;
+                    for (int f = tid - 32; f < TS; f += NU) {
+                        int r, c;
+                        tri_rc(f, r, c);
+                        const int j = kk + 1 + r, i = kk + 1 + c;
+                        A[pk(j, i)] = fma(-cur[j], cur[i], A[pk(j, i)]);
+                    }
+                }
+                __syncthreads();
+            }
+            // column m-1 applied to the Schur complement (rows and columns m..N)
+            const double* cur = ((m - 1) & 1) ? col1 : col0;
+            const int S = N - m + 1, TS = (S * (S + 1)) >> 1;
+            for (int f = tid; f < TS; f += NT) {
+                int r, c;
+                tri_rc(f, r, c);
+                const int j = m + r, i = m + c;
+                A[pk(j, i)] = fma(-cur[j], cur[i], A[pk(j, i)]);
             }
             __syncthreads();
         }
@@ -193,22 +236,24 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
         }
         if (a.coff) {
             double* out = a.cov + a.coff[blk];
-            for (int r = warp; r < b; r += NW)
-                for (int c = lane; c <= r; c += 32) out[pk(r, c)] = failed ? NAN : A[pk(m + r, m + c)];
+            const int TB = (b * (b + 1)) >> 1;
+            for (int f = tid; f < TB; f += NT) {
+                int r, c;
+                tri_rc(f, r, c);
+                out[f] = failed ? NAN : A[pk(m + r, m + c)];
+            }
         }
         if (tid == 0 && failed) atomicMin(a.fail, (unsigned long long)blk);
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ double csim_normal(uint64_t stream, uint64_t c) {
-    const double u1 = 1.0 - (double)(bv_sm64(stream, 2 * c) >> 11) * 0x1p-53;
-    const double u2 = (double)(bv_sm64(stream, 2 * c + 1) >> 11) * 0x1p-53;
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2);
-}
-
-// One warp per new location (grid-stride): two passes over its R draws (sum, then sum of
-// squared deviations), regenerating the counter-based draws in the second pass.
+// One warp per new location (grid-stride).  Lanes take Box-Muller pairs k = lane,
+// lane + 32, ...: pair k of location j is built from SplitMix64 draws 2c and 2c + 1,
+// c = j ceil(R/2) + k, and gives z_2k = rho cos(2 pi u2) and z_2k+1 = rho sin(2 pi u2)
+// (the second dropped when 2k + 1 = R).  Because every draw is mu + sd z, the sample mean
+// is mu + sd zbar and the sample variance sd^2 (sum z^2 - R zbar^2) / (R - 1), so one pass
+// accumulating sum z and sum z^2 replaces the two passes over the draws.
 __global__ void __launch_bounds__(256) k_cond_sim(const double* __restrict__ mean, const double* __restrict__ var,
                                                   const double* __restrict__ ytrue, int64_t n_star, int R,
                                                   uint64_t stream, double zc, double* __restrict__ lower,
@@ -216,24 +261,37 @@ __global__ void __launch_bounds__(256) k_cond_sim(const double* __restrict__ mea
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int half = (R + 1) >> 1;
     for (int64_t j = w0; j < n_star; j += nw) {
-        const double mu = mean[j], v = var[j];
-        const double sd = sqrt(v > 0.0 ? v : 0.0);
-        const uint64_t c0 = (uint64_t)j * (uint64_t)R;
-        double s = 0.0;
-        for (int r = lane; r < R; r += 32) s += mu + sd * csim_normal(stream, c0 + (uint64_t)r);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const double mt = s / (double)R;
-        double ss = 0.0;
-        for (int r = lane; r < R; r += 32) {
-            const double e = mu + sd * csim_normal(stream, c0 + (uint64_t)r) - mt;
-            ss = fma(e, e, ss);
+        const uint64_t c0 = (uint64_t)j * (uint64_t)half;
+        double s1 = 0.0, s2 = 0.0;
+        for (int k = lane; k < half; k += 32) {
+            const uint64_t c = c0 + (uint64_t)k;
+            const double u1 = 1.0 - (double)(bv_sm64(stream, 2 * c) >> 11) * 0x1p-53;
+            const double u2 = (double)(bv_sm64(stream, 2 * c + 1) >> 11) * 0x1p-53;
+            const double rho = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);
+            const double za = rho * cs;
+            s1 += za;
+            s2 = fma(za, za, s2);
+            if (2 * k + 1 < R) {
+                const double zb = rho * sn;
+                s1 += zb;
+                s2 = fma(zb, zb, s2);
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
         if (lane == 0) {
-            const double st = sqrt(ss / (double)(R - 1));
+            const double v = var[j];
+            const double sd = sqrt(v > 0.0 ? v : 0.0);
+            const double zbar = s1 / (double)R;
+            const double vz = fmax(s2 - (double)R * zbar * zbar, 0.0) / (double)(R - 1);
+            const double mt = mean[j] + sd * zbar, st = sd * sqrt(vz);
             const double lo = mt - zc * st, up = mt + zc * st;
             if (lower) lower[j] = lo;
             if (upper) upper[j] = up;
@@ -453,6 +511,7 @@ static int pred_launch(bv_ctx* c, const DevTheta& th, bool with_cov) {
     a.nidx = p->d_nidx;
     a.coff = with_cov ? p->d_coff : nullptr;
     a.th = th;
+    bv_exp_consts(&a.ex);
     a.mean = p->d_mean;
     a.var = p->d_var;
     a.cov = p->d_cov;

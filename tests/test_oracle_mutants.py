@@ -38,6 +38,7 @@ MUTANTS = {
     "prediction neighbour keys shifted by one index": (
         "key.idx = (int32_t)j;", "key.idx = (int32_t)(j > 0 ? j - 1 : 0);"),
     "Box-Muller radius without the factor 2": ("sqrt(-2.0 * log(u1))", "sqrt(-1.0 * log(u1))"),
+    "Box-Muller pair reuses the cosine": ("rho * sin(2.0 * M_PI * u2)", "rho * cos(2.0 * M_PI * u2)"),
 }
 
 
@@ -146,8 +147,9 @@ def _pin_pred_neighbours():
 
 def _pin_csim_normal():
     from scipy import stats
-    z = np.array([oracle.csim_normal(9, c) for c in range(20000)])
-    return stats.kstest(z, "norm").pvalue > 1e-3
+    z = np.array([oracle.csim_normal(9, j, 1000, r) for j in range(20) for r in range(1000)])
+    a, b = z[0::2], z[1::2]
+    return stats.kstest(z, "norm").pvalue > 1e-3 and abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(len(a))
 
 
 PINS = {"kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,

@@ -123,11 +123,19 @@ def test_conditional_law_is_the_block_likelihood():
 
 
 def test_csim_normals_are_standard_normal():
-    z = np.array([oracle.csim_normal(9, c) for c in range(60000)])
+    # 60 locations x 1,001 draws (an odd count: the last pair's second normal is dropped)
+    z = np.array([oracle.csim_normal(9, j, 1001, r) for j in range(60) for r in range(1001)])
     assert stats.kstest(z, "norm").pvalue > 1e-3
     assert abs(z.mean()) < 4 / np.sqrt(len(z))
     assert abs(z.var() - 1.0) < 4 * np.sqrt(2.0 / len(z))
-    assert oracle.csim_normal(9, 5) != oracle.csim_normal(10, 5)
+    # the two normals of a pair are independent: their correlation is within noise, and
+    # the pair's squared radius is exponential with mean 2 (chi-square with 2 dof)
+    a = np.array([oracle.csim_normal(9, j, 1000, 2 * k) for j in range(20) for k in range(500)])
+    b = np.array([oracle.csim_normal(9, j, 1000, 2 * k + 1) for j in range(20) for k in range(500)])
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(len(a))
+    assert stats.kstest(a * a + b * b, "expon", args=(0, 2)).pvalue > 1e-3
+    assert oracle.csim_normal(9, 0, 10, 5) != oracle.csim_normal(10, 0, 10, 5)
+    assert oracle.csim_normal(9, 1, 10, 0) != oracle.csim_normal(9, 0, 10, 0)
 
 
 def test_cond_sim_interval_and_coverage():
