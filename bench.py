@@ -52,6 +52,12 @@ WORKLOADS = {
     "c5_m30": dict(ndata=256, m=30, seed=5, d=2, gen_m=30),
     "c5_m60": dict(ndata=256, m=60, seed=5, d=2, gen_m=30),
     "c5_m120": dict(ndata=256, m=120, seed=5, d=2, gen_m=30),
+    # classic Vecchia (blocks of size 1, random order) on the config-2 data: the paper's
+    # baseline method, m = 30 (its recommended conditioning size) and m = 60
+    "cv_m30": dict(n=200_000, d=2, bc=20_000, m=30, nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-4, seed=1,
+                   gen_m=400, classic=True),
+    "cv_m60": dict(n=200_000, d=2, bc=20_000, m=60, nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-4, seed=1,
+                   gen_m=400, classic=True),
     # prediction (Algorithm 2) + 1,000-round univariate conditional simulation and PICP:
     # the paper's shape (n = 20,000 in the unit square, 10% held out, 200 prediction
     # blocks) and a 10x larger one with the same 1:10 block-to-location ratio
@@ -165,6 +171,8 @@ def setup_gpu(bv, ctx, w, log):
     z = synth.normal(w["seed"], 20, w["n"])
     y = ctx.simulate(true_theta(bv, w), z)
     t2 = time.perf_counter()
+    if w.get("classic"):
+        ctx.build_singletons(seed=w["seed"])
     ctx.select_neighbors(w["m"])
     t3 = time.perf_counter()
     log(f"setup: blocks {t1 - t0:.1f}s, draw(m={w['gen_m']}) {t2 - t1:.1f}s, neighbours {t3 - t2:.1f}s")
@@ -235,10 +243,13 @@ def cpu_oracle_sample(w, seconds=12.0):
     side = (n_s / w["n"]) ** (1.0 / w["d"])
     locs = synth.locs_uniform(n_s, w["d"], w["seed"] + 7) * side
     bc_s = max(1, int(round(w["bc"] * n_s / w["n"])))
-    bp, pi, ce = oracle.build_blocks(locs, bc_s, seed=w["seed"], iters=20)
+    if w.get("classic"):
+        bp, pi, ce = oracle.build_singletons(locs, seed=w["seed"])
+    else:
+        bp, pi, ce = oracle.build_blocks(locs, bc_s, seed=w["seed"], iters=20)
     nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, w["m"])
     y = synth.normal(w["seed"] + 7, 21, n_s)
-    th = oracle.theta(w["sigma2"], w["beta"] * side / side, w["nu"], w["nugget"])
+    th = oracle.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
     reps, t0 = 0, time.perf_counter()
     while True:
         oracle.loglik(th, locs, y, bp, pi, nnp, nni)
@@ -248,7 +259,7 @@ def cpu_oracle_sample(w, seconds=12.0):
             break
     per_eval_sample = el / reps
     nblk_s = len(bp) - 1
-    full_eval = per_eval_sample * (w["bc"] / nblk_s)
+    full_eval = per_eval_sample * ((w["n"] if w.get("classic") else w["bc"]) / nblk_s)
     return (1.0 / full_eval, f"{reps} evals of an n={n_s} sub-square at the same density "
             f"({nblk_s} blocks, m={w['m']}), extrapolated by block count", oracle.num_threads(),
             per_eval_sample)
@@ -269,7 +280,10 @@ def run_reference(args, w):
     side = (n_s / w["n"]) ** (1.0 / w["d"])
     locs = synth.locs_uniform(n_s, w["d"], w["seed"] + 7) * side
     bc_s = max(1, int(round(w["bc"] * n_s / w["n"])))
-    bp, pi, ce = O.build_blocks(locs, bc_s, seed=w["seed"], iters=20)
+    if w.get("classic"):
+        bp, pi, ce = O.build_singletons(locs, seed=w["seed"])
+    else:
+        bp, pi, ce = O.build_blocks(locs, bc_s, seed=w["seed"], iters=20)
     nnp, nni = O.select_neighbors(locs, bp, pi, ce, w["m"])
     y = synth.normal(w["seed"] + 7, 21, n_s)
     f = synth.perturb_factors(w["seed"] + 1000, args.warmup + args.steps)
@@ -281,7 +295,7 @@ def run_reference(args, w):
     for k in range(args.steps):
         O.loglik(ths[args.warmup + k], locs, y, bp, pi, nnp, nni, check=False)
     el = time.perf_counter() - t0
-    scale = w["bc"] / (len(bp) - 1)
+    scale = (w["n"] if w.get("classic") else w["bc"]) / (len(bp) - 1)
     per_full = el / args.steps * scale
     val = 1.0 / per_full
     sample = (f"each step: one FP64 oracle evaluation of an n={n_s} sub-square at the same density "
@@ -299,6 +313,7 @@ def run_reference(args, w):
 
 def config_of(w, args):
     c = {"workload": args.workload, "d": w["d"], "m": w["m"], "y": f"block-Vecchia draw at m={w['gen_m']}",
+         "blocks": "n singletons, random order" if w.get("classic") else f"bc={w.get('bc')} K-means",
          "theta": "perturbed U(0.8,1.2) per step", "precision": args.precision,
          "l2": "flushed between timed steps (256 MB write)",
          "parallelism": "replicas" if _dist()[0] > 1 else "single"}
@@ -313,6 +328,9 @@ def config_of(w, args):
 
 def metric_of(w, args):
     prec = "FP64" if args.precision == "fp64" else "mixed FP32/FP64"
+    if w.get("classic"):
+        return (f"classic-Vecchia loglik evals/sec ({prec}), n={w['n']:.0e}, blocks of size 1, m={w['m']}, "
+                f"nu={w['nu']}, d={w['d']}")
     if "ndata" in w:
         return f"block-Vecchia loglik evals/sec ({prec}), {w['ndata']} datasets in one launch, m={w['m']}"
     return (f"block-Vecchia loglik evals/sec ({prec}), n={w['n']:.0e}, bc={w['bc']:.0e}, m={w['m']}, "

@@ -112,6 +112,13 @@ int bv_build_blocks(bv_ctx* ctx, int64_t bc, uint64_t seed, int32_t lloyd_iters,
 int bv_build_blocks_multi(bv_ctx* ctx, const int64_t* bc_per, uint64_t seed,
                           int32_t lloyd_iters, int64_t* bc_eff_per);
 
+/* Classic Vecchia (Sec. 1: the special case of blocks of size 1): every point its own
+ * block, the blocks in a random order (Fisher-Yates over the n points with the stream of
+ * bv_build_blocks' block permutation), each singleton's query point for
+ * bv_select_neighbors the point itself.  Outputs as bv_build_blocks (n + 1 and n
+ * entries; may be NULL).  One dataset. */
+int bv_build_singletons(bv_ctx* ctx, uint64_t seed, int64_t* block_ptr, int32_t* point_idx);
+
 /* Caller-supplied partition (Algorithm 1 input g and zeta) for the single-dataset case:
  * bc blocks in the order to evaluate, block_ptr[bc+1], point_idx[n] (a permutation of
  * 0..n-1), centroids[bc x d] (the query points of the neighbour search; NULL = member

@@ -8,6 +8,7 @@ leg of ``bench.py`` may import this package.  It shares no code with the CUDA li
 What each function follows (details in the C source):
   matern_corr / cov       Eq. 5 (Matern), closed forms at nu = 1/2, 3/2, 5/2
   kmeans / build_blocks   Sec. 2.1 + Algorithm 1 (clustering, block permutation)
+  build_singletons        classic Vecchia: blocks of size 1 in a random order (Sec. 1)
   select_neighbors        Sec. 2.2 + Algorithm 1 (nearest neighbours of each block)
   block_loglik / loglik   Algorithm 1 (batched steps, literally) and Eq. 4
   exact_loglik            Eq. 1
@@ -108,6 +109,8 @@ def _bind(L):
             L.or_select_neighbors.restype = _int
             L.or_select_neighbors.argtypes = [_P(_d), _i64, _int, _i64, _P(_i64), _P(_i32),
                                               _P(_d), _i32, _P(_i32), _P(_i64), _P(_i32)]
+            L.or_build_singletons.restype = _int
+            L.or_build_singletons.argtypes = [_P(_d), _i64, _int, _u64, _P(_i64), _P(_i32), _P(_d)]
             L.or_build_pred_blocks.restype = _i64
             L.or_build_pred_blocks.argtypes = [_P(_d), _i64, _int, _i64, _u64, _int, _P(_i64),
                                                _P(_i32), _P(_d)]
@@ -219,6 +222,20 @@ def build_blocks(locs, bc, seed, iters=20):
     if nb < 0:
         raise OracleError(-nb, "build_blocks")
     return bp[:nb + 1].copy(), pi, ce[:nb].copy()
+
+
+def build_singletons(locs, seed):
+    """Classic Vecchia structure: singleton blocks in a random order; centroids are the
+    points themselves.  (block_ptr, point_idx, centroids)"""
+    locs = _c(locs, np.float64)
+    n, d = locs.shape
+    bp = np.empty(n + 1, np.int64)
+    pi = np.empty(n, np.int32)
+    ce = np.empty((n, d), np.float64)
+    st = lib().or_build_singletons(_ptr(locs, _d), n, d, seed, _ptr(bp, _i64), _ptr(pi, _i32), _ptr(ce, _d))
+    if st:
+        raise OracleError(st, "build_singletons")
+    return bp, pi, ce
 
 
 def select_neighbors(locs, block_ptr, point_idx, centroids, m, m_per_block=None):

@@ -621,6 +621,28 @@ int64_t or_build_blocks(const double* locs, int64_t n, int d, int64_t bc, uint64
 }
 
 /* ------------------------------------------------------------------------------------
+ * Classic Vecchia (Sec. 1: the special case of blocks of size 1).  Every point is its own
+ * block; the blocks follow a random order drawn by the Fisher-Yates shuffle of the
+ * points with the block-permutation stream (for i = n-1 .. 1, j = floor(r_i (i+1) / 2^64),
+ * swap(perm[i], perm[j])); a singleton's query point for the neighbour search is the
+ * point itself.
+ * ---------------------------------------------------------------------------------- */
+int or_build_singletons(const double* locs, int64_t n, int d, uint64_t seed, int64_t* block_ptr,
+                        int32_t* point_idx, double* centroids) {
+    if (n <= 0 || n > INT32_MAX) return OR_EINVAL;
+    for (int64_t i = 0; i < n; i++) point_idx[i] = (int32_t)i;
+    uint64_t zs = OR_STREAM_ZETA(seed);
+    for (int64_t i = n - 1; i >= 1; i--) {
+        int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)i), (uint64_t)(i + 1));
+        int32_t t = point_idx[i]; point_idx[i] = point_idx[j]; point_idx[j] = t;
+    }
+    for (int64_t p = 0; p <= n; p++) block_ptr[p] = p;
+    for (int64_t p = 0; p < n; p++)
+        for (int k = 0; k < d; k++) centroids[p * d + k] = locs[(int64_t)point_idx[p] * d + k];
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------
  * Block nearest neighbours (Sec. 2.2; Algorithm 1 "Nearest neighbors").  For the block
  * at position i, the candidates are all points of the blocks at positions 0 .. i-1; the
  * query is the block centroid; the key of a candidate j is (D2(centroid, s_j), j) with D2

@@ -71,6 +71,7 @@ _SIGS = {
     "bv_set_datasets": (_int, [_vp, _i32, _P(_i64), _P(_d), _P(_d), _i32]),
     "bv_set_observations": (_int, [_vp, _vp, _i32]),
     "bv_build_blocks": (_int, [_vp, _i64, _u64, _i32, _P(_i64), _P(_i32), _P(_i64)]),
+    "bv_build_singletons": (_int, [_vp, _u64, _P(_i64), _P(_i32)]),
     "bv_build_blocks_multi": (_int, [_vp, _P(_i64), _u64, _i32, _P(_i64)]),
     "bv_set_blocks": (_int, [_vp, _i64, _P(_i64), _P(_i32), _P(_d)]),
     "bv_select_neighbors": (_int, [_vp, _i32, _P(_i32), _P(_i64), _P(_i32)]),
@@ -244,6 +245,13 @@ class Context:
             _check(_lib.bv_set_observations(self.h, yv.ctypes.data, 0), "bv_set_observations")
 
     # preprocessing ------------------------------------------------------------------------
+    def build_singletons(self, seed=0):
+        """Classic Vecchia structure: (block_ptr, point_idx) of n singleton blocks."""
+        bp = np.empty(self.n + 1, np.int64)
+        pi = np.empty(self.n, np.int32)
+        _check(_lib.bv_build_singletons(self.h, seed, _p(bp, _i64), _p(pi, _i32)), "bv_build_singletons")
+        return bp, pi
+
     def build_blocks(self, bc, seed=0, iters=20):
         bp = np.empty(bc + 1, np.int64)
         pi = np.empty(self.n, np.int32)

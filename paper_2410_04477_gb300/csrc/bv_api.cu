@@ -353,6 +353,36 @@ extern "C" int bv_build_blocks(bv_ctx* c, int64_t bc, uint64_t seed, int32_t ite
     return BV_OK;
 }
 
+extern "C" int bv_build_singletons(bv_ctx* c, uint64_t seed, int64_t* block_ptr, int32_t* point_idx) {
+    if (!c) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    const int64_t n = c->n_tot;
+    const int d = c->d;
+    BV_CUDA(cudaSetDevice(c->device));
+    free_blocks(c);
+    std::vector<int32_t> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    const uint64_t zs = BV_STREAM_ZETA(seed);
+    for (int64_t i = n - 1; i >= 1; --i) {
+        const uint64_t r = bv_sm64(zs, (uint64_t)i);
+        const int64_t j = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)(i + 1)) >> 64);
+        std::swap(perm[i], perm[j]);
+    }
+    std::vector<double> cent((size_t)n * d);
+    for (int64_t p = 0; p < n; ++p)
+        for (int k = 0; k < d; ++k) cent[(size_t)p * d + k] = c->h_locs[(size_t)perm[p] * d + k];
+    c->h_bptr.resize(n + 1);
+    std::iota(c->h_bptr.begin(), c->h_bptr.end(), (int64_t)0);
+    c->h_pidx = std::move(perm);
+    c->h_bds.assign(n, 0);
+    c->ds_blk_off = {0, n};
+    c->nblk = n;
+    BV_TRY(upload_blocks(c, cent));
+    if (block_ptr) memcpy(block_ptr, c->h_bptr.data(), sizeof(int64_t) * (n + 1));
+    if (point_idx) memcpy(point_idx, c->h_pidx.data(), sizeof(int32_t) * n);
+    return BV_OK;
+}
+
 extern "C" int bv_set_blocks(bv_ctx* c, int64_t bc, const int64_t* block_ptr, const int32_t* point_idx,
                              const double* centroids) {
     if (!c || bc <= 0 || !block_ptr || !point_idx) return BV_EINVAL;

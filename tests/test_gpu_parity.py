@@ -275,3 +275,21 @@ def test_mixed_precision_per_block(bv, d, m, bc, ranges):
     assert set(Ns % 4) == {0, 1, 2, 3}
     np.testing.assert_allclose(per, per_o, rtol=0, atol=2e-2)
     assert abs(llm - llo) <= 1e-4 * abs(llo), (llm, llo)
+
+
+@pytest.mark.parametrize("n,d,m,seed", [(3000, 2, 30, 0), (1500, 3, 60, 1)])
+def test_classic_vecchia_matches_oracle(bv, n, d, m, seed):
+    locs = synth.locs_uniform(n, d, 70 + seed)
+    th = _otheta(1.0, 0.1, 0.5, 1e-3)
+    y = oracle.exact_draw(th, locs, synth.normal(70 + seed, 20, n))
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        bp, pi = ctx.build_singletons(seed=seed)
+        nnp, nni = ctx.select_neighbors(m)
+        ll, per, _ = ctx.loglik(_gtheta(bv, 1.0, 0.1, 0.5, 1e-3), per_block=True)
+    obp, opi, oce = oracle.build_singletons(locs, seed=seed)
+    onnp, onni = oracle.select_neighbors(locs, obp, opi, oce, m)
+    _same_struct((bp, pi, nnp, nni), (obp, opi, onnp, onni))
+    ll_o, per_o, _ = oracle.loglik(th, locs, y, obp, opi, onnp, onni)
+    assert abs(ll - ll_o) <= REL64 * abs(ll_o), (ll, ll_o)
+    np.testing.assert_allclose(per, per_o, rtol=1e-9, atol=1e-9)

@@ -80,6 +80,47 @@ def test_singleton_blocks_is_classic_vecchia():
     assert ll == pytest.approx(want, rel=1e-11)
 
 
+def test_classic_vecchia_structure():
+    # singleton blocks in a random order: a permutation; each singleton's query point is
+    # the point itself, so its neighbours are the m earlier points nearest to it
+    n = 300
+    locs = synth.locs_uniform(n, 2, 5)
+    bp, pi, ce = oracle.build_singletons(locs, seed=3)
+    np.testing.assert_array_equal(bp, np.arange(n + 1))
+    assert np.array_equal(np.sort(pi), np.arange(n)) and not np.array_equal(pi, np.arange(n))
+    assert np.array_equal(ce, locs[pi])
+    bp2, pi2, _ = oracle.build_singletons(locs, seed=4)
+    assert not np.array_equal(pi, pi2)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 12)
+    for i in range(n):
+        cand = pi[:i].astype(np.int64)
+        d2 = ((locs[cand] - locs[pi[i]]) ** 2).sum(axis=1)
+        np.testing.assert_array_equal(nni[nnp[i]:nnp[i + 1]], cand[np.lexsort((cand, d2))][:12])
+
+
+def test_classic_vecchia_loglik_by_kriging():
+    # Sec. 1: classic Vecchia, each point conditioned on its m nearest earlier points, by
+    # the univariate kriging formula sigma_j^2 = C_jj - c^T C^-1 c
+    n = 240
+    locs = synth.locs_uniform(n, 2, 6)
+    th = oracle.theta(1.1, 0.06, 1.5, 2e-3)
+    S = _ref.full_cov(locs, 1.1, 0.06, 1.5, 2e-3)
+    y = np.linalg.cholesky(S) @ synth.normal(6, 21, n)
+    bp, pi, ce = oracle.build_singletons(locs, seed=7)
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, 10)
+    ll, per, _ = oracle.loglik(th, locs, y, bp, pi, nnp, nni)
+    want = 0.0
+    for i in range(n):
+        j, c = pi[i], nni[nnp[i]:nnp[i + 1]].astype(np.int64)
+        if len(c):
+            w = np.linalg.solve(S[np.ix_(c, c)], S[c, j])
+            mu, var = w @ y[c], S[j, j] - S[c, j] @ w
+        else:
+            mu, var = 0.0, S[j, j]
+        want += -0.5 * (np.log(2 * np.pi) + np.log(var) + (y[j] - mu) ** 2 / var)
+    assert ll == pytest.approx(want, rel=1e-11)
+
+
 @pytest.mark.parametrize("d,ranges", [(2, None), (3, [0.1, 0.15, 0.3])])
 def test_dense_implied_precision(d, ranges):
     # Eq. 4 defines a joint Gaussian with precision A^T D^{-1} A; its log density at y
