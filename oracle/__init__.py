@@ -9,6 +9,8 @@ What each function follows (details in the C source):
   matern_corr / cov       Eq. 5 (Matern), closed forms at nu = 1/2, 3/2, 5/2
   kmeans / build_blocks   Sec. 2.1 + Algorithm 1 (clustering, block permutation)
   build_singletons        classic Vecchia: blocks of size 1 in a random order (Sec. 1)
+  order_blocks            the block orderings of Sec. 2.1 (random, maxmin, Morton, KD-tree,
+                          Hilbert)
   select_neighbors        Sec. 2.2 + Algorithm 1 (nearest neighbours of each block)
   block_loglik / loglik   Algorithm 1 (batched steps, literally) and Eq. 4
   exact_loglik            Eq. 1
@@ -111,6 +113,10 @@ def _bind(L):
                                               _P(_d), _i32, _P(_i32), _P(_i64), _P(_i32)]
             L.or_build_singletons.restype = _int
             L.or_build_singletons.argtypes = [_P(_d), _i64, _int, _u64, _P(_i64), _P(_i32), _P(_d)]
+            L.or_order_blocks.restype = _int
+            L.or_order_blocks.argtypes = [_P(_d), _i64, _int, _int, _u64, _P(_i64)]
+            L.or_hilbert_index.restype = _u64
+            L.or_hilbert_index.argtypes = [_P(_u64), _int]
             L.or_build_pred_blocks.restype = _i64
             L.or_build_pred_blocks.argtypes = [_P(_d), _i64, _int, _i64, _u64, _int, _P(_i64),
                                                _P(_i32), _P(_d)]
@@ -236,6 +242,36 @@ def build_singletons(locs, seed):
     if st:
         raise OracleError(st, "build_singletons")
     return bp, pi, ce
+
+
+ORDERS = {"random": 0, "maxmin": 1, "morton": 2, "kdtree": 3, "hilbert": 4}
+
+
+def order_blocks(centroids, order, seed=0):
+    """New block order by a rule on the centroids: perm[q] = old position at new q."""
+    ce = _c(centroids, np.float64)
+    bc, d = ce.shape
+    perm = np.empty(bc, np.int64)
+    st = lib().or_order_blocks(_ptr(ce, _d), bc, d, ORDERS[order] if isinstance(order, str) else int(order),
+                               seed, _ptr(perm, _i64))
+    if st:
+        raise OracleError(st, "order_blocks")
+    return perm
+
+
+def apply_block_order(block_ptr, point_idx, centroids, perm):
+    """The block structure with its blocks placed in the order perm."""
+    bp = np.asarray(block_ptr)
+    sizes = np.diff(bp)[perm]
+    nbp = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    npi = np.concatenate([point_idx[bp[p]:bp[p + 1]] for p in perm]).astype(np.int32)
+    return nbp, npi, np.asarray(centroids)[perm].copy()
+
+
+def hilbert_index(coords):
+    """Hilbert index of one point of 21-bit integer coordinates (d = 1..3)."""
+    c = _c(np.asarray(coords, np.uint64), np.uint64)
+    return int(lib().or_hilbert_index(_ptr(c, _u64), c.size))
 
 
 def select_neighbors(locs, block_ptr, point_idx, centroids, m, m_per_block=None):

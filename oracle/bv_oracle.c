@@ -643,6 +643,180 @@ int or_build_singletons(const double* locs, int64_t n, int d, uint64_t seed, int
 }
 
 /* ------------------------------------------------------------------------------------
+ * Block orderings (Sec. 2.1, the five permutations the paper compares; Sec. 3.1 KL study).
+ * Each maps the current block sequence (positions 0 .. bc-1, centroids c_p) to a new one:
+ * perm[q] = the old position placed at new position q.  Ties always go to the lower old
+ * position.
+ *   0 random   Fisher-Yates over positions with the block-permutation stream of `seed`
+ *   1 maxmin   first the centroid nearest (squared distance) to the mean centroid; then
+ *              repeatedly the centroid whose smallest squared distance to those already
+ *              placed is largest (Guinness 2018)
+ *   2 Morton   Z-order: coordinates scaled to 21-bit integers over the centroids'
+ *              bounding box, q_k = min(2^21-1, floor((c_k - lo_k) / (hi_k - lo_k) 2^21)),
+ *              bit b of axis k at key bit b d + k; ascending key
+ *   3 KD-tree  recursive median split: at depth t sort the set by (coordinate t mod d,
+ *              position), the first floor(|S|/2) form the left part, the rest the right;
+ *              left before right, down to single blocks (Bentley 1975)
+ *   4 Hilbert  the same 21-bit integers mapped to their Hilbert index by Skilling's
+ *              axes-to-transpose transform (Skilling 2004), transposed bits read from the
+ *              most significant level down, axis 0 first; ascending index
+ * ---------------------------------------------------------------------------------- */
+typedef struct { uint64_t key; int64_t pos; } or_okey;
+
+static int or_okey_cmp(const void* a, const void* b) {
+    const or_okey* x = (const or_okey*)a;
+    const or_okey* y = (const or_okey*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+static void or_quantise21(const double* cent, int64_t bc, int d, uint64_t* q) {
+    for (int k = 0; k < d; k++) {
+        double lo = cent[k], hi = cent[k];
+        for (int64_t p = 1; p < bc; p++) {
+            if (cent[p * d + k] < lo) lo = cent[p * d + k];
+            if (cent[p * d + k] > hi) hi = cent[p * d + k];
+        }
+        for (int64_t p = 0; p < bc; p++) {
+            uint64_t v = 0;
+            if (hi > lo) {
+                double f = floor((cent[p * d + k] - lo) / (hi - lo) * 2097152.0);
+                v = f >= 2097151.0 ? 2097151u : (uint64_t)f;
+            }
+            q[p * d + k] = v;
+        }
+    }
+}
+
+static uint64_t or_hilbert_key(const uint64_t* coords, int d) {
+    uint64_t X[3] = {0, 0, 0};
+    for (int i = 0; i < d; i++) X[i] = coords[i];
+    const uint64_t M = 1u << 20;
+    /* inverse undo of the excess work */
+    for (uint64_t Q = M; Q > 1; Q >>= 1) {
+        const uint64_t P = Q - 1;
+        for (int i = 0; i < d; i++) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                uint64_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    /* Gray encode */
+    for (int i = 1; i < d; i++) X[i] ^= X[i - 1];
+    uint64_t t = 0;
+    for (uint64_t Q = M; Q > 1; Q >>= 1)
+        if (X[d - 1] & Q) t ^= Q - 1;
+    for (int i = 0; i < d; i++) X[i] ^= t;
+    uint64_t key = 0;
+    for (int b = 20; b >= 0; b--)
+        for (int i = 0; i < d; i++) key = (key << 1) | ((X[i] >> b) & 1u);
+    return key;
+}
+
+static void or_kd_order(const double* cent, int d, int64_t* idx, int64_t n, int depth, or_okey* tmp) {
+    if (n <= 1) return;
+    const int ax = depth % d;
+    /* sort idx[0..n) by (coordinate ax, position): insertion into tmp by qsort on a key
+     * built from the coordinate's order-preserving bits */
+    for (int64_t i = 0; i < n; i++) {
+        double v = cent[idx[i] * d + ax];
+        uint64_t u;
+        memcpy(&u, &v, sizeof u);
+        u = (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+        tmp[i].key = u;
+        tmp[i].pos = idx[i];
+    }
+    qsort(tmp, (size_t)n, sizeof(or_okey), or_okey_cmp);
+    for (int64_t i = 0; i < n; i++) idx[i] = tmp[i].pos;
+    const int64_t h = n / 2;
+    or_kd_order(cent, d, idx, h, depth + 1, tmp);
+    or_kd_order(cent, d, idx + h, n - h, depth + 1, tmp);
+}
+
+int or_order_blocks(const double* cent, int64_t bc, int d, int order, uint64_t seed, int64_t* perm) {
+    if (bc <= 0 || d <= 0 || d > 3) return OR_EINVAL;
+    if (order == 0) {
+        for (int64_t p = 0; p < bc; p++) perm[p] = p;
+        uint64_t zs = OR_STREAM_ZETA(seed);
+        for (int64_t i = bc - 1; i >= 1; i--) {
+            int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)i), (uint64_t)(i + 1));
+            int64_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+        }
+        return OR_OK;
+    }
+    if (order == 1) {
+        double mean[3] = {0, 0, 0};
+        for (int k = 0; k < d; k++) {
+            double sacc = 0.0;
+            for (int64_t p = 0; p < bc; p++) sacc += cent[p * d + k];
+            mean[k] = sacc / (double)bc;
+        }
+        double* dmin = (double*)malloc(sizeof(double) * (size_t)bc);
+        char* used = (char*)calloc((size_t)bc, 1);
+        if (!dmin || !used) { free(dmin); free(used); return OR_ENOMEM; }
+        int64_t first = 0;
+        double best = INFINITY;
+        for (int64_t p = 0; p < bc; p++) {
+            double v = or_d2(cent + p * d, mean, d);
+            if (v < best) { best = v; first = p; }
+        }
+        perm[0] = first;
+        used[first] = 1;
+        for (int64_t p = 0; p < bc; p++) dmin[p] = or_d2(cent + p * d, cent + first * d, d);
+        for (int64_t q = 1; q < bc; q++) {
+            int64_t pick = -1;
+            double far = -1.0;
+            for (int64_t p = 0; p < bc; p++)
+                if (!used[p] && dmin[p] > far) { far = dmin[p]; pick = p; }
+            perm[q] = pick;
+            used[pick] = 1;
+            for (int64_t p = 0; p < bc; p++) {
+                double v = or_d2(cent + p * d, cent + pick * d, d);
+                if (v < dmin[p]) dmin[p] = v;
+            }
+        }
+        free(dmin); free(used);
+        return OR_OK;
+    }
+    if (order == 2 || order == 4) {
+        uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(bc * d));
+        or_okey* k = (or_okey*)malloc(sizeof(or_okey) * (size_t)bc);
+        if (!q || !k) { free(q); free(k); return OR_ENOMEM; }
+        or_quantise21(cent, bc, d, q);
+        for (int64_t p = 0; p < bc; p++) {
+            uint64_t key = 0;
+            if (order == 2) {
+                for (int b = 0; b < 21; b++)
+                    for (int a = 0; a < d; a++) key |= ((q[p * d + a] >> b) & 1u) << (b * d + a);
+            } else {
+                key = or_hilbert_key(q + p * d, d);
+            }
+            k[p].key = key;
+            k[p].pos = p;
+        }
+        qsort(k, (size_t)bc, sizeof(or_okey), or_okey_cmp);
+        for (int64_t p = 0; p < bc; p++) perm[p] = k[p].pos;
+        free(q); free(k);
+        return OR_OK;
+    }
+    if (order == 3) {
+        or_okey* tmp = (or_okey*)malloc(sizeof(or_okey) * (size_t)bc);
+        if (!tmp) return OR_ENOMEM;
+        for (int64_t p = 0; p < bc; p++) perm[p] = p;
+        or_kd_order(cent, d, perm, bc, 0, tmp);
+        free(tmp);
+        return OR_OK;
+    }
+    return OR_EINVAL;
+}
+
+uint64_t or_hilbert_index(const uint64_t* coords, int d) { return or_hilbert_key(coords, d); }
+
+/* ------------------------------------------------------------------------------------
  * Block nearest neighbours (Sec. 2.2; Algorithm 1 "Nearest neighbors").  For the block
  * at position i, the candidates are all points of the blocks at positions 0 .. i-1; the
  * query is the block centroid; the key of a candidate j is (D2(centroid, s_j), j) with D2

@@ -39,6 +39,11 @@ MUTANTS = {
         "key.idx = (int32_t)j;", "key.idx = (int32_t)(j > 0 ? j - 1 : 0);"),
     "Box-Muller radius without the factor 2": ("sqrt(-2.0 * log(u1))", "sqrt(-1.0 * log(u1))"),
     "Box-Muller pair reuses the cosine": ("rho * sin(2.0 * M_PI * u2)", "rho * cos(2.0 * M_PI * u2)"),
+    "Hilbert without the Gray encoding": ("for (int i = 1; i < d; i++) X[i] ^= X[i - 1];",
+                                          "for (int i = 1; i < d; i++) X[i] ^= 0;"),
+    "maxmin ties to the highest position": ("if (!used[p] && dmin[p] > far)", "if (!used[p] && dmin[p] >= far)"),
+    "KD-tree split at the wrong axis": ("const int ax = depth % d;", "const int ax = (depth + 1) % d;"),
+    "Morton with the axes' bits swapped": ("<< (b * d + a);", "<< (b * d + (d - 1 - a));"),
 }
 
 
@@ -152,7 +157,41 @@ def _pin_csim_normal():
     return stats.kstest(z, "norm").pvalue > 1e-3 and abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(len(a))
 
 
-PINS = {"kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
+def _pin_hilbert():
+    import itertools
+    cells = np.array(list(itertools.product(range(16), repeat=2)), np.uint64)
+    keys = np.array([oracle.hilbert_index(c << np.uint64(17)) for c in cells], dtype=np.uint64)
+    path = cells[np.argsort(keys)].astype(np.int64)
+    return bool(np.all(np.abs(np.diff(path, axis=0)).sum(axis=1) == 1))
+
+
+def _pin_orders():
+    # a lattice has many exact distance ties: maxmin must break them to the lowest position
+    g = np.arange(6) / 6.0
+    ce = np.array([(a, b) for a in g for b in g])
+    perm = oracle.order_blocks(ce, "maxmin")
+    d2 = ((ce[:, None, :] - ce[None, :, :]) ** 2).sum(-1)
+    placed = [perm[0]]
+    for q in range(1, len(perm)):
+        rest = np.setdiff1d(np.arange(len(ce)), placed)
+        dmin = d2[np.ix_(rest, placed)].min(axis=1)
+        if perm[q] != rest[dmin == dmin.max()].min():
+            return False
+        placed.append(perm[q])
+    # KD-tree: first half on the low side of axis 0; Morton: first quadrant first
+    pts = synth.locs_uniform(64, 2, 9)
+    kd = oracle.order_blocks(pts, "kdtree")
+    if not max(pts[kd[:32], 0]) < min(pts[kd[32:], 0]):
+        return False
+    q = (np.arange(8) + 0.5) / 8
+    grid = np.array([(a, b) for a in q for b in q])
+    mo = oracle.order_blocks(grid, "morton")
+    first = np.floor(grid[mo[:16]] * 8).astype(int)
+    second = np.floor(grid[mo[16:32]] * 8).astype(int)
+    return bool(np.all(first < 4) and np.all(second[:, 0] >= 4) and np.all(second[:, 1] < 4))
+
+
+PINS = {"hilbert adjacency": _pin_hilbert, "orderings": _pin_orders, "kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
         "conditional-simulation normals": _pin_csim_normal, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
         "K-means exact tie": _pin_kmeans_tie}
