@@ -112,6 +112,24 @@ int bv_build_blocks(bv_ctx* ctx, int64_t bc, uint64_t seed, int32_t lloyd_iters,
 int bv_build_blocks_multi(bv_ctx* ctx, const int64_t* bc_per, uint64_t seed,
                           int32_t lloyd_iters, int64_t* bc_eff_per);
 
+/* Block orderings (Sec. 2.1; compared by KL divergence in Sec. 3.1). */
+enum { BV_ORDER_RANDOM = 0, BV_ORDER_MAXMIN = 1, BV_ORDER_MORTON = 2, BV_ORDER_KDTREE = 3,
+       BV_ORDER_HILBERT = 4 };
+
+/* Place the context's blocks (one dataset) in a new order chosen from their centroids,
+ * ties to the lower current position; neighbour sets must be selected again.
+ *   RANDOM   Fisher-Yates over the current positions, block-permutation stream of seed
+ *   MAXMIN   first the block whose centroid is nearest the mean centroid, then repeatedly
+ *            the block farthest (largest smallest squared distance) from those placed
+ *   MORTON   Z-order of the centroids scaled to 21-bit integers over their bounding box
+ *            (q = min(2^21-1, floor((c - lo) / (hi - lo) 2^21)); bit b of axis k at b d + k)
+ *   KDTREE   recursive median split, axis = depth mod d, sorted by (coordinate, position),
+ *            the first floor(|S|/2) first
+ *   HILBERT  Hilbert index of the same integers (Skilling's transform; levels from the
+ *            most significant, axis 0 first)
+ * Outputs (may be NULL): block_ptr[bc+1], point_idx[n] in the new order. */
+int bv_order_blocks(bv_ctx* ctx, int32_t order, uint64_t seed, int64_t* block_ptr, int32_t* point_idx);
+
 /* Classic Vecchia (Sec. 1: the special case of blocks of size 1): every point its own
  * block, the blocks in a random order (Fisher-Yates over the n points with the stream of
  * bv_build_blocks' block permutation), each singleton's query point for

@@ -47,8 +47,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     headers.append(os.path.join(INCLUDE, "bv.h"))
     objs = []
     jobs = []
+    # host code: no contraction of a*b+c into fused multiply-adds (GCC contracts by
+    # default on aarch64), so host-side distance keys round exactly as written
     base = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-            "-I", INCLUDE, "-I", CSRC]
+            "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
     if ptxas_info:
         base += ["-Xptxas", "-v"]
     for s in srcs:

@@ -71,6 +71,7 @@ _SIGS = {
     "bv_set_datasets": (_int, [_vp, _i32, _P(_i64), _P(_d), _P(_d), _i32]),
     "bv_set_observations": (_int, [_vp, _vp, _i32]),
     "bv_build_blocks": (_int, [_vp, _i64, _u64, _i32, _P(_i64), _P(_i32), _P(_i64)]),
+    "bv_order_blocks": (_int, [_vp, _i32, _u64, _P(_i64), _P(_i32)]),
     "bv_build_singletons": (_int, [_vp, _u64, _P(_i64), _P(_i32)]),
     "bv_build_blocks_multi": (_int, [_vp, _P(_i64), _u64, _i32, _P(_i64)]),
     "bv_set_blocks": (_int, [_vp, _i64, _P(_i64), _P(_i32), _P(_d)]),
@@ -245,6 +246,17 @@ class Context:
             _check(_lib.bv_set_observations(self.h, yv.ctypes.data, 0), "bv_set_observations")
 
     # preprocessing ------------------------------------------------------------------------
+    ORDERS = {"random": 0, "maxmin": 1, "morton": 2, "kdtree": 3, "hilbert": 4}
+
+    def order_blocks(self, order, seed=0):
+        """Reorder the blocks by a rule on their centroids: (block_ptr, point_idx)."""
+        o = self.ORDERS[order] if isinstance(order, str) else int(order)
+        nb, _ = self.sizes()
+        bp = np.empty(nb + 1, np.int64)
+        pi = np.empty(self.n, np.int32)
+        _check(_lib.bv_order_blocks(self.h, o, seed, _p(bp, _i64), _p(pi, _i32)), "bv_order_blocks")
+        return bp, pi
+
     def build_singletons(self, seed=0):
         """Classic Vecchia structure: (block_ptr, point_idx) of n singleton blocks."""
         bp = np.empty(self.n + 1, np.int64)

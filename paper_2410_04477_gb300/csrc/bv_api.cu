@@ -353,6 +353,29 @@ extern "C" int bv_build_blocks(bv_ctx* c, int64_t bc, uint64_t seed, int32_t ite
     return BV_OK;
 }
 
+// Reorders the blocks: new position q holds the block at current position perm[q]
+// (ncent: the centroids in the new order).  Neighbour sets are dropped.
+int bv_apply_block_order(bv_ctx* c, const std::vector<int64_t>& perm, const std::vector<double>& ncent) {
+    const int64_t bc = c->nblk;
+    std::vector<int64_t> bptr(bc + 1, 0);
+    std::vector<int32_t> pidx;
+    pidx.reserve(c->n_tot);
+    for (int64_t q = 0; q < bc; ++q) {
+        const int64_t p = perm[q];
+        bptr[q + 1] = bptr[q] + (c->h_bptr[p + 1] - c->h_bptr[p]);
+        pidx.insert(pidx.end(), c->h_pidx.begin() + c->h_bptr[p], c->h_pidx.begin() + c->h_bptr[p + 1]);
+    }
+    std::vector<int32_t> bds(bc, 0);
+    std::vector<int64_t> dsoff = c->ds_blk_off;
+    free_blocks(c);
+    c->h_bptr = std::move(bptr);
+    c->h_pidx = std::move(pidx);
+    c->h_bds = std::move(bds);
+    c->ds_blk_off = std::move(dsoff);
+    c->nblk = bc;
+    return upload_blocks(c, ncent);
+}
+
 extern "C" int bv_build_singletons(bv_ctx* c, uint64_t seed, int64_t* block_ptr, int32_t* point_idx) {
     if (!c) return BV_EINVAL;
     if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;

@@ -293,3 +293,38 @@ def test_classic_vecchia_matches_oracle(bv, n, d, m, seed):
     ll_o, per_o, _ = oracle.loglik(th, locs, y, obp, opi, onnp, onni)
     assert abs(ll - ll_o) <= REL64 * abs(ll_o), (ll, ll_o)
     np.testing.assert_allclose(per, per_o, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("order", ["random", "maxmin", "morton", "kdtree", "hilbert"])
+@pytest.mark.parametrize("n,d,bc", [(4000, 2, 400), (3000, 3, 300)])
+def test_block_orderings_match_oracle(bv, order, n, d, bc):
+    locs = synth.locs_uniform(n, d, 80 + d)
+    th = _otheta(1.0, 0.1, 1.5, 1e-3)
+    y = synth.normal(80 + d, 20, n)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(bc, seed=3)
+        bp, pi = ctx.order_blocks(order, seed=11)
+        nnp, nni = ctx.select_neighbors(40)
+        ll = ctx.loglik(_gtheta(bv, 1.0, 0.1, 1.5, 1e-3))
+    obp, opi, oce = oracle.build_blocks(locs, bc, seed=3)
+    perm = oracle.order_blocks(oce, order, seed=11)
+    obp, opi, oce = oracle.apply_block_order(obp, opi, oce, perm)
+    onnp, onni = oracle.select_neighbors(locs, obp, opi, oce, 40)
+    _same_struct((bp, pi, nnp, nni), (obp, opi, onnp, onni))
+    ll_o, _, _ = oracle.loglik(th, locs, y, obp, opi, onnp, onni)
+    assert abs(ll - ll_o) <= REL64 * abs(ll_o)
+
+
+def test_maxmin_on_many_blocks(bv):
+    # many greedy steps and exact distance ties (centroids of a lattice's blocks)
+    g = np.arange(60) / 60.0
+    locs = np.array([(a, b) for a in g for b in g])
+    with bv.Context() as ctx:
+        ctx.set_data(locs, np.zeros(len(locs)))
+        ctx.build_blocks(900, seed=4, iters=10)
+        bp, pi = ctx.order_blocks("maxmin")
+    obp, opi, oce = oracle.build_blocks(locs, 900, seed=4, iters=10)
+    obp, opi, _ = oracle.apply_block_order(obp, opi, oce, oracle.order_blocks(oce, "maxmin"))
+    np.testing.assert_array_equal(bp, obp)
+    np.testing.assert_array_equal(pi, opi)
