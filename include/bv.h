@@ -180,6 +180,25 @@ int bv_loglik(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out
 int bv_loglik_terms(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_loglik,
                     double* out_quad, double* out_logdet);
 
+/* The exact Gaussian log-likelihood, Eq. 1, of dataset 0 (n <= 65536) by a dense tiled
+ * FP64 Cholesky factorisation on the device (memory: about 4 (n+1)^2 bytes, freed on
+ * return).  use_y = 0 evaluates at y = 0 (as the KL divergence of Sec. 3.1 needs); else
+ * the context's observations.  Outputs (any but none required): ell, quad = y^T Sigma^-1 y,
+ * logdet = log|Sigma|.  BV_ENOTPD if Sigma is not positive definite.  Synchronous. */
+int bv_exact_loglik(bv_ctx* ctx, const bv_theta* theta, int32_t use_y, double* out_loglik,
+                    double* out_quad, double* out_logdet);
+
+/* Leading-term flops of one bv_exact_loglik on n points ((n+1)^3/3 + (n+1)^2). */
+int bv_exact_flops(int64_t n, double* flops);
+
+/* KL divergence of the block-Vecchia approximation from the exact GP (Eq. 7, Sec. 3.1):
+ * KL = ell_0(theta; 0) - ell_a(theta; 0) = (log|Sigma_a| - log|Sigma_0|) / 2, with the
+ * exact log-determinant from bv_exact_loglik and the approximate one from the context's
+ * blocks and neighbour sets (bv_loglik_terms in `precision`).  Without observations the
+ * context's y is set to zeros.  Outputs: kl, and (may be NULL) both log-determinants. */
+int bv_kl_divergence(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_kl,
+                     double* out_logdet_exact, double* out_logdet_approx);
+
 /* All datasets at once: thetas[ndatasets] (host), out_loglik[ndatasets] (host).
  * Synchronous. */
 int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,

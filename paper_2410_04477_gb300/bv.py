@@ -82,6 +82,9 @@ _SIGS = {
     "bv_get_neighbors": (_int, [_vp, _P(_i64), _P(_i32)]),
     "bv_loglik": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d)]),
     "bv_loglik_terms": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
+    "bv_exact_loglik": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
+    "bv_exact_flops": (_int, [_i64, _P(_d)]),
+    "bv_kl_divergence": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
     "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
@@ -160,6 +163,12 @@ def save_blob(path, blob):
     b = _arr(blob, np.float32)
     with open(path, "wb") as f:
         f.write(b"BVWS" + np.array([1, b.size, 0], np.int32).tobytes() + b.tobytes())
+
+
+def exact_flops(n):
+    f = ctypes.c_double(0)
+    _check(_lib.bv_exact_flops(int(n), ctypes.byref(f)), "bv_exact_flops")
+    return f.value
 
 
 def exp_neg_check(x):
@@ -384,6 +393,20 @@ class Context:
         f, e = ctypes.c_double(0), ctypes.c_double(0)
         _check(_lib.bv_pred_plan_info(self.h, ctypes.byref(f), ctypes.byref(e)), "bv_pred_plan_info")
         return f.value, e.value
+
+    def exact_loglik(self, th: bv_theta, use_y=True):
+        """Eq. 1 by a dense device Cholesky: (ell, quad, logdet)."""
+        l, q, d = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(_lib.bv_exact_loglik(self.h, ctypes.byref(th), 1 if use_y else 0, ctypes.byref(l),
+                                    ctypes.byref(q), ctypes.byref(d)), "bv_exact_loglik")
+        return l.value, q.value, d.value
+
+    def kl_divergence(self, th: bv_theta, precision=BV_FP64):
+        """(KL, logdet exact, logdet approximate) of the current blocks/neighbours."""
+        k, a, b = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(_lib.bv_kl_divergence(self.h, ctypes.byref(th), precision, ctypes.byref(k), ctypes.byref(a),
+                                     ctypes.byref(b)), "bv_kl_divergence")
+        return k.value, a.value, b.value
 
     def loglik_terms(self, th: bv_theta, precision=BV_FP64):
         """(ell, quad, logdet) with ell = -(quad + logdet + n log 2 pi) / 2."""
