@@ -58,6 +58,13 @@ WORKLOADS = {
                    gen_m=400, classic=True),
     "cv_m60": dict(n=200_000, d=2, bc=20_000, m=60, nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-4, seed=1,
                    gen_m=400, classic=True),
+    # KL study (Sec. 3.1): n = 20,000 uniform in the unit square, nu = 1.5, beta = 0.052537
+    # (effective range 0.3, Table 1); timed step = one exact log-likelihood (dense FP64
+    # Cholesky); extras: KL of block Vecchia (bc = 1500, five orderings, several m) and of
+    # classic Vecchia (random order), each with its evaluation time
+    "kl_20k": dict(kind="kl", n=20_000, d=2, nu=1.5, sigma2=1.0, beta=0.052537, nugget=0.0, seed=8,
+                   bc=1500, bv_m=[10, 30, 60, 120, 180], cv_m=[10, 30, 60, 150],
+                   orders=["random", "maxmin", "morton", "kdtree", "hilbert"]),
     # prediction (Algorithm 2) + 1,000-round univariate conditional simulation and PICP:
     # the paper's shape (n = 20,000 in the unit square, 10% held out, 200 prediction
     # blocks) and a 10x larger one with the same 1:10 block-to-location ratio
@@ -549,6 +556,132 @@ def run_pred(args, w, log):
     return 0
 
 
+def run_kl(args, w, log):
+    ws, rank, local = _dist()
+    n = w["n"]
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        # the oracle's dense Eq. 1 on a bounded sample (n_s points at the same density)
+        n_s = 3000
+        locs = synth.locs_uniform(n_s, 2, w["seed"]) * (n_s / n) ** 0.5
+        th = oracle.theta(w["sigma2"], w["beta"], w["nu"], max(w["nugget"], 1e-10))
+        zero = np.zeros(n_s)
+        for _ in range(args.warmup):
+            oracle.exact_loglik(th, locs, zero)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.exact_loglik(th, locs, zero)
+        per = (time.perf_counter() - t0) / args.steps * (n / n_s) ** 3
+        val = 1.0 / per
+        line = {"impl": "reference", "metric": kl_metric(w), "value": val, "unit": "evals/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": kl_config(w, args),
+                "cpu_baseline": {"value": val, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": f"each step: the oracle's dense Eq. 1 on n={n_s} points at the same "
+                                 "density, extrapolated by (n / n_s)^3"},
+                "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2410_04477_gb300 import bv
+    stream = torch.cuda.Stream()
+    locs = synth.locs_uniform(n, w["d"], w["seed"])
+    th = bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+    ctx = bv.Context(local, stream.cuda_stream)
+    ctx.set_data(locs, np.zeros(n))
+    flops = bv.exact_flops(n)
+    for _ in range(args.warmup):
+        ctx.exact_loglik(th, use_y=False)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ell0, _, logdet0 = ctx.exact_loglik(th, use_y=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    tot_ms = max_over_ranks(float(sum(ms)))
+    value = ws * args.steps / (tot_ms / 1e3)
+    achieved = flops / (statistics.mean(ms) / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_update + k_trsm + k_potrf (tiled dense Cholesky, one exact evaluation)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": None, "flops_per_launch_sequence": flops,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; probe 1.19)"}
+    # end to end: observations up, ell down, through the public call
+    y = synth.normal(w["seed"], 20, n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_observations(y)
+        ctx.exact_loglik(th)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": 24}
+    # the KL study itself
+    study = {"exact_logdet": logdet0, "exact_ell0": ell0, "bv": [], "cv": []}
+
+    def timed_eval(c):
+        c.loglik(th)
+        t = time.perf_counter()
+        for _ in range(5):
+            c.loglik(th)
+        return (time.perf_counter() - t) / 5 * 1e3
+
+    ctx.set_observations(np.zeros(n))
+    for order in w["orders"]:
+        ctx.build_blocks(w["bc"], seed=w["seed"])
+        ctx.order_blocks(order, seed=w["seed"])
+        for m in w["bv_m"]:
+            ctx.select_neighbors(m)
+            kl, _, _ = ctx.kl_divergence(th)
+            study["bv"].append({"order": order, "bc": w["bc"], "m": m, "kl": kl, "eval_ms": timed_eval(ctx)})
+            log(f"BV-{w['bc']}-{m}-{order}: KL {kl:.3e}")
+    ctx.build_singletons(seed=w["seed"])
+    for m in w["cv_m"]:
+        ctx.select_neighbors(m)
+        kl, _, _ = ctx.kl_divergence(th)
+        study["cv"].append({"order": "random", "m": m, "kl": kl, "eval_ms": timed_eval(ctx)})
+        log(f"CV-{n}-{m}-random: KL {kl:.3e}")
+    if rank == 0:
+        line = {"metric": kl_metric(w), "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": kl_config(w, args), "roofline": roof, "cpu_baseline": None, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": int(3 * ((n + 64) // 64) + 2) * args.steps,
+                "extras": {"kl_study": study}}
+        if not args.no_cpu and ws == 1:
+            import oracle
+            n_s = 3000
+            sub = locs[:n_s] * 1.0
+            oth = oracle.theta(w["sigma2"], w["beta"], w["nu"], max(w["nugget"], 1e-10))
+            t0 = time.perf_counter()
+            oracle.exact_loglik(oth, sub, np.zeros(n_s))
+            per = (time.perf_counter() - t0) * (n / n_s) ** 3
+            line["cpu_baseline"] = {"value": 1.0 / per, "unit": "evals/s", "cores": oracle.num_threads(),
+                                    "kind": "oracle", "sample": f"one dense Eq. 1 on {n_s} points, "
+                                    "extrapolated by (n / n_s)^3"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def kl_metric(w):
+    return (f"exact GP log-likelihood evals/sec (dense FP64 Cholesky, Eq. 1), n={w['n']}, nu={w['nu']}, "
+            f"beta={w['beta']}; KL study of block vs classic Vecchia in extras")
+
+
+def kl_config(w, args):
+    return {"workload": args.workload, "n": w["n"], "d": w["d"], "nu": w["nu"], "beta": w["beta"],
+            "sigma2": w["sigma2"], "nugget": w["nugget"], "bc": w["bc"], "bv_m": w["bv_m"], "cv_m": w["cv_m"],
+            "orders": w["orders"], "l2": "inputs (3.2 GB factor) larger than L2"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -563,6 +696,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     w = dict(WORKLOADS[args.workload])
+    if w.get("kind") == "kl":
+        log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
+        return run_kl(args, w, log)
     if w.get("kind") == "pred":
         log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
         return run_pred(args, w, log)
