@@ -92,6 +92,7 @@ _SIGS = {
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
+    "bv_matern_check": (_int, [_d, _i64, _P(_d), _P(_d)]),
     "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
@@ -169,6 +170,14 @@ def exact_flops(n):
     f = ctypes.c_double(0)
     _check(_lib.bv_exact_flops(int(n), ctypes.byref(f)), "bv_exact_flops")
     return f.value
+
+
+def matern_check(nu, x):
+    """Device Matern correlation at scaled distances x (test support)."""
+    xv = _arr(x, np.float64)
+    out = np.empty_like(xv)
+    _check(_lib.bv_matern_check(float(nu), xv.size, _p(xv, _d), _p(out, _d)), "bv_matern_check")
+    return out
 
 
 def exp_neg_check(x):

@@ -542,14 +542,66 @@ extern "C" int bv_get_neighbors(bv_ctx* c, int64_t* nn_ptr, int32_t* nn_idx) {
 // ------------------------------------------------------------------------------------
 // evaluation plan: size bins, launch shapes, workspace
 // ------------------------------------------------------------------------------------
+// Temme's gamma-function combinations at |mu| <= 1/2, from the series
+//   log(1/G(1+z)) = gamma z - sum_{k>=2} (-1)^k zeta(k) z^k / k   (|z| < 1),
+// split into its even part E(mu) and odd part O(mu): 1/G(1 +- mu) = exp(E +- O), so
+// gam2 = e^E cosh(O) and gam1 = -e^E sinh(O) / mu (no cancellation as mu -> 0).  zeta(k)
+// by direct summation to 1000 with the Euler-Maclaurin tail; all in long double.
+static void temme_constants(double mu, double* gam1, double* gam2, double* gampl, double* gammi) {
+    static long double zeta[65];
+    static bool init = false;
+    if (!init) {
+        for (int k = 2; k <= 64; ++k) {
+            const long double N = 1000.0L;
+            long double s = 0.0L;
+            for (int j = 999; j >= 1; --j) s += powl((long double)j, -(long double)k);
+            const long double Nk = powl(N, -(long double)k);
+            // sum_{j>=N} j^-k = N^{1-k}/(k-1) + N^-k/2 + k N^{-k-1}/12 - k(k+1)(k+2) N^{-k-3}/720 + ...
+            s += N * Nk / (k - 1) + 0.5L * Nk + (long double)k * Nk / N / 12.0L -
+                 (long double)k * (k + 1) * (k + 2) * Nk / (N * N * N) / 720.0L;
+            zeta[k] = s;
+        }
+        init = true;
+    }
+    const long double eg = 0.57721566490153286060651209008240243L;  // Euler's gamma
+    const long double m = mu;
+    long double E = 0.0L, Oq = eg;  // O = mu * Oq
+    long double pk = m;             // m^(k-1)
+    for (int k = 2; k <= 64; ++k) {
+        pk *= m;                    // m^k ... for even k add to E; odd k add m^(k-1) to Oq
+        if (k % 2 == 0) E -= zeta[k] * pk / k;
+        else Oq += zeta[k] * (pk / m) / k;
+        if (m == 0.0L) break;
+    }
+    const long double O = m * Oq;
+    long double shq;  // sinh(O) / O
+    if (fabsl(O) < 1e-4L) shq = 1.0L + O * O / 6.0L + O * O * O * O / 120.0L;
+    else shq = sinhl(O) / O;
+    const long double eE = expl(E);
+    *gam1 = (double)(-eE * shq * Oq);
+    *gam2 = (double)(eE * coshl(O));
+    *gampl = (double)expl(E + O);
+    *gammi = (double)expl(E - O);
+}
+
 int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
     if (!t) return BV_EINVAL;
     if (!(t->sigma2 > 0.0) || !(t->nugget >= 0.0) || !std::isfinite(t->sigma2) || !std::isfinite(t->nugget))
         return BV_EINVAL;
+    *o = DevTheta{};
+    o->nu = t->nu;
     if (t->nu == 0.5) o->nu_code = NU_HALF;
     else if (t->nu == 1.5) o->nu_code = NU_3HALF;
     else if (t->nu == 2.5) o->nu_code = NU_5HALF;
-    else return BV_EINVAL;
+    else if (t->nu > 0.0 && t->nu <= BV_NU_MAX) {
+        o->nu_code = NU_GENERAL;
+        o->nrec = (int32_t)floor(t->nu + 0.5);
+        o->mu = t->nu - (double)o->nrec;
+        temme_constants(o->mu, &o->gam1, &o->gam2, &o->gampl, &o->gammi);
+        o->lognorm = (double)((1.0L - (long double)t->nu) * logl(2.0L) - lgammal((long double)t->nu));
+    } else {
+        return BV_EINVAL;
+    }
     for (int k = 0; k < 3; ++k) {
         const double r = t->aniso ? t->range[k] : t->range[0];
         if (k < d && !(r > 0.0 && std::isfinite(r))) return BV_EINVAL;
@@ -557,7 +609,6 @@ int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
     }
     o->sigma2 = t->sigma2;
     o->nugget = t->nugget;
-    o->pad = 0;
     return BV_OK;
 }
 
@@ -591,6 +642,7 @@ static LLArgs make_args(bv_ctx* c) {
     a.fail = c->d_fail;
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
+    a.gen = c->cur_gen ? 1 : 0;
     bv_exp_consts(&a.ex);
     return a;
 }
@@ -786,7 +838,12 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
 // Graph of one evaluation, captured once per precision after tuning.  theta is copied in
 // front of each launch.
 static int ensure_graph(bv_ctx* c, int prec) {
+    if (c->graph[prec] && c->graph_gen[prec] != c->cur_gen) {
+        cudaGraphExecDestroy(c->graph[prec]);
+        c->graph[prec] = nullptr;
+    }
     if (c->graph[prec]) return BV_OK;
+    c->graph_gen[prec] = c->cur_gen;
     cudaGraph_t g = nullptr;
     BV_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const int st = enqueue_eval_forked(c, prec);
@@ -819,7 +876,12 @@ static int prepare_eval(bv_ctx* c, const bv_theta* thetas, int32_t prec) {
     if (prec != BV_FP64 && prec != BV_MIXED) return BV_EINVAL;
     if (!c->have_nn || !c->have_blocks) return BV_ESTATE;
     BV_CUDA(cudaSetDevice(c->device));
-    for (int k = 0; k < c->ndata; ++k) BV_TRY(bv_theta_to_dev(&thetas[k], c->d, &c->h_theta[k]));
+    bool gen = false;
+    for (int k = 0; k < c->ndata; ++k) {
+        BV_TRY(bv_theta_to_dev(&thetas[k], c->d, &c->h_theta[k]));
+        gen = gen || c->h_theta[k].nu_code == NU_GENERAL;
+    }
+    c->cur_gen = gen;
     return BV_OK;
 }
 

@@ -9,6 +9,8 @@
 
 namespace {
 
+constexpr double kPiD = 3.141592653589793238462643383279502884;
+
 // Row-major packed lower triangle: element (r, c), c <= r, at r(r+1)/2 + c.
 __device__ __forceinline__ int pk(int r, int c) { return (r * (r + 1) >> 1) + c; }
 
@@ -46,13 +48,104 @@ __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ t
     return x > 700.0 ? 0.0 : res;
 }
 
-// Matern correlation times sigma^2 at scaled distance x (Eq. 5, half-integer closed forms).
+// Matern correlation rho(x) = 2^{1-nu}/G(nu) x^nu K_nu(x) of Eq. 5 for any nu > 0.
+// K_mu and K_{mu+1} at |mu| <= 1/2 come from Temme's series for x <= 2 (N. M. Temme,
+// "On the numerical evaluation of the modified Bessel function of the third kind",
+// J. Comput. Phys. 19, 1975) and from Steed's evaluation of Temme's continued fraction
+// for x > 2 (Thompson and Barnett, J. Comput. Phys. 64, 1986); the upward recurrence
+// K_{a+1} = K_{a-1} + (2a/x) K_a (stable for K) reaches nu = nrec + mu.  The product with
+// x^nu is formed in logarithms.
+__device__ __noinline__ double matern_gen_corr(const DevTheta& th, double x) {
+    if (!(x > 0.0)) return 1.0;
+    if (x > 740.0) return 0.0;
+    const double mu = th.mu, eps = 1e-17;
+    double kmu, kmu1;
+    if (x <= 2.0) {
+        const double half = 0.5 * x;
+        const double lnh = -log(half);           // log(2 / x)
+        const double pimu = kPiD * mu;
+        const double fpi = fabs(pimu) < 1e-12 ? 1.0 : pimu / sin(pimu);
+        const double sg = mu * lnh;
+        const double fs = fabs(sg) < 1e-12 ? 1.0 : sinh(sg) / sg;
+        double f = fpi * (th.gam1 * cosh(sg) + th.gam2 * fs * lnh);  // f_0
+        const double es = exp(sg);                                   // (x/2)^{-mu}
+        double p = 0.5 * es / th.gampl;                              // (x/2)^{-mu} G(1+mu) / 2
+        double q = 0.5 / (es * th.gammi);                            // (x/2)^{mu} G(1-mu) / 2
+        double c = 1.0;
+        const double h2 = half * half;
+        double sum = f, sum1 = p;
+        for (int k = 1; k < 500; ++k) {
+            const double dk = (double)k;
+            f = (dk * f + p + q) / (dk * dk - mu * mu);
+            c *= h2 / dk;
+            p /= dk - mu;
+            q /= dk + mu;
+            const double t = c * f;
+            sum += t;
+            sum1 += c * (p - dk * f);
+            if (fabs(t) < fabs(sum) * eps) break;
+        }
+        kmu = sum;
+        kmu1 = sum1 * (2.0 / x);
+    } else {
+        // continued fraction for the ratio, with Steed's simultaneous sum for the scale
+        double b = 2.0 * (1.0 + x);
+        double dd = 1.0 / b;
+        double h = dd, dh = dd;
+        double q1 = 0.0, q2 = 1.0;
+        const double a1 = 0.25 - mu * mu;
+        double q = a1, c = a1, a = -a1;
+        double s = 1.0 + q * dh;
+        for (int i = 2; i < 2000; ++i) {
+            a -= 2.0 * (double)(i - 1);
+            c = -a * c / (double)i;
+            const double qn = (q1 - b * q2) / a;
+            q1 = q2;
+            q2 = qn;
+            q += c * qn;
+            b += 2.0;
+            dd = 1.0 / (b + a * dd);
+            dh = (b * dd - 1.0) * dh;
+            h += dh;
+            const double ds = q * dh;
+            s += ds;
+            if (fabs(ds) < fabs(s) * eps) break;
+        }
+        h *= a1;
+        // K_mu = sqrt(pi / (2x)) e^{-x} / s, formed in logarithms below
+        kmu = sqrt(kPiD / (2.0 * x)) / s;           // times e^{-x}
+        kmu1 = kmu * (mu + x + 0.5 - h) / x;
+    }
+    // upward recurrence in the order: K_{mu+1}, ..., K_{mu+nrec}
+    double km = kmu, kc = kmu1;
+    double knu = th.nrec == 0 ? kmu : kmu1;
+    for (int i = 1; i < th.nrec; ++i) {
+        const double kn = km + (2.0 * (mu + (double)i) / x) * kc;
+        km = kc;
+        kc = kn;
+        knu = kn;
+    }
+    const double lk = log(knu) - (x > 2.0 ? x : 0.0);
+    return exp(th.lognorm + th.nu * log(x) + lk);
+}
+
+// Matern covariance sigma^2 rho(x) at scaled distance x (Eq. 5, half-integer closed forms
+// through the table-driven exponential).
 __device__ __forceinline__ double matern64t(int nu, double sigma2, double x, const double* tab, double K,
                                             double L1, double L2) {
     const double e = exp_neg(x, tab, K, L1, L2);
     if (nu == NU_HALF) return sigma2 * e;
     if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
     return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+}
+
+// Any nu: closed forms for the half-integers, K_nu otherwise.  `g` points at the theta in
+// global memory, so the general branch reads its constants there and the caller keeps
+// only the fields it uses in registers.
+__device__ __forceinline__ double matern64g(const DevTheta* __restrict__ g, int nu, double sigma2, double x,
+                                            const double* tab, double K, double L1, double L2) {
+    if (nu == NU_GENERAL) return sigma2 * matern_gen_corr(*g, x);
+    return matern64t(nu, sigma2, x, tab, K, L1, L2);
 }
 
 }  // namespace

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "bv_device.cuh"
 #include "bv_internal.h"
 
 namespace {
@@ -29,11 +30,12 @@ constexpr int kUpdNT = 256;    // 16 x 16 threads, 4 x 4 outputs each
 
 __device__ __forceinline__ int64_t tile_off(int64_t i, int64_t j) { return ((i * (i + 1)) / 2 + j) * TT; }
 
-__device__ __forceinline__ double matern_exact(int nu, double sigma2, double x) {
+__device__ __forceinline__ double matern_exact(const DevTheta& th, double x) {
+    if (th.nu_code == NU_GENERAL) return th.sigma2 * matern_gen_corr(th, x);
     const double e = exp(-x);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
-    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+    if (th.nu_code == NU_HALF) return th.sigma2 * e;
+    if (th.nu_code == NU_3HALF) return th.sigma2 * ((1.0 + x) * e);
+    return th.sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
 }
 
 struct FillArgs {
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
                 const double t = (a.locs[k * a.n + r] - a.locs[k * a.n + c]) * a.th.inv_range[k];
                 acc = fma(t, t, acc);
             }
-            v = matern_exact(a.th.nu_code, a.th.sigma2, sqrt(acc));
+            v = matern_exact(a.th, sqrt(acc));
             if (r == c) v += a.th.nugget;
         } else if (r == a.n) {
             v = c < a.n ? (a.y ? a.y[c] : 0.0) : 1.0;

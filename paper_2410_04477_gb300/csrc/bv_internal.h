@@ -33,15 +33,23 @@ void bv_record_cuda_error(cudaError_t e, const char* expr, const char* file, int
 // Device-side parameters
 // ------------------------------------------------------------------------------------
 
-// Matern smoothness codes for the closed forms of Eq. 5 at nu = 1/2, 3/2, 5/2.
-enum { NU_HALF = 0, NU_3HALF = 1, NU_5HALF = 2 };
+// Matern smoothness codes: the closed forms of Eq. 5 at nu = 1/2, 3/2, 5/2, and any other
+// nu through K_nu (NU_GENERAL).
+enum { NU_HALF = 0, NU_3HALF = 1, NU_5HALF = 2, NU_GENERAL = 3 };
 
-// theta prepared for the kernels: reciprocal ranges per axis (isotropic: all equal).
+// Largest smoothness accepted for the general form.
+#define BV_NU_MAX 20.0
+
+// theta prepared for the kernels: reciprocal ranges per axis (isotropic: all equal).  For
+// NU_GENERAL the smoothness is split as nu = nrec + mu, |mu| <= 1/2, with the constants
+// of Temme's series at mu (gam1 = (1/G(1-mu) - 1/G(1+mu)) / (2 mu), gam2 = (1/G(1-mu) +
+// 1/G(1+mu)) / 2, gampl = 1/G(1+mu), gammi = 1/G(1-mu)) and lognorm = log(2^{1-nu}/G(nu)).
 struct DevTheta {
     double sigma2, nugget;
     double inv_range[3];
     int32_t nu_code;
-    int32_t pad;
+    int32_t nrec;
+    double nu, mu, gam1, gam2, gampl, gammi, lognorm;
 };
 
 // Constants of the table-driven FP64 exponential (Tang, "Table-driven implementation of
@@ -72,6 +80,7 @@ struct LLArgs {
     const DevTheta* theta;   // per dataset
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
+    int gen;                 // host side: launch the general-smoothness instantiation
     double* ell_blk;         // per-block conditional log-likelihood (output)
     double* u_blk;           // per-block quadratic form u_i = v_i^T v_i (output)
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
@@ -195,6 +204,8 @@ struct bv_ctx {
     bool plan_valid[2] = {false, false};
     bool tuned[2] = {false, false};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_gen[2] = {false, false};   // whether each graph holds the general-nu kernels
+    bool cur_gen = false;                 // whether the current theta needs them
     std::vector<cudaStream_t> side;   // fork/join streams of the captured graph
     std::vector<cudaEvent_t> side_ev; // [0] fork, [1..] joins
     double* graph_out[2] = {nullptr, nullptr};

@@ -43,18 +43,25 @@ __device__ __forceinline__ float matern32(int nu, float sigma2, float x) {
     return sigma2 * ((1.0f + x * (1.0f + x * (1.0f / 3.0f))) * e);
 }
 
+// Block-wide sums of two values at once (one pair of barriers); valid in thread 0.
 template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ double2 block_sum2(double v, double w, double2* red2) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red2[wp] = make_double2(v, w);
     __syncthreads();
-    double s = 0.0;
+    double2 s = make_double2(0.0, 0.0);
     if (threadIdx.x == 0)
-        for (int i = 0; i < NT / 32; ++i) s += red[i];
+        for (int i = 0; i < NT / 32; ++i) {
+            s.x += red2[i].x;
+            s.y += red2[i].y;
+        }
     __syncthreads();
-    return s;  // valid in thread 0
+    return s;
 }
 
 __device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
@@ -64,11 +71,11 @@ __device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
 // ---------------------------------------------------------------------------------
 // FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2][N+1] | pts[d][N]
 // ---------------------------------------------------------------------------------
-template <int NT>
+template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double* sm = reinterpret_cast<double*>(smraw);
-    __shared__ double red[NT / 32];
+    __shared__ double2 red2[NT / 32];
     __shared__ double etab[32];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -111,7 +118,8 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             }
             // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
             const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
-            double v = matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
+            double v = GEN ? matern64g(a.theta + a.bds[blk], th.nu_code, th.sigma2, x, etab, eK, eL1, eL2)
+                           : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
         }
@@ -177,8 +185,8 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             partu += z * z;
             part += z * z + log(A[pk(k, k)]);
         }
-        const double s = block_sum<NT>(part, red);
-        const double su = block_sum<NT>(partu, red);
+        const double2 s2 = block_sum2<NT>(part, partu, red2);
+        const double s = s2.x, su = s2.y;
         if (tid == 0) {
             double ell = -0.5 * (s + (double)b * kLog2Pi);
             if (s_fail || !(ell == ell)) {
@@ -276,7 +284,7 @@ __host__ __device__ __forceinline__ int mixed_floats(int nmax) {
 // group's shared region (mixed_floats(N) floats, 16-byte aligned).  Returns the group's
 // partial sum of z^2 + log pivot over the block columns in every thread (valid after the
 // caller reduces it) and sets *fail.
-template <int NG, bool WARP>
+template <int NG, bool WARP, bool GEN>
 __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
     const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
     const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
@@ -328,7 +336,10 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                 for (int e = 0; e < 4; ++e) {
                     const int c = (J << 2) + e;
                     const float t0 = rx - cx[e], t1 = ry - cy[e], t2 = rz - cz[e];
-                    float v = matern32(th.nu_code, s2, sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0))));
+                    const float xf = sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0)));
+                    float v = (GEN && th.nu_code == NU_GENERAL)
+                                  ? (float)(th.sigma2 * matern_gen_corr(a.theta[a.bds[blk]], (double)xf))
+                                  : matern32(th.nu_code, s2, xf);
                     if (r == c) v += tau2;
                     o[e] = c <= r ? v : 0.0f;
                 }
@@ -436,20 +447,20 @@ __device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, do
 }
 
 // CTA per block.
-template <int NT>
+template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* sm = reinterpret_cast<float*>(smraw);
-    __shared__ double red[NT / 32];
+    __shared__ double2 red2[NT / 32];
     __shared__ int s_fail;
     const int tid = threadIdx.x;
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int blk = a.work[w];
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        const double2 part = mixed_block<NT, false>(a, blk, sm, tid, &s_fail);
-        const double sres = block_sum<NT>(part.x, red);
-        const double sresu = block_sum<NT>(part.y, red);
+        const double2 part = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail);
+        const double2 sr = block_sum2<NT>(part.x, part.y, red2);
+        const double sres = sr.x, sresu = sr.y;
         if (tid == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, sresu, s_fail);
         __syncthreads();
     }
@@ -457,7 +468,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
 
 // Warp per block: each of the NT/32 warps of a CTA factors its own blocks with warp
 // synchronisation only (small blocks, where CTA-wide barriers dominate).
-template <int NT>
+template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int WPB = NT / 32;
@@ -468,7 +479,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
         const int blk = a.work[w];
         if (lane == 0) s_fail[warp] = 0;
         __syncwarp();
-        double2 part = mixed_block<32, true>(a, blk, sm, lane, &s_fail[warp]);
+        double2 part = mixed_block<32, true, GEN>(a, blk, sm, lane, &s_fail[warp]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
@@ -484,9 +495,9 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
 // Large blocks: same algorithm in FP64 with the packed triangle in a global workspace
 // slot (one slot per CTA; the grid never exceeds the number of slots).
 // ---------------------------------------------------------------------------------
-template <int NT>
+template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
-    __shared__ double red[NT / 32];
+    __shared__ double2 red2[NT / 32];
     __shared__ double etab[32];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -525,7 +536,8 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
                     const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                     acc = fma(t, t, acc);
                 }
-                double v = matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
+                double v = GEN ? matern64g(a.theta + a.bds[blk], th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2)
+                               : matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
                 if (r == c) v += th.nugget;
                 row[c] = v;
             }
@@ -573,8 +585,8 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
             partu += z * z;
             part += z * z + log(A[pk(k, k)]);
         }
-        const double s = block_sum<NT>(part, red);
-        const double su = block_sum<NT>(partu, red);
+        const double2 s2 = block_sum2<NT>(part, partu, red2);
+        const double s = s2.x, su = s2.y;
         if (tid == 0) {
             double ell = -0.5 * (s + (double)b * kLog2Pi);
             if (s_fail || !(ell == ell)) {
@@ -640,20 +652,42 @@ __global__ void k_exp_check(const double* x, double* out, int64_t n, ExpConsts e
     if (i < n) out[i] = exp_neg(x[i], ex.tab, ex.k, ex.l1, ex.l2);
 }
 
+__global__ void k_matern_check(const double* x, double* out, int64_t n, const DevTheta* th, ExpConsts ex) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = matern64g(th, th->nu_code, 1.0, x[i], ex.tab, ex.k, ex.l1, ex.l2);
+}
+
 // Dynamic shared-memory cap of the shared-memory kernels.  Every size bin launches the
 // same instantiation with its own footprint, so the per-function maximum is set once to
 // this cap and never lowered (a launch captured in a graph with a larger footprint must
 // stay valid when a smaller bin is launched later).
 constexpr int kSmemCap = 227 * 1024 - 2048;
 
+template <int NT, bool GEN>
+cudaError_t set_smem_cap_g() {
+    cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_mixed<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_mixed_w<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    return e;
+}
+
 template <int NT>
 cudaError_t set_smem_cap() {
-    cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ll_mixed<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ll_mixed_w<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    return e;
+    cudaError_t e = set_smem_cap_g<NT, false>();
+    return e == cudaSuccess ? set_smem_cap_g<NT, true>() : e;
+}
+
+// GEN: the instantiation that also evaluates K_nu for a general smoothness (chosen when
+// any dataset's nu is not 1/2, 3/2 or 5/2); the others carry no call in their inner loops.
+template <int NT, bool GEN>
+cudaError_t launch_kind_g(int kind, int grid, size_t smem, const LLArgs& a, cudaStream_t s) {
+    if (kind == 0) k_ll_fp64<NT, GEN><<<grid, NT, smem, s>>>(a);
+    else if (kind == 1) k_ll_mixed<NT, GEN><<<grid, NT, smem, s>>>(a);
+    else if (kind == 3) k_ll_mixed_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
+    else k_ll_large<NT, GEN><<<grid, NT, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int NT>
@@ -662,11 +696,7 @@ cudaError_t launch_kind(int kind, int grid, size_t smem, const LLArgs& a, cudaSt
         cudaError_t e = set_smem_cap<NT>();
         if (e != cudaSuccess) return e;
     }
-    if (kind == 0) k_ll_fp64<NT><<<grid, NT, smem, s>>>(a);
-    else if (kind == 1) k_ll_mixed<NT><<<grid, NT, smem, s>>>(a);
-    else if (kind == 3) k_ll_mixed_w<NT><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
-    else k_ll_large<NT><<<grid, NT, 0, s>>>(a);
-    return cudaGetLastError();
+    return a.gen ? launch_kind_g<NT, true>(kind, grid, smem, a, s) : launch_kind_g<NT, false>(kind, grid, smem, a, s);
 }
 
 }  // namespace
@@ -730,13 +760,13 @@ int bv_occupancy(int kind, int threads, size_t smem) {
         if (kind != 2) e = set_smem_cap<NT>();                                                \
         if (e == cudaSuccess) {                                                               \
             if (kind == 0)                                                                    \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT>, NT, smem);  \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT, false>, NT, smem);  \
             else if (kind == 1)                                                               \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT>, NT, smem); \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT, false>, NT, smem); \
             else if (kind == 3)                                                               \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed_w<NT>, NT, smem); \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed_w<NT, false>, NT, smem); \
             else                                                                              \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT>, NT, 0);    \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT, false>, NT, 0);    \
         }                                                                                     \
     }
     BV_OCC(64) BV_OCC(128) BV_OCC(96) BV_OCC(160) BV_OCC(288) BV_OCC(544) BV_OCC(256)
@@ -773,5 +803,31 @@ extern "C" int bv_exp_neg_check(int64_t n, const double* x, double* out) {
     BV_CUDA(cudaMemcpy(out, dy, sizeof(double) * n, cudaMemcpyDeviceToHost));
     cudaFree(dx);
     cudaFree(dy);
+    return BV_OK;
+}
+
+extern "C" int bv_matern_check(double nu, int64_t n, const double* x, double* out) {
+    if (n <= 0 || !x || !out) return BV_EINVAL;
+    bv_theta t{};
+    t.sigma2 = 1.0;
+    t.range[0] = 1.0;
+    t.nu = nu;
+    DevTheta th;
+    BV_TRY(bv_theta_to_dev(&t, 1, &th));
+    ExpConsts ex;
+    bv_exp_consts(&ex);
+    double *dx = nullptr, *dy = nullptr;
+    DevTheta* dth = nullptr;
+    BV_CUDA(cudaMalloc(&dx, sizeof(double) * n));
+    BV_CUDA(cudaMalloc(&dy, sizeof(double) * n));
+    BV_CUDA(cudaMalloc(&dth, sizeof(DevTheta)));
+    BV_CUDA(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice));
+    BV_CUDA(cudaMemcpy(dth, &th, sizeof(DevTheta), cudaMemcpyHostToDevice));
+    k_matern_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, dy, n, dth, ex);
+    BV_CUDA(cudaGetLastError());
+    BV_CUDA(cudaMemcpy(out, dy, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    cudaFree(dx);
+    cudaFree(dy);
+    cudaFree(dth);
     return BV_OK;
 }

@@ -28,6 +28,7 @@
 
 #include <mutex>
 
+#include "bv_device.cuh"
 #include "bv_internal.h"
 
 #define BV_NOALLOC_MAX_DEVICES 64
@@ -55,11 +56,12 @@ __device__ __forceinline__ void na_tri(int f, int& r, int& c) {
     c = f - (rr * (rr + 1) >> 1);
 }
 
-__device__ __forceinline__ double na_matern(int nu, double sigma2, double x) {
+__device__ __forceinline__ double na_matern(const DevTheta& th, double x) {
+    if (th.nu_code == NU_GENERAL) return th.sigma2 * matern_gen_corr(th, x);
     const double e = exp(-x);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
-    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+    if (th.nu_code == NU_HALF) return th.sigma2 * e;
+    if (th.nu_code == NU_3HALF) return th.sigma2 * ((1.0 + x) * e);
+    return th.sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
 }
 
 __global__ void k_na_init(double* s) {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_na_ll(const double* __restrict__ locs, i
                 const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                 acc = fma(t, t, acc);
             }
-            double v = na_matern(th.nu_code, th.sigma2, sqrt(acc));
+            double v = na_matern(th, sqrt(acc));
             if (r == c) v += th.nugget;
             A[f] = v;
         }

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
                 acc = fma(t, t, acc);
             }
             const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
-            double v = matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
+            double v = (th.nu_code == NU_GENERAL ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2));
             if (r == c) v += th.nugget;
             A[f] = v;
         }

@@ -17,17 +17,20 @@
 #include <algorithm>
 #include <vector>
 
+#include "bv_device.cuh"
 #include "bv_internal.h"
 
 namespace {
 
 __device__ __forceinline__ int64_t pk64(int64_t r, int64_t c) { return ((r * (r + 1)) >> 1) + c; }
 
-__device__ __forceinline__ double matern64s(int nu, double sigma2, double x) {
+
+__device__ __forceinline__ double matern64s(const DevTheta& th, double x) {
+    if (th.nu_code == NU_GENERAL) return th.sigma2 * matern_gen_corr(th, x);
     const double e = exp(-x);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
-    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+    if (th.nu_code == NU_HALF) return th.sigma2 * e;
+    if (th.nu_code == NU_3HALF) return th.sigma2 * ((1.0 + x) * e);
+    return th.sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
 }
 
 struct SimArgs {
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(256) k_sim_factor(SimArgs a) {
                     const double t = (px[k * N + r] - px[k * N + c]) * a.th.inv_range[k];
                     acc = fma(t, t, acc);
                 }
-                double v = matern64s(a.th.nu_code, a.th.sigma2, sqrt(acc));
+                double v = matern64s(a.th, sqrt(acc));
                 if (r == c) v += a.th.nugget;
                 A[pk64(r, c)] = v;
             }
