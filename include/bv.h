@@ -277,8 +277,10 @@ int bv_simulate(bv_ctx* ctx, const bv_theta* theta, const double* z, double* y_o
 /* ---- maximum likelihood --------------------------------------------------------- */
 
 /* Bits of bv_mle's free_mask: which parameters the optimizer moves (others stay at
- * theta0).  Ranges move together (anisotropic ranges keep their ratios). */
-enum { BV_FREE_SIGMA2 = 1, BV_FREE_RANGE = 2, BV_FREE_NUGGET = 4 };
+ * theta0).  Ranges move together (anisotropic ranges keep their ratios).  A free
+ * smoothness nu (the paper estimates it, Sec. 3.2) is searched in log nu inside
+ * [lo.nu, hi.nu], hi.nu <= 20; any value other than 1/2, 3/2, 5/2 goes through K_nu. */
+enum { BV_FREE_SIGMA2 = 1, BV_FREE_RANGE = 2, BV_FREE_NUGGET = 4, BV_FREE_NU = 8 };
 
 typedef struct bv_mle_opts {
     int32_t precision;   /* bv_precision of every evaluation                         */
@@ -292,7 +294,7 @@ typedef struct bv_mle_opts {
                                 so a start point can be much surer of sigma^2 and beta */
 } bv_mle_opts;
 
-/* Maximise ell over log(sigma^2), log(beta), log(tau^2) (free_mask selects) inside the
+/* Maximise ell over log(sigma^2), log(beta), log(nu), log(tau^2) (free_mask selects) inside the
  * box [lo, hi] by a bounded Nelder-Mead search (derivative-free, as the paper's BOBYQA,
  * Sec. 3.2).  When sigma^2 is free and the nugget is free or zero, sigma^2 is profiled
  * out: the search runs over log beta and log(tau^2 / sigma^2) and sigma^2 takes its

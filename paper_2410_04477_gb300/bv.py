@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbv.so")
 
 BV_OK, BV_EINVAL, BV_ENOMEM, BV_ECUDA, BV_ENOTPD, BV_ETIMEOUT, BV_ESTATE, BV_EINTERNAL = range(8)
 BV_FP64, BV_MIXED = 0, 1
-BV_FREE_SIGMA2, BV_FREE_RANGE, BV_FREE_NUGGET = 1, 2, 4
+BV_FREE_SIGMA2, BV_FREE_RANGE, BV_FREE_NUGGET, BV_FREE_NU = 1, 2, 4, 8
 BV_NFEAT = 40
 BV_MLP_NPARAM = 39046
 BV_MLP_BLOB = BV_MLP_NPARAM + 2 * BV_NFEAT + 6

@@ -45,9 +45,8 @@ struct Space {
     bv_theta base;
     uint32_t mask;
     int dim;
-    double lo[3], hi[3];  // log-box of sigma^2, range, nugget (in that order, all three)
-    double two_nu;
-    bool profile;         // sigma^2 profiled out; coordinates (log beta, log eta)
+    double lo[4], hi[4];  // log-box of sigma^2, range, nugget, smoothness (in that order)
+    bool profile;         // sigma^2 profiled out; coordinates (log beta, log nu, log eta)
     double n;             // number of observations
 };
 
@@ -55,12 +54,14 @@ struct Space {
 bool to_unit_theta(const Space& S, const double* x, bv_theta* t, double* leta) {
     *t = S.base;
     int k = 0;
-    double lbeta = log(S.base.range[0]);
+    double lbeta = log(S.base.range[0]), lnu = log(S.base.nu);
     *leta = -INFINITY;  // eta = 0 when the nugget is fixed at zero
     if (S.mask & BV_FREE_RANGE) lbeta = x[k++];
+    if (S.mask & BV_FREE_NU) lnu = x[k++];
     if (S.mask & BV_FREE_NUGGET) *leta = x[k++];
-    if (lbeta < S.lo[1] || lbeta > S.hi[1]) return false;
+    if (lbeta < S.lo[1] || lbeta > S.hi[1] || lnu < S.lo[3] || lnu > S.hi[3]) return false;
     t->sigma2 = 1.0;
+    if (S.mask & BV_FREE_NU) t->nu = exp(lnu);
     if (S.mask & BV_FREE_RANGE) {
         const double f = exp(lbeta) / S.base.range[0];
         for (int j = 0; j < 3; ++j) t->range[j] = S.base.range[j] * f;
@@ -88,20 +89,26 @@ bool profile_sigma2(const Space& S, double Q, double leta, double* s2, double* l
 }
 
 // Internal coordinates x -> theta.  x holds, for the free parameters in order:
-// u = log sigma^2 - 2 nu log beta (if sigma^2 free), log beta (if range free), log tau^2.
+// u = log sigma^2 - 2 nu log beta (if sigma^2 free), log beta (if range free), log nu (if
+// the smoothness is free), log tau^2.
 bool to_theta(const Space& S, const double* x, bv_theta* t) {
     *t = S.base;
     int k = 0;
     double lsig = log(S.base.sigma2), lbeta = log(S.base.range[0]), ltau = log(S.base.nugget > 0 ? S.base.nugget : 1e-300);
+    double lnu = log(S.base.nu);
     double u = 0.0;
-    const bool fs = S.mask & BV_FREE_SIGMA2, fr = S.mask & BV_FREE_RANGE, fn = S.mask & BV_FREE_NUGGET;
+    const bool fs = S.mask & BV_FREE_SIGMA2, fr = S.mask & BV_FREE_RANGE, fn = S.mask & BV_FREE_NUGGET,
+               fv = S.mask & BV_FREE_NU;
     if (fs) u = x[k++];
     if (fr) lbeta = x[k++];
+    if (fv) lnu = x[k++];
     if (fn) ltau = x[k++];
-    if (fs) lsig = u + S.two_nu * lbeta;
-    if (lsig < S.lo[0] || lsig > S.hi[0] || lbeta < S.lo[1] || lbeta > S.hi[1] || ltau < S.lo[2] || ltau > S.hi[2])
+    if (fs) lsig = u + 2.0 * exp(lnu) * lbeta;
+    if (lsig < S.lo[0] || lsig > S.hi[0] || lbeta < S.lo[1] || lbeta > S.hi[1] || ltau < S.lo[2] || ltau > S.hi[2] ||
+        lnu < S.lo[3] || lnu > S.hi[3])
         return false;
     if (fs) t->sigma2 = exp(lsig);
+    if (fv) t->nu = exp(lnu);
     if (fr) {
         const double f = exp(lbeta) / S.base.range[0];
         for (int j = 0; j < 3; ++j) t->range[j] = S.base.range[j] * f;
@@ -115,11 +122,13 @@ void from_theta(const Space& S, const bv_theta& t, double* x) {
     const double lb = log(t.range[0]);
     if (S.profile) {
         if (S.mask & BV_FREE_RANGE) x[k++] = lb;
+        if (S.mask & BV_FREE_NU) x[k++] = log(t.nu);
         if (S.mask & BV_FREE_NUGGET) x[k++] = log(t.nugget) - log(t.sigma2);
         return;
     }
-    if (S.mask & BV_FREE_SIGMA2) x[k++] = log(t.sigma2) - S.two_nu * lb;
+    if (S.mask & BV_FREE_SIGMA2) x[k++] = log(t.sigma2) - 2.0 * t.nu * lb;
     if (S.mask & BV_FREE_RANGE) x[k++] = lb;
+    if (S.mask & BV_FREE_NU) x[k++] = log(t.nu);
     if (S.mask & BV_FREE_NUGGET) x[k++] = log(t.nugget);
 }
 
@@ -340,17 +349,18 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
     if (!c || !theta0 || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
     if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
     if (!c->have_nn) return BV_ESTATE;
-    if ((free_mask & ~7u) != 0 || free_mask == 0) return BV_EINVAL;
+    if ((free_mask & ~15u) != 0 || free_mask == 0) return BV_EINVAL;
     if (opts->max_evals < 1 || opts->init_step <= 0.0) return BV_EINVAL;
     if (opts->precision != BV_FP64 && opts->precision != BV_MIXED) return BV_EINVAL;
     Space S;
     S.base = *theta0;
     S.mask = free_mask;
-    S.two_nu = 2.0 * theta0->nu;
-    const double vals[3] = {theta0->sigma2, theta0->range[0], theta0->nugget};
-    const double los[3] = {lo->sigma2, lo->range[0], lo->nugget}, his[3] = {hi->sigma2, hi->range[0], hi->nugget};
+    const double vals[4] = {theta0->sigma2, theta0->range[0], theta0->nugget, theta0->nu};
+    const double los[4] = {lo->sigma2, lo->range[0], lo->nugget, lo->nu};
+    const double his[4] = {hi->sigma2, hi->range[0], hi->nugget, hi->nu};
+    if ((free_mask & BV_FREE_NU) && !(his[3] <= BV_NU_MAX)) return BV_EINVAL;
     S.dim = 0;
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < 4; ++j) {
         if (!(free_mask & (1u << j))) {  // fixed parameters are never checked against the box
             S.lo[j] = -1e300;
             S.hi[j] = 1e300;
@@ -370,6 +380,7 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
         for (int j = 0; j < 3; ++j) t0.range[j] *= f;
     }
     if (free_mask & BV_FREE_NUGGET) t0.nugget = std::min(his[2], std::max(los[2], t0.nugget));
+    if (free_mask & BV_FREE_NU) t0.nu = std::min(his[3], std::max(los[3], t0.nu));
     S.base = t0;
     S.n = (double)c->n_tot;
     S.profile = (free_mask & BV_FREE_SIGMA2) && ((free_mask & BV_FREE_NUGGET) || t0.nugget == 0.0);

@@ -147,3 +147,23 @@ def test_mle_with_all_earlier_points_is_the_exact_mle(bv):
         th, ll, _ = ctx.mle(bv.theta(1.0, 0.1, nu, 1e-2), lo, hi, ftol_rel=1e-13, xtol=1e-8)
     assert abs(ll + r.fun) <= 1e-10 * abs(r.fun), (ll, -r.fun)
     np.testing.assert_allclose([np.log(th.sigma2), np.log(th.range[0]), np.log(th.nugget)], r.x, atol=2e-3)
+
+
+def test_mle_with_free_smoothness(bv):
+    # nu free (Sec. 3.2 estimates it): a stationary maximum in all four log-parameters,
+    # at least as high as the maximum with nu held at its true value
+    locs, y, st, bc, m, seed = _problem(n=4000, nu=1.2, s2=1.1, beta=0.06, tau2=5e-3, seed=35, bc=400, m=40)
+    lo, hi = bv.theta(0.01, 0.001, 0.2, 1e-6), bv.theta(100.0, 3.0, 5.0, 10.0)
+    free = bv.BV_FREE_SIGMA2 | bv.BV_FREE_RANGE | bv.BV_FREE_NUGGET | bv.BV_FREE_NU
+    with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
+        th, ll, ne = ctx.mle(bv.theta(1.0, 0.1, 0.8, 1e-2), lo, hi, free_mask=free, ftol_rel=1e-13, xtol=1e-7)
+        _, ll_fix, _ = ctx.mle(bv.theta(1.0, 0.1, 1.2, 1e-2), lo, hi, ftol_rel=1e-13, xtol=1e-7)
+        assert ll >= ll_fix - 1e-9 * abs(ll)
+        assert abs(th.nu - 1.2) < 0.3, th.nu
+        assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)
+        for k in range(4):
+            for sgn in (-1, 1):
+                v = [th.sigma2, th.range[0], th.nugget, th.nu]
+                v[k] *= np.exp(sgn * 1e-3)
+                assert ctx.loglik(bv.theta(v[0], v[1], v[3], v[2])) < ll
+    assert abs(ll - _oracle_ell(th, locs, y, st)) <= 1e-10 * abs(ll)
