@@ -42,6 +42,9 @@ WORKLOADS = {
                    seed=1, gen_m=400),
     "c2_m120": dict(n=200_000, d=2, bc=20_000, m=120, nu=1.5, sigma2=1.0, beta=0.05,
                     nugget=1e-4, seed=1, gen_m=400),
+    # general smoothness (K_nu path): the config-2 shape at nu = 1.2
+    "c2_nu12": dict(n=200_000, d=2, bc=20_000, m=60, nu=1.2, sigma2=1.0, beta=0.05, nugget=1e-4,
+                    seed=1, gen_m=400),
     # 3D profile: 20,000 sites x 50 jittered levels = 1e6 points, anisotropic range
     "c3": dict(n=1_000_000, d=3, sites=20_000, levels=50, bc=100_000, m=200, nu=0.5, sigma2=1.0,
                beta=0.1, ranges=[0.1, 0.1, 0.3], nugget=1e-3, seed=2, gen_m=400),

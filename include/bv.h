@@ -258,8 +258,9 @@ int bv_plan_info(bv_ctx* ctx, int32_t precision, int32_t* launches_per_eval, int
 
 /* Test support: the device's Matern correlation rho(x) of Eq. 5 (sigma^2 = 1, beta = 1)
  * at n scaled distances x (host arrays), for 0 < nu <= 20; the half-integers use their
- * closed forms, any other nu the library's K_nu (Temme's series / continued fraction). */
-int bv_matern_check(double nu, int64_t n, const double* x, double* out);
+ * closed forms, any other nu the library's K_nu (Temme's series / continued fraction) or,
+ * with tabulated != 0, the per-evaluation octave table the log-likelihood kernels use. */
+int bv_matern_check(double nu, int32_t tabulated, int64_t n, const double* x, double* out);
 
 /* Diagnostic: the library's device FP64 exponential e^{-x} (x >= 0; Tang's table-driven
  * method, used for the Matern kernel in the FP64 path) evaluated on the GPU for host

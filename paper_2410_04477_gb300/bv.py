@@ -92,7 +92,7 @@ _SIGS = {
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
-    "bv_matern_check": (_int, [_d, _i64, _P(_d), _P(_d)]),
+    "bv_matern_check": (_int, [_d, _i32, _i64, _P(_d), _P(_d)]),
     "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
@@ -172,11 +172,12 @@ def exact_flops(n):
     return f.value
 
 
-def matern_check(nu, x):
+def matern_check(nu, x, tabulated=False):
     """Device Matern correlation at scaled distances x (test support)."""
     xv = _arr(x, np.float64)
     out = np.empty_like(xv)
-    _check(_lib.bv_matern_check(float(nu), xv.size, _p(xv, _d), _p(out, _d)), "bv_matern_check")
+    _check(_lib.bv_matern_check(float(nu), 1 if tabulated else 0, xv.size, _p(xv, _d), _p(out, _d)),
+           "bv_matern_check")
     return out
 
 

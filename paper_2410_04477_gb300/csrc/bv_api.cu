@@ -96,6 +96,7 @@ static void free_data(bv_ctx* c) {
     if (c->h_quad) cudaFreeHost(c->h_quad);
     c->h_quad = nullptr;
     dfree(c->d_theta);
+    dfree(c->d_gtab);
     if (c->h_out) cudaFreeHost(c->h_out);
     c->h_out = nullptr;
     c->h_theta.clear();
@@ -193,6 +194,7 @@ extern "C" int bv_set_datasets(bv_ctx* c, int32_t ndata, const int64_t* n_per, c
     BV_CUDA(cudaMalloc(&c->d_quad, sizeof(double) * ndata));
     BV_CUDA(cudaMallocHost(&c->h_quad, sizeof(double) * ndata));
     BV_CUDA(cudaMalloc(&c->d_theta, sizeof(DevTheta) * ndata));
+    BV_CUDA(cudaMalloc(&c->d_gtab, sizeof(double) * BV_GTAB_DOUBLES * ndata));
     BV_CUDA(cudaMallocHost(&c->h_out, sizeof(double) * ndata));
     c->h_theta.assign(ndata, DevTheta{});
     BV_CUDA(cudaMemcpyAsync(c->d_locs, soa.data(), sizeof(double) * n_tot * d, cudaMemcpyHostToDevice,
@@ -643,6 +645,7 @@ static LLArgs make_args(bv_ctx* c) {
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
     a.gen = c->cur_gen ? 1 : 0;
+    a.gtab = c->d_gtab;
     bv_exp_consts(&a.ex);
     return a;
 }
@@ -731,6 +734,7 @@ static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     cudaEventCreate(&e1);
     const LLArgs a = make_args(c);
     float best = 1e30f;
+    if (c->cur_gen && bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream) != cudaSuccess) return best;
     for (int r = 0; r < reps + 1; ++r) {
         cudaEventRecord(e0, c->stream);
         cudaError_t e = bv_launch_bin(bp, a, c->stream);
@@ -823,6 +827,7 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         c->side_ev.push_back(e);
     }
     BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
+    if (c->cur_gen) BV_CUDA(bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream));
     BV_CUDA(cudaEventRecord(c->side_ev[0], c->stream));
     const LLArgs a = make_args(c);
     for (size_t i = 0; i < nb; ++i) {

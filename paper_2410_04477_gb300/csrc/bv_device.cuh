@@ -54,10 +54,8 @@ __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ t
 // J. Comput. Phys. 19, 1975) and from Steed's evaluation of Temme's continued fraction
 // for x > 2 (Thompson and Barnett, J. Comput. Phys. 64, 1986); the upward recurrence
 // K_{a+1} = K_{a-1} + (2a/x) K_a (stable for K) reaches nu = nrec + mu.  The product with
-// x^nu is formed in logarithms.
-__device__ __noinline__ double matern_gen_corr(const DevTheta& th, double x) {
-    if (!(x > 0.0)) return 1.0;
-    if (x > 740.0) return 0.0;
+// x^nu is formed in logarithms: the routine returns log rho(x) for x > 0.
+__device__ __noinline__ double matern_gen_logcorr(const DevTheta& th, double x) {
     const double mu = th.mu, eps = 1e-17;
     double kmu, kmu1;
     if (x <= 2.0) {
@@ -126,7 +124,45 @@ __device__ __noinline__ double matern_gen_corr(const DevTheta& th, double x) {
         knu = kn;
     }
     const double lk = log(knu) - (x > 2.0 ? x : 0.0);
-    return exp(th.lognorm + th.nu * log(x) + lk);
+    return th.lognorm + th.nu * log(x) + lk;
+}
+
+__device__ __forceinline__ double matern_gen_corr(const DevTheta& th, double x) {
+    if (!(x > 0.0)) return 1.0;
+    if (x > 745.0) return 0.0;
+    return exp(matern_gen_logcorr(th, x));
+}
+
+// Per-evaluation table of a general-nu Matern (built by k_gtab_build for every dataset):
+// on each octave [2^e, 2^{e+1}), e = GTAB_E0 .. GTAB_E0 + GTAB_NOCT - 1, the Chebyshev
+// expansion of degree GTAB_DEG - 1 of L(x) = x + log rho(x) in t = 2 x / 2^e - 3.  L has
+// its only singularity at x = 0, so each octave converges at the same geometric rate,
+// and rho = exp(-(x - L)) keeps the relative accuracy over the whole range (about 1e-13
+// for nu <= 20).  Distances outside the tabulated octaves use K_nu directly.
+#define GTAB_E0 (-40)
+#define GTAB_NOCT 49
+#define GTAB_DEG 19
+#define GTAB_SIZE (GTAB_NOCT * GTAB_DEG)
+
+__device__ __forceinline__ double matern_gen_tab(const double* __restrict__ tab, const DevTheta* __restrict__ g,
+                                                 double x, const double* etab, double K, double L1, double L2) {
+    const long long ux = __double_as_longlong(x);
+    const int ex = (int)((ux >> 52) & 0x7ff) - 1023;
+    const int o = ex - GTAB_E0;
+    if (x == 0.0) return 1.0;
+    if (o < 0 || o >= GTAB_NOCT) return matern_gen_corr(*g, x);
+    const double m = __longlong_as_double((ux & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);  // [1, 2)
+    const double t = 2.0 * m - 3.0;
+    const double* c = tab + o * GTAB_DEG;
+    double b1 = 0.0, b2 = 0.0;
+#pragma unroll
+    for (int k = GTAB_DEG - 1; k >= 1; --k) {
+        const double b0 = fma(2.0 * t, b1, c[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    const double L = fma(t, b1, c[0] - b2);
+    return exp_neg(fmax(x - L, 0.0), etab, K, L1, L2);
 }
 
 // Matern covariance sigma^2 rho(x) at scaled distance x (Eq. 5, half-integer closed forms
@@ -139,12 +175,34 @@ __device__ __forceinline__ double matern64t(int nu, double sigma2, double x, con
     return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
 }
 
-// Any nu: closed forms for the half-integers, K_nu otherwise.  `g` points at the theta in
-// global memory, so the general branch reads its constants there and the caller keeps
-// only the fields it uses in registers.
-__device__ __forceinline__ double matern64g(const DevTheta* __restrict__ g, int nu, double sigma2, double x,
-                                            const double* tab, double K, double L1, double L2) {
-    if (nu == NU_GENERAL) return sigma2 * matern_gen_corr(*g, x);
+// FP32 evaluation of the same table (mixed precision: covariance entries are FP32).
+__device__ __forceinline__ float matern_gen_tab32(const double* __restrict__ tab, const DevTheta* __restrict__ g,
+                                                  float x) {
+    const int ux = __float_as_int(x);
+    const int ex = ((ux >> 23) & 0xff) - 127;
+    const int o = ex - GTAB_E0;
+    if (x == 0.0f) return 1.0f;
+    if (o < 0 || o >= GTAB_NOCT) return (float)matern_gen_corr(*g, (double)x);
+    const float m = __int_as_float((ux & 0x007FFFFF) | 0x3F800000);  // [1, 2)
+    const float t = 2.0f * m - 3.0f;
+    const double* c = tab + o * GTAB_DEG;
+    float b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+    for (int k = GTAB_DEG - 1; k >= 1; --k) {
+        const float b0 = fmaf(2.0f * t, b1, (float)c[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    const float L = fmaf(t, b1, (float)c[0] - b2);
+    return expf(-fmaxf(x - L, 0.0f));
+}
+
+// Any nu: closed forms for the half-integers, the dataset's table otherwise.  `g` points
+// at the theta in global memory (read only off the table's range).
+__device__ __forceinline__ double matern64g(const double* __restrict__ gtab, const DevTheta* __restrict__ g, int nu,
+                                            double sigma2, double x, const double* tab, double K, double L1,
+                                            double L2) {
+    if (nu == NU_GENERAL) return sigma2 * matern_gen_tab(gtab, g, x, tab, K, L1, L2);
     return matern64t(nu, sigma2, x, tab, K, L1, L2);
 }
 

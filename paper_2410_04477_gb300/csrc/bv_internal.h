@@ -81,6 +81,7 @@ struct LLArgs {
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
     int gen;                 // host side: launch the general-smoothness instantiation
+    const double* gtab;      // per dataset: general-nu Matern table (GTAB_SIZE doubles)
     double* ell_blk;         // per-block conditional log-likelihood (output)
     double* u_blk;           // per-block quadratic form u_i = v_i^T v_i (output)
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
@@ -113,6 +114,9 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a, cudaStream_t s);
 cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_blk_off,
                              int32_t ndata, double* out, double* out_quad, cudaStream_t s);
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
+// Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
+cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s);
+#define BV_GTAB_DOUBLES 931  // GTAB_NOCT * GTAB_DEG
 
 // K-means and neighbour search (bv_kmeans.cu, bv_nn.cu).
 int bv_kmeans_device(const double* d_locs_soa, int64_t n_tot, int64_t off, int64_t n, int d,
@@ -193,6 +197,7 @@ struct bv_ctx {
     double* d_out = nullptr;          // ndata
     double* h_out = nullptr;          // pinned, ndata
     DevTheta* d_theta = nullptr;      // ndata
+    double* d_gtab = nullptr;         // ndata x BV_GTAB_DOUBLES general-nu Matern tables
     std::vector<DevTheta> h_theta;    // ndata (pageable: copies are staged by the driver)
     unsigned long long* h_fail = nullptr;  // pinned
     double* d_ws = nullptr;

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             }
             // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
             const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
-            double v = GEN ? matern64g(a.theta + a.bds[blk], th.nu_code, th.sigma2, x, etab, eK, eL1, eL2)
+            double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
+                                       th.sigma2, x, etab, eK, eL1, eL2)
                            : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
@@ -338,7 +339,8 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                     const float t0 = rx - cx[e], t1 = ry - cy[e], t2 = rz - cz[e];
                     const float xf = sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0)));
                     float v = (GEN && th.nu_code == NU_GENERAL)
-                                  ? (float)(th.sigma2 * matern_gen_corr(a.theta[a.bds[blk]], (double)xf))
+                                  ? s2 * matern_gen_tab32(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE,
+                                                          a.theta + a.bds[blk], xf)
                                   : matern32(th.nu_code, s2, xf);
                     if (r == c) v += tau2;
                     o[e] = c <= r ? v : 0.0f;
@@ -536,7 +538,8 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
                     const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
                     acc = fma(t, t, acc);
                 }
-                double v = GEN ? matern64g(a.theta + a.bds[blk], th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2)
+                double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
+                                           th.sigma2, sqrt(acc), etab, eK, eL1, eL2)
                                : matern64t(th.nu_code, th.sigma2, sqrt(acc), etab, eK, eL1, eL2);
                 if (r == c) v += th.nugget;
                 row[c] = v;
@@ -652,9 +655,35 @@ __global__ void k_exp_check(const double* x, double* out, int64_t n, ExpConsts e
     if (i < n) out[i] = exp_neg(x[i], ex.tab, ex.k, ex.l1, ex.l2);
 }
 
-__global__ void k_matern_check(const double* x, double* out, int64_t n, const DevTheta* th, ExpConsts ex) {
+// One CTA per dataset: L(x) = x + log rho(x) at the Chebyshev nodes of every octave, then
+// the coefficients c_k = (2 / D) sum_j L_j cos(pi k (j + 1/2) / D), c_0 halved.
+__global__ void __launch_bounds__(1024) k_gtab_build(const DevTheta* theta, double* gtab) {
+    __shared__ double node[GTAB_SIZE];
+    const DevTheta* g = theta + blockIdx.x;
+    if (g->nu_code != NU_GENERAL) return;
+    double* out = gtab + (int64_t)blockIdx.x * GTAB_SIZE;
+    for (int f = threadIdx.x; f < GTAB_SIZE; f += blockDim.x) {
+        const int o = f / GTAB_DEG, j = f % GTAB_DEG;
+        const double a = ldexp(1.0, o + GTAB_E0);
+        const double x = a * (1.5 + 0.5 * cospi((j + 0.5) / GTAB_DEG));
+        node[f] = x + matern_gen_logcorr(*g, x);
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < GTAB_SIZE; f += blockDim.x) {
+        const int o = f / GTAB_DEG, k = f % GTAB_DEG;
+        double s = 0.0;
+        for (int j = 0; j < GTAB_DEG; ++j) s = fma(node[o * GTAB_DEG + j], cospi(k * (j + 0.5) / GTAB_DEG), s);
+        s *= 2.0 / GTAB_DEG;
+        out[f] = k == 0 ? 0.5 * s : s;
+    }
+}
+
+__global__ void k_matern_check(const double* x, double* out, int64_t n, const DevTheta* th, const double* gtab,
+                               int tabulated, ExpConsts ex) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = matern64g(th, th->nu_code, 1.0, x[i], ex.tab, ex.k, ex.l1, ex.l2);
+    if (i >= n) return;
+    if (th->nu_code == NU_GENERAL && !tabulated) out[i] = matern_gen_corr(*th, x[i]);
+    else out[i] = matern64g(gtab, th, th->nu_code, 1.0, x[i], ex.tab, ex.k, ex.l1, ex.l2);
 }
 
 // Dynamic shared-memory cap of the shared-memory kernels.  Every size bin launches the
@@ -746,6 +775,11 @@ cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const i
     return cudaGetLastError();
 }
 
+cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s) {
+    k_gtab_build<<<ndata, 1024, 0, s>>>(theta, gtab);
+    return cudaGetLastError();
+}
+
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {
     k_fail_reset<<<1, 1, 0, s>>>(fail);
     return cudaGetLastError();
@@ -806,7 +840,7 @@ extern "C" int bv_exp_neg_check(int64_t n, const double* x, double* out) {
     return BV_OK;
 }
 
-extern "C" int bv_matern_check(double nu, int64_t n, const double* x, double* out) {
+extern "C" int bv_matern_check(double nu, int32_t tabulated, int64_t n, const double* x, double* out) {
     if (n <= 0 || !x || !out) return BV_EINVAL;
     bv_theta t{};
     t.sigma2 = 1.0;
@@ -816,18 +850,22 @@ extern "C" int bv_matern_check(double nu, int64_t n, const double* x, double* ou
     BV_TRY(bv_theta_to_dev(&t, 1, &th));
     ExpConsts ex;
     bv_exp_consts(&ex);
-    double *dx = nullptr, *dy = nullptr;
+    double *dx = nullptr, *dy = nullptr, *dtab = nullptr;
     DevTheta* dth = nullptr;
     BV_CUDA(cudaMalloc(&dx, sizeof(double) * n));
     BV_CUDA(cudaMalloc(&dy, sizeof(double) * n));
     BV_CUDA(cudaMalloc(&dth, sizeof(DevTheta)));
+    BV_CUDA(cudaMalloc(&dtab, sizeof(double) * GTAB_SIZE));
     BV_CUDA(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice));
     BV_CUDA(cudaMemcpy(dth, &th, sizeof(DevTheta), cudaMemcpyHostToDevice));
-    k_matern_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, dy, n, dth, ex);
+    k_gtab_build<<<1, 1024>>>(dth, dtab);
+    BV_CUDA(cudaGetLastError());
+    k_matern_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, dy, n, dth, dtab, tabulated, ex);
     BV_CUDA(cudaGetLastError());
     BV_CUDA(cudaMemcpy(out, dy, sizeof(double) * n, cudaMemcpyDeviceToHost));
     cudaFree(dx);
     cudaFree(dy);
     cudaFree(dth);
+    cudaFree(dtab);
     return BV_OK;
 }

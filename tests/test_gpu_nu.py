@@ -28,6 +28,10 @@ def test_device_matern_matches_scipy(bv, nu):
     got = bv.matern_check(nu, x)
     want = _ref.matern_kv(nu, x)
     np.testing.assert_allclose(got, want, rtol=2e-13, atol=1e-300)
+    # the per-evaluation octave table of the log-likelihood kernels, out to 600
+    xt = np.concatenate([x, np.logspace(np.log10(60.0), np.log10(600.0), 50), [1e-13, 2.0 ** -40, 511.9, 512.0]])
+    tab = bv.matern_check(nu, xt, tabulated=True)
+    np.testing.assert_allclose(tab, _ref.matern_kv(nu, xt), rtol=5e-13, atol=1e-300)
 
 
 @pytest.mark.parametrize("nu,beta,tau2", [(0.3, 0.1, 1e-3), (0.8, 0.08, 1e-4), (1.2, 0.05, 1e-3),
