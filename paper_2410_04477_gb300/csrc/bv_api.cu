@@ -78,6 +78,7 @@ static void free_blocks(bv_ctx* c) {
     dfree(c->d_ds_blk_off);
     dfree(c->d_ell_blk);
     dfree(c->d_u_blk);
+    dfree(c->d_red_part);
     c->h_bptr.clear();
     c->h_pidx.clear();
     c->h_bds.clear();
@@ -240,6 +241,12 @@ static int upload_blocks(bv_ctx* c, const std::vector<double>& cent) {
     BV_CUDA(cudaMalloc(&c->d_ds_blk_off, sizeof(int64_t) * (c->ndata + 1)));
     BV_CUDA(cudaMalloc(&c->d_ell_blk, sizeof(double) * nb));
     BV_CUDA(cudaMalloc(&c->d_u_blk, sizeof(double) * nb));
+    {
+        int64_t mx = 1;
+        for (int k = 0; k < c->ndata; ++k) mx = std::max<int64_t>(mx, c->ds_blk_off[k + 1] - c->ds_blk_off[k]);
+        c->red_chunks = bv_reduce_chunks(mx);
+        BV_CUDA(cudaMalloc(&c->d_red_part, sizeof(double) * 4 * (size_t)c->ndata * c->red_chunks));
+    }
     BV_CUDA(cudaMemcpyAsync(c->d_bptr, c->h_bptr.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
                             c->stream));
     BV_CUDA(cudaMemcpyAsync(c->d_pidx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot, cudaMemcpyHostToDevice,
@@ -775,6 +782,9 @@ static int autotune(bv_ctx* c, int prec) {
             trial.threads = kt.second;
             if (set_grid(c, trial) != BV_OK) continue;
             const float ms = time_bin(c, trial, 2);
+            if (getenv("BV_LOG_PLAN") && atoi(getenv("BV_LOG_PLAN")) >= 2)
+                fprintf(stderr, "[bv plan]   candidate kind %d threads %d grid %d: %.3f ms\n", trial.kind,
+                        trial.threads, trial.grid, ms);
             if (ms < best_ms) {
                 best_ms = ms;
                 best_k = kt.first;
@@ -836,7 +846,8 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
     }
     for (size_t i = 0; i < nb; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
-    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->d_out, c->d_quad, c->stream));
+    BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->red_chunks, c->d_red_part,
+                             c->d_out, c->d_quad, c->stream));
     return BV_OK;
 }
 
@@ -939,7 +950,8 @@ extern "C" int bv_plan_info(bv_ctx* c, int32_t prec, int32_t* launches, int32_t*
     if (!c->have_nn) return BV_ESTATE;
     BV_CUDA(cudaSetDevice(c->device));
     BV_TRY(bv_ensure_plan(c, prec));
-    if (launches) *launches = (int32_t)c->plan[prec].size() + 2;  // bins + failure reset + reduction
+    // bins + failure reset + two reduction stages (+ the general-nu table)
+    if (launches) *launches = (int32_t)c->plan[prec].size() + 3 + (c->cur_gen ? 1 : 0);
     if (nbins) *nbins = (int32_t)c->plan[prec].size();
     double f = 0.0, e = 0.0;
     for (int64_t i = 0; i < c->nblk; ++i) {

@@ -111,8 +111,12 @@ int bv_occupancy(int kind, int threads, size_t smem);
 // Largest augmented size the global-memory path accepts (packed indices stay in int32).
 #define BV_LARGE_MAX_N 30000
 cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a, cudaStream_t s);
+// Per-dataset sums of ell_i and u_i in two deterministic stages; part holds
+// ndata x maxchunks partials of 4 doubles; maxchunks = bv_reduce_chunks(largest dataset).
+int bv_reduce_chunks(int64_t max_blocks_per_dataset);
 cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_blk_off,
-                             int32_t ndata, double* out, double* out_quad, cudaStream_t s);
+                             int32_t ndata, int32_t maxchunks, void* part, double* out, double* out_quad,
+                             cudaStream_t s);
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
 // Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
 cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s);
@@ -191,6 +195,8 @@ struct bv_ctx {
     // evaluation state
     double* d_ell_blk = nullptr;
     double* d_u_blk = nullptr;        // per-block quadratic forms
+    double* d_red_part = nullptr;     // reduction partials (ndata x red_chunks x 4)
+    int32_t red_chunks = 1;
     double* d_quad = nullptr;         // ndata: sum of the quadratic forms
     double* h_quad = nullptr;         // pinned, ndata
     unsigned long long* d_fail = nullptr;

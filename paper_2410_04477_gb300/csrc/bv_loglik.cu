@@ -29,6 +29,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "bv_device.cuh"
 #include "bv_internal.h"
 
@@ -614,38 +616,66 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     s = t;
 }
 
-// Fixed-order compensated sums of a per-block array over one dataset's blocks.
-__device__ double dataset_sum(const double* v, int64_t lo, int64_t hi, double* ss, double* sc) {
-    const int tid = threadIdx.x;
-    double s = 0.0, c = 0.0;
-    for (int64_t i = lo + tid; i < hi; i += 256) neumaier_add(s, c, v[i]);
-    ss[tid] = s;
-    sc[tid] = c;
-    __syncthreads();
-    double r = 0.0;
-    if (tid == 0) {
-        double S = 0.0, C = 0.0;
-        for (int i = 0; i < 256; ++i) {
-            neumaier_add(S, C, ss[i]);
-            C += sc[i];
-        }
-        r = S + C;
-    }
-    __syncthreads();
-    return r;
+// Deterministic two-stage compensated sums of the per-block ell_i and u_i of every
+// dataset (the order depends only on the block order, never on the launch plan).
+// Stage 1: CTA (x, ds) sums blocks [lo + x C, lo + (x+1) C) of dataset ds, C = kRedChunk:
+// each thread a Neumaier sum over its strided elements, then a fixed binary tree of
+// (sum, compensation) pairs.  Stage 2: one thread per dataset adds its chunks in order.
+// Spreading stage 1 over many SMs matters on this part, whose FP64 rate per SM is low.
+constexpr int kRedChunk = 1024;
+
+__device__ __forceinline__ void pair_add(double& S, double& C, double s, double c) {
+    neumaier_add(S, C, s);
+    C += c;
 }
 
-__global__ void __launch_bounds__(256) k_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_off,
-                                                double* out, double* out_quad) {
-    __shared__ double ss[256], sc[256];
-    const int ds = blockIdx.x;
-    const int64_t lo = ds_off[ds], hi = ds_off[ds + 1];
-    const double l = dataset_sum(ell_blk, lo, hi, ss, sc);
-    const double q = dataset_sum(u_blk, lo, hi, ss, sc);
-    if (threadIdx.x == 0) {
-        out[ds] = (l == l) ? l : -INFINITY;
-        out_quad[ds] = q;
+__global__ void __launch_bounds__(256) k_reduce_part(const double* __restrict__ ell_blk,
+                                                     const double* __restrict__ u_blk, const int64_t* ds_off,
+                                                     int maxchunks, double4_16a* part) {
+    __shared__ double4_16a sh[256];
+    const int ds = blockIdx.y, tid = threadIdx.x;
+    const int64_t end = ds_off[ds + 1];
+    const int64_t lo = ds_off[ds] + (int64_t)blockIdx.x * kRedChunk;
+    if (lo >= end) return;
+    const int64_t hi = min(end, lo + (int64_t)kRedChunk);
+    double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0;
+    for (int64_t i = lo + tid; i < hi; i += 256) {
+        neumaier_add(s1, c1, ell_blk[i]);
+        neumaier_add(s2, c2, u_blk[i]);
     }
+    sh[tid].x = s1;
+    sh[tid].y = c1;
+    sh[tid].z = s2;
+    sh[tid].w = c2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+            double4_16a a = sh[tid];
+            const double4_16a b = sh[tid + w];
+            pair_add(a.x, a.y, b.x, b.y);
+            pair_add(a.z, a.w, b.z, b.w);
+            sh[tid] = a;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) part[(int64_t)ds * maxchunks + blockIdx.x] = sh[0];
+}
+
+__global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64_t* ds_off, int ndata, int maxchunks,
+                               double* out, double* out_quad) {
+    const int ds = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ds >= ndata) return;
+    const int64_t nb = ds_off[ds + 1] - ds_off[ds];
+    const int nch = (int)((nb + kRedChunk - 1) / kRedChunk);
+    double S1 = 0.0, C1 = 0.0, S2 = 0.0, C2 = 0.0;
+    for (int ch = 0; ch < nch; ++ch) {
+        const double4_16a p = part[(int64_t)ds * maxchunks + ch];
+        pair_add(S1, C1, p.x, p.y);
+        pair_add(S2, C2, p.z, p.w);
+    }
+    const double l = S1 + C1;
+    out[ds] = (l == l) ? l : -INFINITY;
+    out_quad[ds] = S2 + C2;
 }
 
 __global__ void k_fail_reset(unsigned long long* f) { *f = ~0ull; }
@@ -769,9 +799,19 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     }
 }
 
+int bv_reduce_chunks(int64_t max_blocks_per_dataset) {
+    return (int)std::max<int64_t>(1, (max_blocks_per_dataset + kRedChunk - 1) / kRedChunk);
+}
+
 cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const int64_t* ds_blk_off,
-                             int32_t ndata, double* out, double* out_quad, cudaStream_t s) {
-    k_reduce<<<ndata, 256, 0, s>>>(ell_blk, u_blk, ds_blk_off, out, out_quad);
+                             int32_t ndata, int32_t maxchunks, void* part, double* out, double* out_quad,
+                             cudaStream_t s) {
+    k_reduce_part<<<dim3(maxchunks, ndata), 256, 0, s>>>(ell_blk, u_blk, ds_blk_off, maxchunks,
+                                                         static_cast<double4_16a*>(part));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<(ndata + 127) / 128, 128, 0, s>>>(static_cast<const double4_16a*>(part), ds_blk_off, ndata,
+                                                       maxchunks, out, out_quad);
     return cudaGetLastError();
 }
 
