@@ -212,6 +212,9 @@ int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
 int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
                     double* d_out_loglik);
 
+/* First failing block (not positive definite) of the last synchronous evaluation, or -1. */
+int bv_last_error_block(bv_ctx* ctx, int64_t* block);
+
 /* Wait for the context's stream; report any device-side failure since the last check
  * (BV_ENOTPD with the first failing block in *failed_block, may be NULL). */
 int bv_sync(bv_ctx* ctx, int64_t* failed_block);
@@ -300,7 +303,8 @@ typedef struct bv_mle_opts {
  * Sec. 3.2).  When sigma^2 is free and the nugget is free or zero, sigma^2 is profiled
  * out: the search runs over log beta and log(tau^2 / sigma^2) and sigma^2 takes its
  * closed-form maximiser Q / n (bv_loglik_terms) clamped to the box.  theta0: start
- * point.  Outputs: theta_hat, loglik_hat (the FP64 ell at theta_hat), n_evals.
+ * point, or NULL for the learned warm start (bv_warmstart_load first; it is applied to
+ * the geometric centre of [lo, hi], whose smoothness and range ratios it keeps).  Outputs: theta_hat, loglik_hat (the FP64 ell at theta_hat), n_evals.
  * Synchronous (one device evaluation per optimizer step). */
 int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,

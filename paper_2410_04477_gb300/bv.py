@@ -88,6 +88,7 @@ _SIGS = {
     "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
+    "bv_last_error_block": (_int, [_vp, _P(_i64)]),
     "bv_loglik_noalloc": (_int, [_P(bv_theta), _vp, _vp, _i64, _i32, _i64, _vp, _vp, _vp, _vp,
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
@@ -418,6 +419,12 @@ class Context:
                                      ctypes.byref(b)), "bv_kl_divergence")
         return k.value, a.value, b.value
 
+    def last_error_block(self):
+        """First failing block of the last synchronous evaluation, or -1."""
+        b = ctypes.c_int64(0)
+        _check(_lib.bv_last_error_block(self.h, ctypes.byref(b)), "bv_last_error_block")
+        return b.value
+
     def loglik_terms(self, th: bv_theta, precision=BV_FP64):
         """(ell, quad, logdet) with ell = -(quad + logdet + n log 2 pi) / 2."""
         l, q, d = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
@@ -466,7 +473,7 @@ class Context:
         out = bv_theta()
         ll = ctypes.c_double(0.0)
         ne = ctypes.c_int32(0)
-        _check(_lib.bv_mle(self.h, ctypes.byref(th0), ctypes.byref(lo), ctypes.byref(hi),
+        _check(_lib.bv_mle(self.h, ctypes.byref(th0) if th0 is not None else None, ctypes.byref(lo), ctypes.byref(hi),
                            free_mask, ctypes.byref(o), ctypes.byref(out), ctypes.byref(ll),
                            ctypes.byref(ne)), "bv_mle")
         return out, ll.value, ne.value

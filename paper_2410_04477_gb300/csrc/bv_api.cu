@@ -976,3 +976,9 @@ extern "C" int bv_loglik_terms(bv_ctx* c, const bv_theta* theta, int32_t prec, d
     if (out_logdet) *out_logdet = -2.0 * c->h_out[0] - q - (double)c->n_tot * 1.8378770664093454835606594728112;
     return st;
 }
+
+extern "C" int bv_last_error_block(bv_ctx* c, int64_t* block) {
+    if (!c || !block) return BV_EINVAL;
+    *block = (c->h_fail && *c->h_fail != ~0ull) ? (int64_t)*c->h_fail : -1;
+    return BV_OK;
+}

@@ -346,7 +346,20 @@ bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double*
 extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
                       uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
                       int32_t* n_evals) {
-    if (!c || !theta0 || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
+    if (!c || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
+    bv_theta warm;
+    if (!theta0) {
+        // learned warm start from the geometric centre of the box (the smoothness and the
+        // range ratios are taken from it; the network sets sigma^2, the range and tau^2)
+        if (!c->have_mlp) return BV_ESTATE;
+        bv_theta mid = *lo;
+        mid.sigma2 = sqrt(lo->sigma2 * hi->sigma2);
+        for (int j = 0; j < 3; ++j) mid.range[j] = sqrt(lo->range[j] * hi->range[j]);
+        mid.nugget = sqrt(lo->nugget * hi->nugget);
+        mid.nu = sqrt(lo->nu * hi->nu);
+        BV_TRY(bv_warmstart_predict(c, &mid, &warm));
+        theta0 = &warm;
+    }
     if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
     if (!c->have_nn) return BV_ESTATE;
     if ((free_mask & ~15u) != 0 || free_mask == 0) return BV_EINVAL;

@@ -179,7 +179,11 @@ def test_not_positive_definite_status(bv):
         ctx.set_blocks(bp, pi)
         ctx.select_neighbors(10)
         ll, per, st = ctx.loglik(_gtheta(bv, 1.0, 0.1, 1.5, 0.0), per_block=True, allow_notpd=True)
+        first_bad = ctx.last_error_block()
+        ctx.loglik(_gtheta(bv, 1.0, 0.1, 1.5, 1e-3))     # a nugget restores positive definiteness
+        cleared = ctx.last_error_block()
     assert st == bv.BV_ENOTPD and ll == -np.inf and per[0] == -np.inf
+    assert first_bad == 0 and cleared == -1
 
 
 def test_multi_dataset_batched(bv):

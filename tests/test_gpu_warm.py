@@ -106,3 +106,24 @@ def test_warm_start_cuts_loglik_calls(bv):
         assert abs(ll_w - ll_c) <= 1e-6 * abs(ll_c), (ll_w, ll_c)
         calls.append((ne_c, ne_w))
     assert sum(w for _, w in calls) < sum(c for c, _ in calls), calls
+
+
+def test_mle_without_a_start_uses_the_warm_start(bv):
+    wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained warm-start weights committed")
+    n = 8000
+    locs = synth.locs_uniform(n, 2, 950)
+    with bv.Context() as ctx:
+        ctx.set_data(locs)
+        ctx.build_blocks(n // 10, seed=950)
+        ctx.select_neighbors(60)
+        ctx.simulate(bv.theta(1.3, 0.08, 1.5, 5e-3), synth.normal(950, 20, n))
+        lo, hi = bv.theta(0.01, 0.001, 1.5, 1e-6), bv.theta(100.0, 3.0, 1.5, 10.0)
+        with pytest.raises(bv.BVError):
+            ctx.mle(None, lo, hi)                       # no weights loaded yet
+        ctx.warmstart_load(wpath)
+        th_w, ll_w, _ = ctx.mle(None, lo, hi, ftol_rel=1e-12, xtol=1e-6)
+        th_c, ll_c, _ = ctx.mle(bv.theta(1.0, 0.1, 1.5, 1e-2), lo, hi, ftol_rel=1e-12, xtol=1e-6)
+    assert abs(ll_w - ll_c) <= 1e-8 * abs(ll_c)
+    assert th_w.nu == 1.5
