@@ -212,6 +212,11 @@ int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
 int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
                     double* d_out_loglik);
 
+/* Blocks of the last mixed-precision evaluation whose FP32 factorisation broke down (a
+ * non-positive pivot) and that were recomputed in FP64 within the same evaluation; only
+ * a block that also fails in FP64 makes ell -inf. */
+int bv_mixed_fallbacks(bv_ctx* ctx, int64_t* count);
+
 /* First failing block (not positive definite) of the last synchronous evaluation, or -1. */
 int bv_last_error_block(bv_ctx* ctx, int64_t* block);
 

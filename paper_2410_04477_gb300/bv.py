@@ -89,6 +89,7 @@ _SIGS = {
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
     "bv_last_error_block": (_int, [_vp, _P(_i64)]),
+    "bv_mixed_fallbacks": (_int, [_vp, _P(_i64)]),
     "bv_loglik_noalloc": (_int, [_P(bv_theta), _vp, _vp, _i64, _i32, _i64, _vp, _vp, _vp, _vp,
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
@@ -418,6 +419,12 @@ class Context:
         _check(_lib.bv_kl_divergence(self.h, ctypes.byref(th), precision, ctypes.byref(k), ctypes.byref(a),
                                      ctypes.byref(b)), "bv_kl_divergence")
         return k.value, a.value, b.value
+
+    def mixed_fallbacks(self):
+        """Blocks recomputed in FP64 in the last mixed-precision evaluation."""
+        b = ctypes.c_int64(0)
+        _check(_lib.bv_mixed_fallbacks(self.h, ctypes.byref(b)), "bv_mixed_fallbacks")
+        return b.value
 
     def last_error_block(self):
         """First failing block of the last synchronous evaluation, or -1."""

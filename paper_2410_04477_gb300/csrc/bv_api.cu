@@ -79,6 +79,9 @@ static void free_blocks(bv_ctx* c) {
     dfree(c->d_ell_blk);
     dfree(c->d_u_blk);
     dfree(c->d_red_part);
+    dfree(c->d_fb);
+    dfree(c->d_fb_ws);
+    c->fb_slots = 0;
     c->h_bptr.clear();
     c->h_pidx.clear();
     c->h_bds.clear();
@@ -135,6 +138,8 @@ extern "C" int bv_create(bv_ctx** out, int device, void* stream) {
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_fail, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_fail, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_fb, sizeof(int));
+    if (e == cudaSuccess) *c->h_fb = 0;
     if (e != cudaSuccess) {
         bv_record_cuda_error(e, "bv_create", __FILE__, __LINE__);
         bv_destroy(c);
@@ -156,6 +161,7 @@ extern "C" void bv_destroy(bv_ctx* c) {
     for (auto s : c->side) cudaStreamDestroy(s);
     for (auto e : c->side_ev) cudaEventDestroy(e);
     if (c->h_fail) cudaFreeHost(c->h_fail);
+    if (c->h_fb) cudaFreeHost(c->h_fb);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -652,6 +658,8 @@ static LLArgs make_args(bv_ctx* c) {
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
     a.gen = c->cur_gen ? 1 : 0;
+    a.fb = nullptr;
+    a.dyn = 0;
     a.gtab = c->d_gtab;
     bv_exp_consts(&a.ex);
     return a;
@@ -709,6 +717,22 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
             c->ws_stride = stride;
             c->ws_slots = slots;
         }
+    }
+    // mixed precision: FP64 fallback list and workspace slots sized for the largest block
+    if (prec == BV_MIXED) {
+        int64_t maxN = 1;
+        for (int v : Nof) maxN = std::max<int64_t>(maxN, v);
+        const int64_t R = maxN + 1;
+        const int64_t stride = (R * (R + 1)) / 2 + 2 * R + 3 * maxN + 8;
+        int slots = (int)std::min<int64_t>(c->nblk, (int64_t)c->num_sms);
+        while (slots > 1 && (double)slots * stride * 8.0 > 2e9) --slots;
+        dfree(c->d_fb_ws);
+        dfree(c->d_fb);
+        BV_CUDA(cudaMalloc(&c->d_fb_ws, sizeof(double) * stride * slots));
+        BV_CUDA(cudaMalloc(&c->d_fb, sizeof(int) * (c->nblk + 1)));
+        BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));
+        c->fb_stride = stride;
+        c->fb_slots = slots;
     }
     for (size_t b = 0; b < lists.size(); ++b) {
         auto& L = lists[b];
@@ -838,14 +862,23 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
     }
     BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
     if (c->cur_gen) BV_CUDA(bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream));
+    const bool fallback = prec == BV_MIXED && c->d_fb;
+    if (fallback) BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));
     BV_CUDA(cudaEventRecord(c->side_ev[0], c->stream));
-    const LLArgs a = make_args(c);
+    LLArgs a = make_args(c);
+    if (fallback) a.fb = c->d_fb;
     for (size_t i = 0; i < nb; ++i) {
         BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
         BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
         BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
     }
     for (size_t i = 0; i < nb; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
+    if (fallback) {
+        LLArgs fa = a;
+        fa.ws = c->d_fb_ws;
+        fa.ws_stride = c->fb_stride;
+        BV_CUDA(bv_launch_fallback(fa, c->fb_slots, c->stream));
+    }
     BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->red_chunks, c->d_red_part,
                              c->d_out, c->d_quad, c->stream));
     return BV_OK;
@@ -905,6 +938,7 @@ static int finish_sync(bv_ctx* c, double* out, int nout) {
     BV_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
     BV_CUDA(cudaMemcpyAsync(c->h_quad, c->d_quad, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
     BV_CUDA(cudaMemcpyAsync(c->h_fail, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    if (c->d_fb) BV_CUDA(cudaMemcpyAsync(c->h_fb, c->d_fb, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BV_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < nout; ++k) out[k] = c->h_out[k];
     return *c->h_fail != ~0ull ? BV_ENOTPD : BV_OK;
@@ -980,5 +1014,11 @@ extern "C" int bv_loglik_terms(bv_ctx* c, const bv_theta* theta, int32_t prec, d
 extern "C" int bv_last_error_block(bv_ctx* c, int64_t* block) {
     if (!c || !block) return BV_EINVAL;
     *block = (c->h_fail && *c->h_fail != ~0ull) ? (int64_t)*c->h_fail : -1;
+    return BV_OK;
+}
+
+extern "C" int bv_mixed_fallbacks(bv_ctx* c, int64_t* count) {
+    if (!c || !count) return BV_EINVAL;
+    *count = c->h_fb ? *c->h_fb : 0;
     return BV_OK;
 }

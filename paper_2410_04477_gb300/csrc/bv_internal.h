@@ -81,6 +81,8 @@ struct LLArgs {
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
     int gen;                 // host side: launch the general-smoothness instantiation
+    int* fb;                 // mixed precision: [0] count, [1..] blocks to redo in FP64 (or null)
+    int dyn;                 // global-memory kernel: take the work list and count from fb
     const double* gtab;      // per dataset: general-nu Matern table (GTAB_SIZE doubles)
     double* ell_blk;         // per-block conditional log-likelihood (output)
     double* u_blk;           // per-block quadratic form u_i = v_i^T v_i (output)
@@ -118,6 +120,8 @@ cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const i
                              int32_t ndata, int32_t maxchunks, void* part, double* out, double* out_quad,
                              cudaStream_t s);
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
+// FP64 recomputation (global-memory kernel) of the blocks listed in a.fb.
+cudaError_t bv_launch_fallback(const LLArgs& a, int grid, cudaStream_t s);
 // Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
 cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s);
 #define BV_GTAB_DOUBLES 931  // GTAB_NOCT * GTAB_DEG
@@ -196,6 +200,11 @@ struct bv_ctx {
     double* d_ell_blk = nullptr;
     double* d_u_blk = nullptr;        // per-block quadratic forms
     double* d_red_part = nullptr;     // reduction partials (ndata x red_chunks x 4)
+    int* d_fb = nullptr;              // mixed-precision FP64 fallback list: [0] count, [1..] blocks
+    int* h_fb = nullptr;              // pinned copy of the count
+    double* d_fb_ws = nullptr;        // FP64 workspace slots for the fallback pass
+    int64_t fb_stride = 0;
+    int fb_slots = 0;
     int32_t red_chunks = 1;
     double* d_quad = nullptr;         // ndata: sum of the quadratic forms
     double* h_quad = nullptr;         // pinned, ndata

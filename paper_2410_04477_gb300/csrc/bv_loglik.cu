@@ -440,11 +440,14 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
     return make_double2(part, partu);
 }
 
+// A block whose FP32 factorisation breaks down (non-positive pivot) is queued for the FP64
+// fallback pass instead of failing the evaluation.
 __device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, double su, int failed) {
     double ell = -0.5 * (s + (double)b * kLog2Pi);
     if (failed || !(ell == ell)) {
         ell = -INFINITY;
-        record_fail(a.fail, blk);
+        if (a.fb) a.fb[1 + atomicAdd(a.fb, 1)] = blk;
+        else record_fail(a.fail, blk);
     }
     a.ell_blk[blk] = ell;
     a.u_blk[blk] = su;
@@ -508,9 +511,11 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
     double* slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
     if (tid < 32) etab[tid] = a.ex.tab[tid];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
+    const int nwork = a.dyn ? *a.fb : a.nwork;
+    const int* work = a.dyn ? a.fb + 1 : a.work;
 
-    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
-        const int blk = a.work[w];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int blk = work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
         const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
         const int N = m + b, R = N + 1;
@@ -818,6 +823,13 @@ cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const i
 cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s) {
     k_gtab_build<<<ndata, 1024, 0, s>>>(theta, gtab);
     return cudaGetLastError();
+}
+
+cudaError_t bv_launch_fallback(const LLArgs& a0, int grid, cudaStream_t s) {
+    LLArgs a = a0;
+    a.dyn = 1;
+    a.fb = a0.fb;
+    return a.gen ? launch_kind_g<256, true>(2, grid, 0, a, s) : launch_kind_g<256, false>(2, grid, 0, a, s);
 }
 
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {

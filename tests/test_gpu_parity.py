@@ -332,3 +332,27 @@ def test_maxmin_on_many_blocks(bv):
     obp, opi, _ = oracle.apply_block_order(obp, opi, oce, oracle.order_blocks(oce, "maxmin"))
     np.testing.assert_array_equal(bp, obp)
     np.testing.assert_array_equal(pi, opi)
+
+
+def test_mixed_precision_fp64_fallback(bv):
+    # a smooth, long-range field with a tiny nugget: FP32 factorisations of many blocks
+    # break down, the FP64 pass recomputes exactly those blocks, and the mixed result
+    # stays next to the FP64 one (the oracle's)
+    n = 2000
+    locs = synth.locs_uniform(n, 2, 110)
+    th = _otheta(1.0, 0.3, 2.5, 1e-7)
+    y = synth.normal(110, 20, n)
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        bp, pi = ctx.build_blocks(200, seed=3)
+        nnp, nni = ctx.select_neighbors(40)
+        l64 = ctx.loglik(_gtheta(bv, 1.0, 0.3, 2.5, 1e-7))
+        lmx, per_mx, st = ctx.loglik(_gtheta(bv, 1.0, 0.3, 2.5, 1e-7), bv.BV_MIXED, per_block=True)
+        nfb = ctx.mixed_fallbacks()
+        ctx.loglik(_gtheta(bv, 1.0, 0.1, 0.5, 1e-2), bv.BV_MIXED)
+        nfb_easy = ctx.mixed_fallbacks()
+    lo, _, _ = oracle.loglik(th, locs, y, bp, pi, nnp, nni)
+    assert abs(l64 - lo) <= 1e-7 * abs(lo)
+    assert nfb > 0 and nfb_easy == 0
+    assert np.all(np.isfinite(per_mx)) and st == 0
+    assert abs(lmx - l64) <= 1e-2 * abs(l64), (lmx, l64, nfb)
