@@ -36,6 +36,11 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor), used as the A
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5 at max clock
 
+# DRAM bytes (read + write) of one evaluation's likelihood-kernel launches, summed over
+# the size bins, from an ncu capture of the same command (profiles/k_ll_fp64_c2_m60.md);
+# reported as roofline.traffic for that workload and precision only.
+NCU_TRAFFIC = {("c2_m60", "fp64"): 18_530_304 + 256}
+
 WORKLOADS = {
     # batched plain FP64: 2e5 uniform points, bc 2e4, m 60 / 120, y from BV at m=400
     "c2_m60": dict(n=200_000, d=2, bc=20_000, m=60, nu=1.5, sigma2=1.0, beta=0.05, nugget=1e-4,
@@ -769,7 +774,8 @@ def main():
     achieved = info["flops"] / (mean_ms / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": "k_ll_fp64 (all size bins) + reduction, one evaluation",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+            "traffic_unit": "bytes per evaluation (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; probe 1.19)",
             "flops_per_eval": info["flops"], "cov_entries_per_eval": info["cov_entries"]}
     if prec == bv.BV_MIXED:
