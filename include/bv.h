@@ -199,6 +199,11 @@ int bv_exact_flops(int64_t n, double* flops);
 int bv_kl_divergence(bv_ctx* ctx, const bv_theta* theta, int32_t precision, double* out_kl,
                      double* out_logdet_exact, double* out_logdet_approx);
 
+/* ell and the quadratic form of every dataset (host arrays of ndatasets; out_quad may be
+ * NULL); as bv_loglik_multi otherwise. */
+int bv_loglik_terms_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision, double* out_loglik,
+                          double* out_quad);
+
 /* All datasets at once: thetas[ndatasets] (host), out_loglik[ndatasets] (host).
  * Synchronous. */
 int bv_loglik_multi(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
@@ -364,6 +369,18 @@ int bv_cond_sim(bv_ctx* ctx, int32_t rounds, uint64_t seed, double z_crit, doubl
  * evaluations. */
 int bv_pred_plan_info(bv_ctx* ctx, double* flops, double* cov_evals);
 
+/* Maximum likelihood for every dataset of a multi-dataset context at once (e.g. the
+ * paper's study of 50 simulated datasets, Sec. 3.2): each dataset runs bv_mle's search;
+ * their log-likelihood evaluations are gathered and issued as batched evaluations of all
+ * datasets (one graph launch per precision requested).  theta0[ndatasets] (or NULL for
+ * the learned warm start of every dataset); lo, hi, free_mask, opts shared.  Outputs
+ * (ndatasets each, any but theta_hat may be NULL): theta_hat, loglik_hat, n_evals, status
+ * (bv_mle's status per dataset); n_batches: batched evaluations issued.  Returns BV_OK
+ * unless a dataset hit an error other than BV_ENOTPD. */
+int bv_mle_multi(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+                 uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
+                 double* loglik_hat, int32_t* n_evals, int32_t* status, int32_t* n_batches);
+
 /* ---- learned warm start --------------------------------------------------------- */
 
 /* The paper suggests warm-starting the estimation from a cheaper fit (Sec. 2.3: estimate
@@ -418,6 +435,8 @@ int bv_mlp_loss_grad(const float* blob, const float* X, const float* T, int64_t 
  * sigma^2, the range (all axes scaled together) and the nugget come from the network. */
 int bv_warmstart_load(bv_ctx* ctx, const char* weights_path);
 int bv_warmstart_predict(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);
+/* The same for every dataset of a multi-dataset context (theta_in/theta_out[ndatasets]). */
+int bv_warmstart_predict_multi(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);
 
 #ifdef __cplusplus
 }

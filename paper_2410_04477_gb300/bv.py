@@ -85,6 +85,10 @@ _SIGS = {
     "bv_exact_loglik": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
     "bv_exact_flops": (_int, [_i64, _P(_d)]),
     "bv_kl_divergence": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d), _P(_d)]),
+    "bv_loglik_terms_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d), _P(_d)]),
+    "bv_mle_multi": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
+                            _P(bv_theta), _P(_d), _P(_i32), _P(_i32), _P(_i32)]),
+    "bv_warmstart_predict_multi": (_int, [_vp, _P(bv_theta), _P(bv_theta)]),
     "bv_loglik_multi": (_int, [_vp, _P(bv_theta), _i32, _P(_d)]),
     "bv_loglik_async": (_int, [_vp, _P(bv_theta), _i32, _vp]),
     "bv_sync": (_int, [_vp, _P(_i64)]),
@@ -484,6 +488,31 @@ class Context:
                            free_mask, ctypes.byref(o), ctypes.byref(out), ctypes.byref(ll),
                            ctypes.byref(ne)), "bv_mle")
         return out, ll.value, ne.value
+
+    def mle_multi(self, th0, lo: bv_theta, hi: bv_theta,
+                  free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
+                  max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0):
+        """Every dataset's MLE with batched evaluations: (thetas, logliks, evals, statuses, batches).
+        th0: a list of starts (one per dataset) or None for the learned warm start."""
+        nd = self.ndata
+        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget)
+        starts = (bv_theta * nd)(*th0) if th0 is not None else None
+        out = (bv_theta * nd)()
+        ll = np.empty(nd)
+        ne = np.empty(nd, np.int32)
+        st = np.empty(nd, np.int32)
+        nb = ctypes.c_int32(0)
+        _check(_lib.bv_mle_multi(self.h, starts, ctypes.byref(lo), ctypes.byref(hi), free_mask, ctypes.byref(o),
+                                 out, _p(ll, _d), _p(ne, _i32), _p(st, _i32), ctypes.byref(nb)), "bv_mle_multi")
+        return list(out), ll, ne, st, nb.value
+
+    def loglik_terms_multi(self, thetas, precision=BV_FP64):
+        """(ell[ndata], quad[ndata])."""
+        arr = (bv_theta * self.ndata)(*thetas)
+        ll = np.empty(self.ndata)
+        q = np.empty(self.ndata)
+        _check(_lib.bv_loglik_terms_multi(self.h, arr, precision, _p(ll, _d), _p(q, _d)), "bv_loglik_terms_multi")
+        return ll, q
 
     def features(self, max_points=10000, seed=0):
         out = np.empty((self.ndata, BV_NFEAT), np.float32)

@@ -951,6 +951,16 @@ extern "C" int bv_loglik_multi(bv_ctx* c, const bv_theta* thetas, int32_t prec, 
     return finish_sync(c, out, c->ndata);
 }
 
+extern "C" int bv_loglik_terms_multi(bv_ctx* c, const bv_theta* thetas, int32_t prec, double* out_loglik,
+                                     double* out_quad) {
+    if (!c || !out_loglik) return BV_EINVAL;
+    BV_TRY(prepare_eval(c, thetas, prec));
+    BV_TRY(bv_enqueue_loglik(c, prec, nullptr, true));
+    const int st = finish_sync(c, out_loglik, c->ndata);
+    if (out_quad) memcpy(out_quad, c->h_quad, sizeof(double) * c->ndata);
+    return st;
+}
+
 extern "C" int bv_loglik(bv_ctx* c, const bv_theta* theta, int32_t prec, double* out, double* per_block) {
     if (!c || !out) return BV_EINVAL;
     if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;

@@ -34,6 +34,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <numeric>
 #include <vector>
 
@@ -132,10 +135,27 @@ void from_theta(const Space& S, const bv_theta& t, double* x) {
     if (S.mask & BV_FREE_NUGGET) x[k++] = log(t.nugget);
 }
 
+// One log-likelihood evaluation for a search: (ell, and with want_q the quadratic form
+// Q) at theta in the given precision; returns a bv_status.
+struct Evaluator {
+    virtual int eval(const bv_theta& t, int prec, bool want_q, double* ll, double* Q) = 0;
+    virtual ~Evaluator() = default;
+};
+
+// A single-dataset context: direct synchronous calls.
+struct DirectEval : Evaluator {
+    bv_ctx* c;
+    explicit DirectEval(bv_ctx* ctx) : c(ctx) {}
+    int eval(const bv_theta& t, int prec, bool want_q, double* ll, double* Q) override {
+        if (want_q) return bv_loglik_terms(c, &t, prec, ll, Q, nullptr);
+        return bv_loglik(c, &t, prec, ll, nullptr);
+    }
+};
+
 // The objective f = -ell at internal coordinates x, one device evaluation per call.
 // Remembers the best full theta it has scored (reset() between precisions).
 struct Objective {
-    bv_ctx* c;
+    Evaluator* ev;
     const Space* S;
     int prec = BV_FP64;
     int evals = 0;
@@ -155,7 +175,7 @@ struct Objective {
             double leta, Q = 0.0;
             if (!to_unit_theta(*S, x.data(), &t, &leta)) return INFINITY;
             ++evals;
-            const int st = bv_loglik_terms(c, &t, prec, &ll, &Q, nullptr);
+            const int st = ev->eval(t, prec, true, &ll, &Q);
             if (st != BV_OK && st != BV_ENOTPD) hard_error = st;
             double s2, lsig;
             if (st != BV_OK || !std::isfinite(ll) || !profile_sigma2(*S, Q, leta, &s2, &lsig)) return INFINITY;
@@ -166,7 +186,8 @@ struct Objective {
         } else {
             if (!to_theta(*S, x.data(), &t)) return INFINITY;
             ++evals;
-            const int st = bv_loglik(c, &t, prec, &ll, nullptr);
+            double Qd = 0.0;
+            const int st = ev->eval(t, prec, false, &ll, &Qd);
             if (st != BV_OK && st != BV_ENOTPD) hard_error = st;
             if (st != BV_OK || !std::isfinite(ll)) return INFINITY;
         }
@@ -343,25 +364,12 @@ bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double*
 
 }  // namespace
 
-extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
-                      uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
-                      int32_t* n_evals) {
-    if (!c || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
-    bv_theta warm;
-    if (!theta0) {
-        // learned warm start from the geometric centre of the box (the smoothness and the
-        // range ratios are taken from it; the network sets sigma^2, the range and tau^2)
-        if (!c->have_mlp) return BV_ESTATE;
-        bv_theta mid = *lo;
-        mid.sigma2 = sqrt(lo->sigma2 * hi->sigma2);
-        for (int j = 0; j < 3; ++j) mid.range[j] = sqrt(lo->range[j] * hi->range[j]);
-        mid.nugget = sqrt(lo->nugget * hi->nugget);
-        mid.nu = sqrt(lo->nu * hi->nu);
-        BV_TRY(bv_warmstart_predict(c, &mid, &warm));
-        theta0 = &warm;
-    }
-    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
-    if (!c->have_nn) return BV_ESTATE;
+// The search of one dataset with n observations: checks, start point, the stages.
+static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* theta0, const bv_theta* lo,
+                      const bv_theta* hi, uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
+                      double* loglik_hat, int32_t* n_evals) {
+    if (!c || !lo || !hi || !opts || !theta_hat || !theta0) return BV_EINVAL;
+
     if ((free_mask & ~15u) != 0 || free_mask == 0) return BV_EINVAL;
     if (opts->max_evals < 1 || opts->init_step <= 0.0) return BV_EINVAL;
     if (opts->precision != BV_FP64 && opts->precision != BV_MIXED) return BV_EINVAL;
@@ -395,12 +403,12 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
     if (free_mask & BV_FREE_NUGGET) t0.nugget = std::min(his[2], std::max(los[2], t0.nugget));
     if (free_mask & BV_FREE_NU) t0.nu = std::min(his[3], std::max(los[3], t0.nu));
     S.base = t0;
-    S.n = (double)c->n_tot;
+    S.n = n_obs;
     S.profile = (free_mask & BV_FREE_SIGMA2) && ((free_mask & BV_FREE_NUGGET) || t0.nugget == 0.0);
     if (S.profile) --S.dim;
     std::vector<double> x(S.dim), xb;
     from_theta(S, t0, x.data());
-    Objective obj{c, &S};
+    Objective obj{ev, &S};
     double fb = INFINITY;
     const int prec = opts->precision;
     if (S.dim == 0) {
@@ -460,4 +468,161 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
     if (loglik_hat) *loglik_hat = -obj.fbest;
     if (n_evals) *n_evals = obj.evals;
     return BV_OK;
+}
+
+// Geometric centre of the box (the warm start's input when no start is given).
+static bv_theta box_centre(const bv_theta* lo, const bv_theta* hi) {
+    bv_theta mid = *lo;
+    mid.sigma2 = sqrt(lo->sigma2 * hi->sigma2);
+    for (int j = 0; j < 3; ++j) mid.range[j] = sqrt(lo->range[j] * hi->range[j]);
+    mid.nugget = sqrt(lo->nugget * hi->nugget);
+    mid.nu = sqrt(lo->nu * hi->nu);
+    return mid;
+}
+
+extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+                      uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
+                      int32_t* n_evals) {
+    if (!c || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
+    if (c->ndata != 1) return c->ndata == 0 ? BV_ESTATE : BV_EINVAL;
+    if (!c->have_nn) return BV_ESTATE;
+    bv_theta warm;
+    if (!theta0) {
+        // learned warm start from the centre of the box (the smoothness and the range
+        // ratios are taken from it; the network sets sigma^2, the range and tau^2)
+        if (!c->have_mlp) return BV_ESTATE;
+        const bv_theta mid = box_centre(lo, hi);
+        BV_TRY(bv_warmstart_predict(c, &mid, &warm));
+        theta0 = &warm;
+    }
+    DirectEval ev(c);
+    return mle_search(c, &ev, (double)c->n_tot, theta0, lo, hi, free_mask, opts, theta_hat, loglik_hat, n_evals);
+}
+
+// ------------------------------------------------------------------------------------
+// Many datasets at once.  Each dataset's search runs unchanged in its own host thread;
+// its evaluations meet at a barrier, and when every unfinished search is waiting one
+// batched evaluation (one graph launch over all datasets, per precision requested) scores
+// them all.  Datasets without a pending request are evaluated at their last point.
+// ------------------------------------------------------------------------------------
+namespace {
+
+struct Batch {
+    bv_ctx* c;
+    int nd;
+    std::mutex mu;
+    std::condition_variable cv;
+    int active = 0, waiting = 0;
+    uint64_t generation = 0;
+    std::vector<bv_theta> th, last;
+    std::vector<int> prec;
+    std::vector<char> pending;
+    std::vector<double> ll, Q;
+    std::vector<int> st;
+    int batches = 0;
+
+    int request(int ds, const bv_theta& t, int p, double* oll, double* oQ) {
+        std::unique_lock<std::mutex> lk(mu);
+        th[ds] = t;
+        last[ds] = t;
+        prec[ds] = p;
+        pending[ds] = 1;
+        ++waiting;
+        const uint64_t gen = generation;
+        if (waiting == active) run_locked();
+        else cv.wait(lk, [&] { return generation != gen; });
+        *oll = ll[ds];
+        *oQ = Q[ds];
+        return st[ds];
+    }
+    void finish() {
+        std::unique_lock<std::mutex> lk(mu);
+        --active;
+        if (active > 0 && waiting == active) run_locked();
+    }
+    void run_locked() {
+        std::vector<bv_theta> ths(nd);
+        std::vector<double> l(nd), q(nd);
+        for (int p : {(int)BV_FP64, (int)BV_MIXED}) {
+            bool any = false;
+            for (int k = 0; k < nd; ++k) any = any || (pending[k] && prec[k] == p);
+            if (!any) continue;
+            for (int k = 0; k < nd; ++k) ths[k] = (pending[k] && prec[k] == p) ? th[k] : last[k];
+            const int s = bv_loglik_terms_multi(c, ths.data(), p, l.data(), q.data());
+            ++batches;
+            for (int k = 0; k < nd; ++k)
+                if (pending[k] && prec[k] == p) {
+                    ll[k] = l[k];
+                    Q[k] = q[k];
+                    st[k] = (s == BV_OK || s == BV_ENOTPD) ? (std::isfinite(l[k]) ? BV_OK : BV_ENOTPD) : s;
+                }
+        }
+        for (int k = 0; k < nd; ++k) pending[k] = 0;
+        waiting = 0;
+        ++generation;
+        cv.notify_all();
+    }
+};
+
+struct BatchEval : Evaluator {
+    Batch* b;
+    int ds;
+    int eval(const bv_theta& t, int prec, bool, double* ll, double* Q) override {
+        return b->request(ds, t, prec, ll, Q);
+    }
+};
+
+}  // namespace
+
+extern "C" int bv_mle_multi(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+                            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
+                            int32_t* n_evals, int32_t* status, int32_t* n_batches) {
+    if (!c || !lo || !hi || !opts || !theta_hat) return BV_EINVAL;
+    if (c->ndata < 1) return BV_ESTATE;
+    if (!c->have_nn) return BV_ESTATE;
+    const int nd = c->ndata;
+    std::vector<bv_theta> start(nd);
+    if (theta0) {
+        for (int k = 0; k < nd; ++k) start[k] = theta0[k];
+    } else {
+        if (!c->have_mlp) return BV_ESTATE;
+        std::vector<bv_theta> mid(nd, box_centre(lo, hi));
+        BV_TRY(bv_warmstart_predict_multi(c, mid.data(), start.data()));
+    }
+    Batch b;
+    b.c = c;
+    b.nd = nd;
+    b.active = nd;
+    b.th = start;
+    b.last = start;
+    b.prec.assign(nd, BV_FP64);
+    b.pending.assign(nd, 0);
+    b.ll.assign(nd, -INFINITY);
+    b.Q.assign(nd, 0.0);
+    b.st.assign(nd, BV_OK);
+    std::vector<int> res(nd, BV_OK);
+    std::vector<double> llh(nd, -INFINITY);
+    std::vector<int32_t> ne(nd, 0);
+    std::vector<std::thread> pool;
+    pool.reserve(nd);
+    for (int k = 0; k < nd; ++k) {
+        pool.emplace_back([&, k] {
+            BatchEval ev;
+            ev.b = &b;
+            ev.ds = k;
+            const double n_obs = (double)(c->pt_off[k + 1] - c->pt_off[k]);
+            res[k] = mle_search(c, &ev, n_obs, &start[k], lo, hi, free_mask, opts, &theta_hat[k], &llh[k], &ne[k]);
+            b.finish();
+        });
+    }
+    for (auto& t : pool) t.join();
+    int worst = BV_OK;
+    for (int k = 0; k < nd; ++k) {
+        if (loglik_hat) loglik_hat[k] = llh[k];
+        if (n_evals) n_evals[k] = ne[k];
+        if (status) status[k] = res[k];
+        if (res[k] != BV_OK && res[k] != BV_ENOTPD) worst = res[k];
+    }
+    if (n_batches) *n_batches = b.batches;
+    return worst;
 }

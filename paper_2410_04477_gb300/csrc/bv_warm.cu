@@ -650,6 +650,29 @@ extern "C" int bv_warmstart_load(bv_ctx* c, const char* path) {
     return BV_OK;
 }
 
+extern "C" int bv_warmstart_predict_multi(bv_ctx* c, const bv_theta* in, bv_theta* out) {
+    if (!c || !in || !out) return BV_EINVAL;
+    if (!c->have_mlp) return BV_ESTATE;
+    if (c->ndata < 1) return BV_ESTATE;
+    const int nd = c->ndata;
+    std::vector<float> feat((size_t)nd * BV_NFEAT), o((size_t)nd * kOut);
+    BV_TRY(bv_features(c, 10000, 0, feat.data()));
+    BV_TRY(bv_mlp_forward(c->mlp_w.data(), feat.data(), nd, o.data()));
+    const float* ym = c->mlp_w.data() + 2 * BV_NFEAT;
+    const float* ys = ym + 3;
+    for (int k = 0; k < nd; ++k) {
+        double lt[3];
+        for (int j = 0; j < 3; ++j) lt[j] = (double)(o[(size_t)k * kOut + j] * ys[j] + ym[j]);
+        out[k] = in[k];
+        out[k].sigma2 = exp(lt[0]);
+        const double beta = exp(lt[1]);
+        const double f = beta / in[k].range[0];
+        for (int j = 0; j < 3; ++j) out[k].range[j] = in[k].aniso ? in[k].range[j] * f : beta;
+        out[k].nugget = exp(lt[2]);
+    }
+    return BV_OK;
+}
+
 extern "C" int bv_warmstart_predict(bv_ctx* c, const bv_theta* in, bv_theta* out) {
     if (!c || !in || !out) return BV_EINVAL;
     if (!c->have_mlp) return BV_ESTATE;

@@ -167,3 +167,33 @@ def test_mle_with_free_smoothness(bv):
                 v[k] *= np.exp(sgn * 1e-3)
                 assert ctx.loglik(bv.theta(v[0], v[1], v[3], v[2])) < ll
     assert abs(ll - _oracle_ell(th, locs, y, st)) <= 1e-10 * abs(ll)
+
+
+def test_batched_mle_over_datasets(bv):
+    # several datasets, one context: every dataset's search issues its evaluations into
+    # shared batched launches; each result matches the same dataset fitted alone
+    sizes = [1500, 2200, 1800, 2600, 1200, 2000]
+    truths = [(1.2, 0.05, 1e-3), (0.8, 0.08, 5e-3), (1.5, 0.04, 2e-3), (1.0, 0.06, 1e-2), (0.6, 0.1, 3e-3),
+              (1.3, 0.07, 4e-3)]
+    nu = 1.5
+    locs, ys = [], []
+    for k, (n, (s2, beta, tau2)) in enumerate(zip(sizes, truths)):
+        l = synth.locs_uniform(n, 2, 400 + k)
+        locs.append(l)
+        ys.append(oracle.exact_draw(oracle.theta(s2, beta, nu, tau2), l, synth.normal(400 + k, 20, n)))
+    lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
+    starts = [bv.theta(1.0, 0.1, nu, 1e-2)] * len(sizes)
+    with bv.Context() as ctx:
+        ctx.set_datasets(locs, ys)
+        ctx.build_blocks_multi([n // 10 for n in sizes], seed=500)
+        ctx.select_neighbors(30)
+        ths, lls, nes, sts, nb = ctx.mle_multi(starts, lo, hi, ftol_rel=1e-13, xtol=1e-7)
+    assert np.all(sts == 0) and nb < nes.sum()
+    for k, n in enumerate(sizes):
+        with bv.Context() as ctx:
+            ctx.set_data(locs[k], ys[k])
+            ctx.build_blocks(n // 10, seed=500 + k)
+            ctx.select_neighbors(30)
+            th, ll, _ = ctx.mle(starts[k], lo, hi, ftol_rel=1e-13, xtol=1e-7)
+            assert ctx.loglik(ths[k]) == pytest.approx(lls[k], rel=1e-11)
+        assert abs(lls[k] - ll) <= 1e-9 * abs(ll), (k, lls[k], ll)
