@@ -76,6 +76,11 @@ WORKLOADS = {
     # the paper's small-scale KL case (n = 8,000, its supplementary study), bc = 650
     "kl_8k": dict(kind="kl", n=8_000, d=2, nu=1.5, sigma2=1.0, beta=0.052537, nugget=0.0, seed=9,
                   bc=650, bv_m=[30, 120], cv_m=[30, 60], orders=["random", "maxmin"]),
+    # the paper's estimation study (Sec. 3.2): 50 datasets of n = 20,000 in the unit square,
+    # nu = 1.5, beta = 0.052537, sigma^2 = 1; block Vecchia bc = 1,500, m = 30; sigma^2,
+    # beta, tau^2 estimated for every dataset, batched vs one dataset after another
+    "mle50": dict(kind="mle_batch", ndata=50, n=20_000, d=2, nu=1.5, sigma2=1.0, beta=0.052537, nugget=1e-3,
+                  bc=1500, m=30, gen_bc=2000, gen_m=100, seed=11),
     # prediction (Algorithm 2) + 1,000-round univariate conditional simulation and PICP:
     # the paper's shape (n = 20,000 in the unit square, 10% held out, 200 prediction
     # blocks) and a 10x larger one with the same 1:10 block-to-location ratio
@@ -700,6 +705,99 @@ def kl_config(w, args):
             "orders": w["orders"], "l2": "inputs (3.2 GB factor) larger than L2"}
 
 
+def run_mle_batch(args, w, log):
+    ws, rank, local = _dist()
+    nd, n = w["ndata"], w["n"]
+    metric = (f"block-Vecchia MLE datasets/sec ({nd} datasets x n={n}, bc={w['bc']}, m={w['m']}, nu={w['nu']} "
+              f"fixed; sigma^2, beta, tau^2 free; FP64)")
+    cfg = {"workload": args.workload, "ndata": nd, "n": n, "bc": w["bc"], "m": w["m"], "nu": w["nu"],
+           "theta_true": [w["sigma2"], w["beta"], w["nugget"]], "y": f"block-Vecchia draws at m={w['gen_m']}",
+           "start": "cold (1, 0.1, 1e-2)", "l2": "inputs larger than L2 over a step",
+           "parallelism": "replicas" if ws > 1 else "single"}
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps({"impl": "reference", "unavailable": "an oracle MLE of 50 datasets of n=20,000 takes "
+                          "hours on the host; the oracle is timed per evaluation in the ours line's cpu_baseline"}),
+              flush=True)
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2410_04477_gb300 import bv
+    th_true = bv.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+    locs_l, y_l = [], []
+    t0 = time.perf_counter()
+    with bv.Context(local) as gen:
+        for k in range(nd):
+            locs = synth.locs_uniform(n, 2, w["seed"] * 1000 + k)
+            gen.set_data(locs)
+            gen.build_blocks(w["gen_bc"], seed=w["seed"] * 1000 + k)
+            gen.select_neighbors(w["gen_m"])
+            y_l.append(gen.simulate(th_true, synth.normal(w["seed"] * 1000 + k, 20, n)))
+            locs_l.append(locs)
+    log(f"setup: {nd} draws {time.perf_counter() - t0:.1f}s")
+    lo, hi = bv.theta(0.01, 0.001, w["nu"], 1e-6), bv.theta(100.0, 3.0, w["nu"], 10.0)
+    start = bv.theta(1.0, 0.1, w["nu"], 1e-2)
+    opts = dict(ftol_rel=1e-10, xtol=1e-5)
+    ctx = bv.Context(local)
+    ctx.set_datasets(locs_l, y_l)
+    ctx.build_blocks_multi([w["bc"]] * nd, seed=w["seed"])
+    ctx.select_neighbors(w["m"])
+    ctx.loglik_multi([start] * nd)                 # plan, tune and capture outside the timed region
+    clk = Clocks(local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ths, lls, nes, sts, nb = ctx.mle_multi([start] * nd, lo, hi, **opts)
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t0
+    clocks = clk.stop()
+    launches = int(ctx.plan_info(bv.BV_FP64)["launches_per_eval"]) * nb
+    ctx.close()
+    # the same fits one dataset after another, each in its own context
+    seq_s, seq_ll = 0.0, []
+    for k in range(nd):
+        with bv.Context(local) as one:
+            one.set_data(locs_l[k], y_l[k])
+            one.build_blocks(w["bc"], seed=w["seed"] + k)
+            one.select_neighbors(w["m"])
+            one.loglik(start)
+            t0 = time.perf_counter()
+            _, ll1, _ = one.mle(start, lo, hi, **opts)
+            seq_s += time.perf_counter() - t0
+            seq_ll.append(ll1)
+    rel = float(np.max(np.abs(np.array(seq_ll) - lls) / np.abs(lls)))
+    est = np.array([[t.sigma2, t.range[0], t.nugget] for t in ths])
+    value = ws * nd / max_over_ranks(batched_s)
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        import oracle
+        bp, pi, ce = oracle.build_blocks(locs_l[0], w["bc"], seed=w["seed"])
+        nnp, nni = oracle.select_neighbors(locs_l[0], bp, pi, ce, w["m"])
+        oth = oracle.theta(w["sigma2"], w["beta"], w["nu"], w["nugget"])
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0 and reps < 50:
+            oracle.loglik(oth, locs_l[0], y_l[0], bp, pi, nnp, nni)
+            reps += 1
+        per = (time.perf_counter() - t0) / reps
+        cpu = {"value": 1.0 / (per * float(np.mean(nes))), "unit": "datasets/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{reps} oracle evaluations of dataset 0, times the mean number of "
+               f"evaluations per fit ({float(np.mean(nes)):.0f})"}
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": "datasets/s", "n_gpus": ws, "steps": 1, "warmup": 1,
+                "ms_per_step": batched_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": cfg,
+                "roofline": None, "cpu_baseline": cpu,
+                "e2e": {"value": value, "unit": "datasets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "clocks": clocks, "gpu_launches": launches,
+                "extras": {"batched_s": batched_s, "sequential_s": seq_s, "speedup": seq_s / batched_s,
+                           "batches": nb, "evals_mean": float(np.mean(nes)), "evals_max": int(np.max(nes)),
+                           "max_rel_diff_loglik_vs_sequential": rel,
+                           "estimates_mean": est.mean(axis=0).tolist(), "estimates_sd": est.std(axis=0).tolist()}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -714,6 +812,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     w = dict(WORKLOADS[args.workload])
+    if w.get("kind") == "mle_batch":
+        log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
+        return run_mle_batch(args, w, log)
     if w.get("kind") == "kl":
         log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
         return run_kl(args, w, log)
