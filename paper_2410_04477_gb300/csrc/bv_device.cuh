@@ -24,10 +24,11 @@ __device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
 }
 
 // e^{-x} for x >= 0 by Tang's table-driven method (see ExpConsts): reduction to
-// |r| <= ln2/64, e^r - 1 by its Taylor polynomial through r^6 (truncation < 4e-18), one
-// table multiply and an exponent-field scaling.  11 FP64 operations.  Results below
-// e^{-700} are flushed to zero (a covariance entry that small is irrelevant next to the
-// diagonal).  Accuracy: within 2 ulp of e^{-x} (checked against libm in the tests).
+// |r| <= ln2/512, e^r - 1 by its Taylor polynomial through r^4 (truncation below 4e-17
+// relative), one table multiply and an exponent-field scaling.  9 FP64 operations.
+// Results below e^{-700} are flushed to zero (a covariance entry that small is irrelevant
+// next to the diagonal).  Accuracy: within 2 ulp of e^{-x} (checked against libm in the
+// tests).
 __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ tab, double K, double L1,
                                           double L2) {
     const double shift = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
@@ -36,14 +37,12 @@ __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ t
     const double nd = s - shift;               // round(-x K), exact
     double r = fma(nd, -L1, -x);
     r = fma(nd, -L2, r);
-    double q = fma(1.0 / 720.0, r, 1.0 / 120.0);
-    q = fma(q, r, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
+    double q = fma(1.0 / 24.0, r, 1.0 / 6.0);
     q = fma(q, r, 0.5);
     const double p = fma(q * r, r, r);         // e^r - 1
-    const double t = tab[n & 31];
-    const double v = fma(t, p, t);             // 2^{j/32} e^r in [0.98, 2)
-    const int hi = __double2hiint(v) + ((n >> 5) << 20);
+    const double t = tab[n & (BV_EXP_TAB - 1)];
+    const double v = fma(t, p, t);             // 2^{j/256} e^r in [0.99, 2)
+    const int hi = __double2hiint(v) + ((n >> 8) << 20);
     const double res = __hiloint2double(hi, __double2loint(v));
     return x > 700.0 ? 0.0 : res;
 }

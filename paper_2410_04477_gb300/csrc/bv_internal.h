@@ -54,12 +54,14 @@ struct DevTheta {
 
 // Constants of the table-driven FP64 exponential (Tang, "Table-driven implementation of
 // the exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-// e^{-x} = 2^{n/32} e^{r},  n = round(-x 32/ln2),  r = -x - n (L1 + L2),  L1 + L2 = ln2/32,
-// 2^{n/32} = 2^{floor(n/32)} tab[n mod 32].  Filled on the host in long double.
+// e^{-x} = 2^{n/256} e^{r},  n = round(-x 256/ln2),  r = -x - n (L1 + L2),
+// L1 + L2 = ln2/256, 2^{n/256} = 2^{floor(n/256)} tab[n mod 256].  Filled on the host in
+// long double.
+#define BV_EXP_TAB 256
 struct ExpConsts {
-    double tab[32];   // 2^{j/32}, j = 0..31
-    double k;         // 32 / ln 2
-    double l1, l2;    // ln2/32 split: l1 has its low 21 bits zero so n*l1 is exact
+    double tab[BV_EXP_TAB];   // 2^{j/256}, j = 0..255
+    double k;                 // 256 / ln 2
+    double l1, l2;            // ln2/256 split: l1 has its low 21 bits zero so n*l1 is exact
 };
 void bv_exp_consts(ExpConsts* out);
 

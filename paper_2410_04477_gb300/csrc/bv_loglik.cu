@@ -78,10 +78,10 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double* sm = reinterpret_cast<double*>(smraw);
     __shared__ double2 red2[NT / 32];
-    __shared__ double etab[32];
+    __shared__ double etab[BV_EXP_TAB];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    for (int i = tid; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
 
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         // gather: conditioning points first, then the block (Algorithm 1 order)
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * th.inv_range[k];
             A[pk(N, t)] = a.y[g];
         }
         if (tid == 0) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             tri_rc(f, r, c);
             double acc = 0.0;
             for (int k = 0; k < d; ++k) {
-                const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                const double t = px[k * N + r] - px[k * N + c];
                 acc = fma(t, t, acc);
             }
             // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
@@ -505,11 +505,11 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
 template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
     __shared__ double2 red2[NT / 32];
-    __shared__ double etab[32];
+    __shared__ double etab[BV_EXP_TAB];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
-    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    for (int i = tid; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
     const int nwork = a.dyn ? *a.fb : a.nwork;
     const int* work = a.dyn ? a.fb + 1 : a.work;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
 
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * th.inv_range[k];
             A[pk(N, t)] = a.y[g];
         }
         if (tid == 0) {
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
             for (int c = lane; c <= r; c += 32) {
                 double acc = 0.0;
                 for (int k = 0; k < d; ++k) {
-                    const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                    const double t = px[k * N + r] - px[k * N + c];
                     acc = fma(t, t, acc);
                 }
                 double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
@@ -725,7 +725,7 @@ __global__ void k_matern_check(const double* x, double* out, int64_t n, const De
 // same instantiation with its own footprint, so the per-function maximum is set once to
 // this cap and never lowered (a launch captured in a graph with a larger footprint must
 // stay valid when a smaller bin is launched later).
-constexpr int kSmemCap = 227 * 1024 - 2048;
+constexpr int kSmemCap = 227 * 1024 - 3072;
 
 template <int NT, bool GEN>
 cudaError_t set_smem_cap_g() {
@@ -863,8 +863,8 @@ int bv_occupancy(int kind, int threads, size_t smem) {
 
 void bv_exp_consts(ExpConsts* o) {
     const long double ln2 = 0.693147180559945309417232121458176568L;
-    for (int j = 0; j < 32; ++j) o->tab[j] = (double)exp2l((long double)j / 32.0L);
-    const long double L = ln2 / 32.0L;
+    for (int j = 0; j < BV_EXP_TAB; ++j) o->tab[j] = (double)exp2l((long double)j / (long double)BV_EXP_TAB);
+    const long double L = ln2 / (long double)BV_EXP_TAB;
     double l1 = (double)L;
     unsigned long long bits;
     memcpy(&bits, &l1, sizeof(bits));
@@ -872,7 +872,7 @@ void bv_exp_consts(ExpConsts* o) {
     memcpy(&l1, &bits, sizeof(bits));
     o->l1 = l1;
     o->l2 = (double)(L - (long double)l1);
-    o->k = (double)(32.0L / ln2);
+    o->k = (double)((long double)BV_EXP_TAB / ln2);
 }
 
 // Diagnostic: the library's FP64 exp(-x) on the device for host inputs x[n].

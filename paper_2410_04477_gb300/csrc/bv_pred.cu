@@ -65,7 +65,7 @@ struct PredState {
 namespace {
 
 constexpr int kPredNT = 256;
-constexpr size_t kPredSmemCap = 227 * 1024 - 1024;
+constexpr size_t kPredSmemCap = 227 * 1024 - 3072;
 
 template <class T>
 void dfree(T*& p) {
@@ -135,10 +135,10 @@ __host__ __device__ inline int64_t pred_doubles(int64_t N) { return (N + 1) * (N
 __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
     constexpr int NT = kPredNT, NU = NT - 32;
     extern __shared__ __align__(16) double sm[];
-    __shared__ double etab[32];
+    __shared__ double etab[BV_EXP_TAB];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 32) etab[tid] = a.ex.tab[tid];
+    for (int i = tid; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
     const DevTheta th = a.th;
     const int d = a.d;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
             const bool obs = t < m;
             const int64_t g = obs ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
             for (int k = 0; k < d; ++k)
-                px[k * N + t] = obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g];
+                px[k * N + t] = (obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g]) * th.inv_range[k];
             A[pk(N, t)] = obs ? a.y[g] : 0.0;  // data row: [y_NN, 0]
         }
         if (tid == 0) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
             tri_rc(f, r, c);
             double acc = 0.0;
             for (int k = 0; k < d; ++k) {
-                const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                const double t = px[k * N + r] - px[k * N + c];
                 acc = fma(t, t, acc);
             }
             const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
