@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5 a
 # DRAM bytes (read + write) of one evaluation's likelihood-kernel launches, summed over
 # the size bins, from an ncu capture of the same command (profiles/k_ll_fp64_c2_m60.md);
 # reported as roofline.traffic for that workload and precision only.
-NCU_TRAFFIC = {("c2_m60", "fp64"): 18_501_632 + 256}
+NCU_TRAFFIC = {("c2_m60", "fp64"): 18_500_864 + 256}
 
 WORKLOADS = {
     # batched plain FP64: 2e5 uniform points, bc 2e4, m 60 / 120, y from BV at m=400
