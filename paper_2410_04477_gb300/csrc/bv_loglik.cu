@@ -429,13 +429,15 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
         gsync<WARP>();
     }
 
-    // quadratic form and log-determinant terms of the block columns, in FP64
+    // quadratic form and log-determinant terms of the block columns, accumulated in FP64
+    // (the logarithm of an FP32 pivot is taken in FP32: its 1-ulp error is far below the
+    // pivot's own FP32 rounding)
     double part = 0.0, partu = 0.0;
     for (int k = m + tid; k < N; k += NG) {
         const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
                                               : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
         partu += z * z;
-        part += z * z + log((double)piv[k]);
+        part += z * z + (double)logf(piv[k]);
     }
     return make_double2(part, partu);
 }
