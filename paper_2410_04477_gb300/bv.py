@@ -3,6 +3,24 @@
 Every computation runs in the CUDA library ``_build/libbv.so``; there is no CPU fallback.
 Importing this module raises if the library has not been built, and every call raises
 ``BVError`` on a non-OK status.  ``Context`` wraps one ``bv_ctx``.
+
+Typical use (locations ``locs`` n x d, observations ``y``)::
+
+    with Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(bc=n // 10, seed=0)          # K-means blocks, random order
+        ctx.select_neighbors(m=60)                    # conditioning sets
+        ell = ctx.loglik(theta(1.0, 0.05, 1.5, 1e-4))             # FP64
+        ell32 = ctx.loglik(theta(1.0, 0.05, 1.5, 1e-4), BV_MIXED)  # mixed precision
+        th, ell_hat, calls = ctx.mle(theta(1.0, 0.1, 1.5, 1e-2),   # start
+                                     theta(0.01, 1e-3, 1.5, 1e-6),  # lower box
+                                     theta(100, 3.0, 1.5, 10.0))    # upper box
+        ctx.set_pred_locations(new_locs)              # prediction (Algorithm 2)
+        ctx.build_pred_blocks(bc=len(new_locs) // 10)
+        ctx.select_pred_neighbors(m=60)
+        mean, var, _ = ctx.predict(th)
+
+Many datasets: ``set_datasets`` + ``build_blocks_multi`` + ``loglik_multi`` / ``mle_multi``.
 """
 from __future__ import annotations
 
