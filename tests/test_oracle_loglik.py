@@ -121,11 +121,13 @@ def test_classic_vecchia_loglik_by_kriging():
     assert ll == pytest.approx(want, rel=1e-11)
 
 
-@pytest.mark.parametrize("d,ranges", [(2, None), (3, [0.1, 0.15, 0.3])])
-def test_dense_implied_precision(d, ranges):
+@pytest.mark.parametrize("d,ranges,nu", [(2, None, 0.5), (3, [0.1, 0.15, 0.3], 0.5), (2, None, 1.2),
+                                         (2, None, 3.7)])
+def test_dense_implied_precision(d, ranges, nu):
     # Eq. 4 defines a joint Gaussian with precision A^T D^{-1} A; its log density at y
-    # equals the sum of the per-block conditionals.
-    locs, th, S, y, (bp, pi, nnp, nni) = _setup(n=320, d=d, bc=40, m=12, seed=5, nu=0.5,
+    # equals the sum of the per-block conditionals (here also at non-half-integer nu,
+    # where both sides need K_nu: the oracle's quadrature, the reference SciPy's kv).
+    locs, th, S, y, (bp, pi, nnp, nni) = _setup(n=320, d=d, bc=40, m=12, seed=5, nu=nu,
                                                ranges=ranges, nugget=1e-3)
     ll, per, _ = oracle.loglik(th, locs, y, bp, pi, nnp, nni)
     P, ldP, _, _ = _ref.bv_dense_precision(S, bp, pi, nnp, nni)
