@@ -375,6 +375,7 @@ def run_mle(bv, ctx, w, log):
         warm0 = ctx.warmstart_predict(cold0)
         res["warm_predict_s"] = time.perf_counter() - t0
         res["warm_start_theta"] = [warm0.sigma2, warm0.range[0], warm0.nugget]
+        res["warm_start_nu_class"] = ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu  # truth: w["nu"]
     # initial simplex scale: 0.5 in log-parameters from the fixed cold start; from the
     # learned warm start its validation RMSE (0.2 for log sigma^2 and log beta, 0.75 for
     # log tau^2, weights/warmstart.json)

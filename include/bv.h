@@ -434,6 +434,8 @@ int bv_mlp_loss_grad(const float* blob, const float* X, const float* T, int64_t 
  * current data's features (max_points 10000, seed 0).  theta_in supplies nu and aniso;
  * sigma^2, the range (all axes scaled together) and the nugget come from the network. */
 int bv_warmstart_load(bv_ctx* ctx, const char* weights_path);
+/* theta_in with nu = 0 asks for the network's smoothness class too (1/2, 3/2 or 5/2,
+ * the arg-max of its three-way head); otherwise nu is kept. */
 int bv_warmstart_predict(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);
 /* The same for every dataset of a multi-dataset context (theta_in/theta_out[ndatasets]). */
 int bv_warmstart_predict_multi(bv_ctx* ctx, const bv_theta* theta_in, bv_theta* theta_out);

@@ -491,8 +491,10 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
         // learned warm start from the centre of the box (the smoothness and the range
         // ratios are taken from it; the network sets sigma^2, the range and tau^2)
         if (!c->have_mlp) return BV_ESTATE;
-        const bv_theta mid = box_centre(lo, hi);
+        bv_theta mid = box_centre(lo, hi);
+        if (free_mask & BV_FREE_NU) mid.nu = 0.0;  // start from the network's smoothness class
         BV_TRY(bv_warmstart_predict(c, &mid, &warm));
+        if (free_mask & BV_FREE_NU) warm.nu = std::min(hi->nu, std::max(lo->nu, warm.nu));
         theta0 = &warm;
     }
     DirectEval ev(c);
@@ -587,7 +589,11 @@ extern "C" int bv_mle_multi(bv_ctx* c, const bv_theta* theta0, const bv_theta* l
     } else {
         if (!c->have_mlp) return BV_ESTATE;
         std::vector<bv_theta> mid(nd, box_centre(lo, hi));
+        if (free_mask & BV_FREE_NU)
+            for (auto& t : mid) t.nu = 0.0;  // start from the network's smoothness class
         BV_TRY(bv_warmstart_predict_multi(c, mid.data(), start.data()));
+        if (free_mask & BV_FREE_NU)
+            for (auto& t : start) t.nu = std::min(hi->nu, std::max(lo->nu, t.nu));
     }
     Batch b;
     b.c = c;

@@ -650,6 +650,14 @@ extern "C" int bv_warmstart_load(bv_ctx* c, const char* path) {
     return BV_OK;
 }
 
+// The smoothness class of the network's three-way head: 1/2, 3/2 or 5/2 (arg-max logit).
+static double nu_of_logits(const float* lg) {
+    int c = 0;
+    for (int j = 1; j < 3; ++j)
+        if (lg[j] > lg[c]) c = j;
+    return 0.5 + (double)c;
+}
+
 extern "C" int bv_warmstart_predict_multi(bv_ctx* c, const bv_theta* in, bv_theta* out) {
     if (!c || !in || !out) return BV_EINVAL;
     if (!c->have_mlp) return BV_ESTATE;
@@ -669,6 +677,7 @@ extern "C" int bv_warmstart_predict_multi(bv_ctx* c, const bv_theta* in, bv_thet
         const double f = beta / in[k].range[0];
         for (int j = 0; j < 3; ++j) out[k].range[j] = in[k].aniso ? in[k].range[j] * f : beta;
         out[k].nugget = exp(lt[2]);
+        if (!(in[k].nu > 0.0)) out[k].nu = nu_of_logits(&o[(size_t)k * kOut + 3]);
     }
     return BV_OK;
 }
@@ -691,5 +700,6 @@ extern "C" int bv_warmstart_predict(bv_ctx* c, const bv_theta* in, bv_theta* out
     const double f = beta / in->range[0];
     for (int k = 0; k < 3; ++k) out->range[k] = in->aniso ? in->range[k] * f : beta;
     out->nugget = exp(lt[2]);
+    if (!(in->nu > 0.0)) out->nu = nu_of_logits(o + 3);
     return BV_OK;
 }

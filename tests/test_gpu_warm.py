@@ -127,3 +127,25 @@ def test_mle_without_a_start_uses_the_warm_start(bv):
         th_c, ll_c, _ = ctx.mle(bv.theta(1.0, 0.1, 1.5, 1e-2), lo, hi, ftol_rel=1e-12, xtol=1e-6)
     assert abs(ll_w - ll_c) <= 1e-8 * abs(ll_c)
     assert th_w.nu == 1.5
+
+
+def test_warm_start_smoothness_head(bv):
+    # theta_in.nu = 0 asks the network for the smoothness class; on fields drawn at
+    # nu = 1/2 and 5/2 (clearly different roughness) it should tell them apart
+    wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained warm-start weights committed")
+    n = 10000
+    got = []
+    for k, nu in enumerate((0.5, 2.5)):
+        locs = synth.locs_uniform(n, 2, 960 + k)
+        with bv.Context() as ctx:
+            ctx.set_data(locs)
+            ctx.build_blocks(n // 10, seed=960 + k)
+            ctx.select_neighbors(100)
+            ctx.simulate(bv.theta(1.0, 0.1, nu, 1e-3), synth.normal(960 + k, 20, n))
+            ctx.warmstart_load(wpath)
+            got.append(ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu)
+            kept = ctx.warmstart_predict(bv.theta(1.0, 0.1, 1.5, 1e-2)).nu
+            assert kept == 1.5
+    assert got == [0.5, 2.5], got
