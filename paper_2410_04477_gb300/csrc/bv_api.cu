@@ -61,8 +61,18 @@ void bv_invalidate_plans(bv_ctx* c) {
     free_plan(c, 1);
 }
 
+static void free_layout(bv_ctx* c) {
+    dfree(c->d_inv);
+    dfree(c->d_locs_int);
+    dfree(c->d_y_int);
+    dfree(c->d_pidx_int);
+    dfree(c->d_nidx_int);
+    c->have_layout = false;
+}
+
 static void free_neighbors(bv_ctx* c) {
     bv_invalidate_plans(c);
+    free_layout(c);
     dfree(c->d_nptr);
     dfree(c->d_nidx);
     c->h_nptr.clear();
@@ -88,6 +98,73 @@ static void free_blocks(bv_ctx* c) {
     c->ds_blk_off.clear();
     c->nblk = 0;
     c->have_blocks = false;
+}
+
+__global__ void k_gather_soa(const double* __restrict__ src, int64_t n, int d, const int32_t* __restrict__ inv,
+                             double* __restrict__ dst) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t g = inv[j];
+    for (int k = 0; k < d; ++k) dst[(int64_t)k * n + j] = src[(int64_t)k * n + g];
+}
+
+__global__ void k_map_index(const int32_t* __restrict__ idx, int64_t cnt, const int32_t* __restrict__ pos,
+                            int32_t* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < cnt) out[i] = pos[idx[i]];
+}
+
+__global__ void k_inverse_perm(const int32_t* __restrict__ inv, int64_t n, int32_t* __restrict__ pos) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) pos[inv[j]] = (int32_t)j;
+}
+
+// The observations in the evaluation layout (after any change of d_y).
+static int refresh_layout_y(bv_ctx* c) {
+    if (!c->have_layout || !c->d_y) return BV_OK;
+    const int64_t n = c->n_tot;
+    k_gather_soa<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->d_y, n, 1, c->d_inv, c->d_y_int);
+    BV_CUDA(cudaGetLastError());
+    return BV_OK;
+}
+
+int bv_refresh_layout_y(bv_ctx* c) { return refresh_layout_y(c); }
+
+// Hilbert order of every dataset's points; internal copies of the locations and y and the
+// block / neighbour lists mapped to internal positions.  Results do not change: every
+// kernel reads the same values, only from other addresses.
+static int build_layout(bv_ctx* c) {
+    if (c->have_layout) return BV_OK;
+    const int64_t n = c->n_tot;
+    const int d = c->d;
+    std::vector<int32_t> inv;
+    inv.reserve(n);
+    for (int ds = 0; ds < c->ndata; ++ds) {
+        std::vector<int32_t> o;
+        bv_hilbert_order(c->h_locs.data(), c->pt_off[ds], c->pt_off[ds + 1] - c->pt_off[ds], d, o);
+        inv.insert(inv.end(), o.begin(), o.end());
+    }
+    int32_t* d_pos = nullptr;
+    BV_CUDA(cudaMalloc(&c->d_inv, sizeof(int32_t) * n));
+    BV_CUDA(cudaMalloc(&d_pos, sizeof(int32_t) * n));
+    BV_CUDA(cudaMalloc(&c->d_locs_int, sizeof(double) * n * d));
+    BV_CUDA(cudaMalloc(&c->d_y_int, sizeof(double) * n));
+    BV_CUDA(cudaMalloc(&c->d_pidx_int, sizeof(int32_t) * n));
+    const int64_t nn = std::max<int64_t>(c->h_nptr.back(), 1);
+    BV_CUDA(cudaMalloc(&c->d_nidx_int, sizeof(int32_t) * nn));
+    BV_CUDA(cudaMemcpyAsync(c->d_inv, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_inverse_perm<<<g, 256, 0, c->stream>>>(c->d_inv, n, d_pos);
+    k_gather_soa<<<g, 256, 0, c->stream>>>(c->d_locs, n, d, c->d_inv, c->d_locs_int);
+    k_map_index<<<g, 256, 0, c->stream>>>(c->d_pidx, n, d_pos, c->d_pidx_int);
+    if (c->h_nptr.back() > 0)
+        k_map_index<<<(unsigned)((c->h_nptr.back() + 255) / 256), 256, 0, c->stream>>>(c->d_nidx, c->h_nptr.back(),
+                                                                                     d_pos, c->d_nidx_int);
+    BV_CUDA(cudaGetLastError());
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    cudaFree(d_pos);
+    c->have_layout = true;
+    return refresh_layout_y(c);
 }
 
 static void free_data(bv_ctx* c) {
@@ -230,7 +307,7 @@ extern "C" int bv_set_observations(bv_ctx* c, const double* y, int32_t on_device
         BV_CUDA(cudaStreamSynchronize(c->stream));
     }
     c->have_y = true;
-    return BV_OK;
+    return refresh_layout_y(c);
 }
 
 // ------------------------------------------------------------------------------------
@@ -639,14 +716,15 @@ static int default_threads(int kind, int nmax) {
 
 static LLArgs make_args(bv_ctx* c) {
     LLArgs a;
-    a.locs = c->d_locs;
+    const bool lay = c->have_layout;
+    a.locs = lay ? c->d_locs_int : c->d_locs;
     a.n_tot = c->n_tot;
     a.d = c->d;
-    a.y = c->d_y;
+    a.y = lay ? c->d_y_int : c->d_y;
     a.bptr = c->d_bptr;
-    a.pidx = c->d_pidx;
+    a.pidx = lay ? c->d_pidx_int : c->d_pidx;
     a.nptr = c->d_nptr;
-    a.nidx = c->d_nidx;
+    a.nidx = lay ? c->d_nidx_int : c->d_nidx;
     a.cent = c->d_cent;
     a.bds = c->d_bds;
     a.theta = c->d_theta;
@@ -680,6 +758,7 @@ static int set_grid(bv_ctx* c, BinPlan& bp) {
 
 int bv_ensure_plan(bv_ctx* c, int prec) {
     if (c->plan_valid[prec]) return BV_OK;
+    BV_TRY(build_layout(c));
     free_plan(c, prec);
     const int smem_kind = prec == BV_MIXED ? 1 : 0;
     const int nsm = bv_smem_max_n(smem_kind, c->d);

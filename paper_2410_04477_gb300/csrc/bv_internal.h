@@ -192,6 +192,16 @@ struct bv_ctx {
     int64_t* d_ds_blk_off = nullptr;
     bool have_blocks = false;
 
+    // evaluation layout: the likelihood kernels read points in Hilbert order (per
+    // dataset) so that a block's neighbours lie close together in memory; built at
+    // planning time from the structures above (which keep the original numbering)
+    bool have_layout = false;
+    int32_t* d_inv = nullptr;         // internal position -> original point
+    double* d_locs_int = nullptr;     // SoA d x n_tot, internal order
+    double* d_y_int = nullptr;        // internal order
+    int32_t* d_pidx_int = nullptr;    // block members, internal positions
+    int32_t* d_nidx_int = nullptr;    // conditioning points, internal positions
+
     // neighbours
     std::vector<int64_t> h_nptr;
     int64_t* d_nptr = nullptr;
@@ -243,8 +253,12 @@ struct bv_ctx {
 // prediction state teardown (bv_pred.cu); also called when the observations change
 void bv_pred_free(bv_ctx* ctx);
 
+// Hilbert order of the points of one dataset (bv_order.cu): global indices.
+void bv_hilbert_order(const double* locs_rowmajor, int64_t off, int64_t n, int d, std::vector<int32_t>& order);
+
 // helpers in bv_api.cu
 int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* out);
 int bv_ensure_plan(bv_ctx* ctx, int precision);
+int bv_refresh_layout_y(bv_ctx* ctx);
 void bv_invalidate_plans(bv_ctx* ctx);
 int bv_enqueue_loglik(bv_ctx* ctx, int precision, double* d_out, bool with_theta_copy);

@@ -245,3 +245,20 @@ extern "C" int bv_order_blocks(bv_ctx* c, int32_t order, uint64_t seed, int64_t*
     if (point_idx) memcpy(point_idx, c->h_pidx.data(), sizeof(int32_t) * c->n_tot);
     return BV_OK;
 }
+
+// Points of [off, off + n) (row-major host coordinates) in the order of the Hilbert index
+// of their coordinates scaled to 21-bit integers over the range's bounding box (ties by
+// index).  order receives the global point indices.
+void bv_hilbert_order(const double* locs, int64_t off, int64_t n, int d, std::vector<int32_t>& order) {
+    std::vector<double> pts((size_t)n * d);
+    for (int64_t i = 0; i < n * d; ++i) pts[(size_t)i] = locs[(size_t)off * d + i];
+    std::vector<uint64_t> q;
+    quantise21(pts, n, d, q);
+    std::vector<uint64_t> key(n);
+    for (int64_t i = 0; i < n; ++i) key[i] = hilbert21(&q[(size_t)i * d], d);
+    order.resize(n);
+    std::iota(order.begin(), order.end(), (int32_t)0);
+    std::sort(order.begin(), order.end(),
+              [&](int32_t a, int32_t b) { return key[a] < key[b] || (key[a] == key[b] && a < b); });
+    for (auto& v : order) v = (int32_t)(v + off);
+}

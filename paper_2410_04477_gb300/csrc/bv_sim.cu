@@ -252,7 +252,8 @@ extern "C" int bv_simulate(bv_ctx* c, const bv_theta* theta, const double* z, do
     BV_CUDA(cudaMalloc(&d_z, sizeof(double) * c->n_tot));
     BV_CUDA(cudaMemcpyAsync(d_z, z, sizeof(double) * c->n_tot, cudaMemcpyHostToDevice, c->stream));
     BV_CUDA(cudaMemsetAsync(c->d_y, 0, sizeof(double) * c->n_tot, c->stream));
-    const int st = bv_simulate_device(c, th, d_z, c->d_y);
+    int st = bv_simulate_device(c, th, d_z, c->d_y);
+    if (st == BV_OK) st = bv_refresh_layout_y(c);
     cudaFree(d_z);
     if (st != BV_OK) return st;
     c->have_y = true;
