@@ -214,6 +214,7 @@ extern "C" int bv_create(bv_ctx** out, int device, void* stream) {
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_fail, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_wctr, sizeof(int) * 2 * BV_WCTR_PER_PREC);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_fail, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_fb, sizeof(int));
     if (e == cudaSuccess) *c->h_fb = 0;
@@ -234,6 +235,7 @@ extern "C" void bv_destroy(bv_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_data(c);
     dfree(c->d_fail);
+    dfree(c->d_wctr);
     dfree(c->d_ws);
     for (auto s : c->side) cudaStreamDestroy(s);
     for (auto e : c->side_ev) cudaEventDestroy(e);
@@ -730,6 +732,7 @@ static LLArgs make_args(bv_ctx* c) {
     a.theta = c->d_theta;
     a.work = nullptr;
     a.nwork = 0;
+    a.ctr = nullptr;
     a.ell_blk = c->d_ell_blk;
     a.u_blk = c->d_u_blk;
     a.fail = c->d_fail;
@@ -818,6 +821,7 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
         if (L.empty()) continue;
         std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) { return Nof[x] > Nof[y]; });
         BinPlan bp;
+        bp.d_ctr = nullptr;
         bp.kind = b < edges.size() ? smem_kind : 2;
         bp.nmax = Nof[L.front()];
         bp.threads = default_threads(bp.kind, bp.nmax);
@@ -832,6 +836,8 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
     // largest bins first so the long blocks start early
     std::stable_sort(c->plan[prec].begin(), c->plan[prec].end(),
                      [](const BinPlan& x, const BinPlan& y) { return x.nmax > y.nmax; });
+    if (c->plan[prec].size() > BV_WCTR_PER_PREC) return BV_EINVAL;
+    for (size_t i = 0; i < c->plan[prec].size(); ++i) c->plan[prec][i].d_ctr = c->d_wctr + prec * BV_WCTR_PER_PREC + i;
     BV_CUDA(cudaStreamSynchronize(c->stream));
     c->plan_valid[prec] = true;
     return BV_OK;
@@ -846,6 +852,7 @@ static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     float best = 1e30f;
     if (c->cur_gen && bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream) != cudaSuccess) return best;
     for (int r = 0; r < reps + 1; ++r) {
+        if (bv_launch_eval_reset(c->d_fail, c->d_wctr, 2 * BV_WCTR_PER_PREC, c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
         cudaError_t e = bv_launch_bin(bp, a, c->stream);
         cudaEventRecord(e1, c->stream);
@@ -939,7 +946,7 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         BV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->side_ev.push_back(e);
     }
-    BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
+    BV_CUDA(bv_launch_eval_reset(c->d_fail, c->d_wctr, 2 * BV_WCTR_PER_PREC, c->stream));
     if (c->cur_gen) BV_CUDA(bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream));
     const bool fallback = prec == BV_MIXED && c->d_fb;
     if (fallback) BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));

@@ -14,6 +14,12 @@ constexpr double kPiD = 3.141592653589793238462643383279502884;
 // Row-major packed lower triangle: element (r, c), c <= r, at r(r+1)/2 + c.
 __device__ __forceinline__ int pk(int r, int c) { return (r * (r + 1) >> 1) + c; }
 
+// Inverse range of coordinate k (k < 3) read without a dynamically indexed array, which
+// would make the compiler copy the whole parameter struct to local memory.
+__device__ __forceinline__ double inv_range_k(const DevTheta& th, int k) {
+    return k == 0 ? th.inv_range[0] : (k == 1 ? th.inv_range[1] : th.inv_range[2]);
+}
+
 // Inverse of pk over a full triangle: flat index f -> (r, c).
 __device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
     int rr = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
         } else if (r < a.n) {
             double acc = 0.0;
             for (int k = 0; k < a.d; ++k) {
-                const double t = (a.locs[k * a.n + r] - a.locs[k * a.n + c]) * a.th.inv_range[k];
+                const double t = (a.locs[k * a.n + r] - a.locs[k * a.n + c]) * inv_range_k(a.th, k);
                 acc = fma(t, t, acc);
             }
             v = matern_exact(a.th, sqrt(acc));

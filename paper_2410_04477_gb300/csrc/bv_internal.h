@@ -58,6 +58,8 @@ struct DevTheta {
 // L1 + L2 = ln2/256, 2^{n/256} = 2^{floor(n/256)} tab[n mod 256].  Filled on the host in
 // long double.
 #define BV_EXP_TAB 256
+// work counters per precision (at most 15 shared-memory bins and one global-memory bin)
+#define BV_WCTR_PER_PREC 32
 struct ExpConsts {
     double tab[BV_EXP_TAB];   // 2^{j/256}, j = 0..255
     double k;                 // 256 / ln 2
@@ -82,6 +84,7 @@ struct LLArgs {
     const DevTheta* theta;   // per dataset
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
+    int* ctr;                // work counter of this launch (zeroed before it), or null: grid stride
     int gen;                 // host side: launch the general-smoothness instantiation
     int* fb;                 // mixed precision: [0] count, [1..] blocks to redo in FP64 (or null)
     int dyn;                 // global-memory kernel: take the work list and count from fb
@@ -104,6 +107,7 @@ struct BinPlan {
     size_t smem;         // dynamic shared memory bytes
     int32_t* d_work;     // device block ids (largest N first)
     int32_t nwork;
+    int* d_ctr;          // this bin's work counter (a slot of the context's counter array)
     std::vector<int32_t> h_work;
 };
 
@@ -122,6 +126,8 @@ cudaError_t bv_launch_reduce(const double* ell_blk, const double* u_blk, const i
                              int32_t ndata, int32_t maxchunks, void* part, double* out, double* out_quad,
                              cudaStream_t s);
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
+// failure flag reset plus zeroing of n work counters (start of one evaluation)
+cudaError_t bv_launch_eval_reset(unsigned long long* fail, int* ctr, int n, cudaStream_t s);
 // FP64 recomputation (global-memory kernel) of the blocks listed in a.fb.
 cudaError_t bv_launch_fallback(const LLArgs& a, int grid, cudaStream_t s);
 // Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
@@ -221,6 +227,7 @@ struct bv_ctx {
     double* d_quad = nullptr;         // ndata: sum of the quadratic forms
     double* h_quad = nullptr;         // pinned, ndata
     unsigned long long* d_fail = nullptr;
+    int* d_wctr = nullptr;  // per-bin work counters, BV_WCTR_PER_PREC per precision
     double* d_out = nullptr;          // ndata
     double* h_out = nullptr;          // pinned, ndata
     DevTheta* d_theta = nullptr;      // ndata

@@ -70,6 +70,15 @@ __device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
     atomicMin(fail, (unsigned long long)blk);
 }
 
+// Work distribution of one launch.  With a counter, each CTA (or warp) takes its next
+// work item from the launch's atomic counter, asked for one item ahead so that the
+// atomic's latency hides behind the current block; a CTA that starts late (its SM held
+// by a concurrent bin of the same evaluation) then takes fewer items instead of a fixed
+// share.  Without a counter: the fixed grid stride `stride_next`.
+__device__ __forceinline__ int take_work(int* ctr, int stride_next) {
+    return ctr ? atomicAdd(ctr, 1) : stride_next;
+}
+
 // ---------------------------------------------------------------------------------
 // FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2][N+1] | pts[d][N]
 // ---------------------------------------------------------------------------------
@@ -84,7 +93,11 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     for (int i = tid; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
 
-    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+    __shared__ int s_w;
+    if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
+    __syncthreads();
+    for (int w = s_w; w < a.nwork; w = s_w) {
+        const int nx = tid == 0 ? take_work(a.ctr, w + gridDim.x) : 0;
         const int blk = a.work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
         const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
@@ -99,7 +112,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         // gather: conditioning points first, then the block (Algorithm 1 order)
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * th.inv_range[k];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * inv_range_k(th, k);
             A[pk(N, t)] = a.y[g];
         }
         if (tid == 0) {
@@ -198,6 +211,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             }
             a.ell_blk[blk] = ell;
             a.u_blk[blk] = su;
+            s_w = nx;
         }
         __syncthreads();
     }
@@ -462,15 +476,22 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ double2 red2[NT / 32];
     __shared__ int s_fail;
+    __shared__ int s_w;
     const int tid = threadIdx.x;
-    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+    if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
+    __syncthreads();
+    for (int w = s_w; w < a.nwork; w = s_w) {
+        const int nx = tid == 0 ? take_work(a.ctr, w + gridDim.x) : 0;
         const int blk = a.work[w];
         if (tid == 0) s_fail = 0;
         __syncthreads();
         const double2 part = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail);
         const double2 sr = block_sum2<NT>(part.x, part.y, red2);
         const double sres = sr.x, sresu = sr.y;
-        if (tid == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, sresu, s_fail);
+        if (tid == 0) {
+            finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, sresu, s_fail);
+            s_w = nx;
+        }
         __syncthreads();
     }
 }
@@ -484,7 +505,9 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
     __shared__ int s_fail[WPB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* sm = reinterpret_cast<float*>(smraw) + (size_t)warp * region_floats;
-    for (int w = blockIdx.x * WPB + warp; w < a.nwork; w += gridDim.x * WPB) {
+    int w = __shfl_sync(0xffffffffu, lane == 0 ? take_work(a.ctr, blockIdx.x * WPB + warp) : 0, 0);
+    while (w < a.nwork) {
+        const int nx = lane == 0 ? take_work(a.ctr, w + gridDim.x * WPB) : 0;
         const int blk = a.work[w];
         if (lane == 0) s_fail[warp] = 0;
         __syncwarp();
@@ -497,6 +520,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
         __syncwarp();
         if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part.x, part.y, s_fail[warp]);
         __syncwarp();
+        w = __shfl_sync(0xffffffffu, nx, 0);
     }
 }
 
@@ -516,7 +540,11 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
     const int nwork = a.dyn ? *a.fb : a.nwork;
     const int* work = a.dyn ? a.fb + 1 : a.work;
 
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    __shared__ int s_w;
+    if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
+    __syncthreads();
+    for (int w = s_w; w < nwork; w = s_w) {
+        const int nx = tid == 0 ? take_work(a.ctr, w + gridDim.x) : 0;
         const int blk = work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
         const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
@@ -530,7 +558,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
 
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
-            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * th.inv_range[k];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * inv_range_k(th, k);
             A[pk(N, t)] = a.y[g];
         }
         if (tid == 0) {
@@ -607,6 +635,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
             }
             a.ell_blk[blk] = ell;
             a.u_blk[blk] = su;
+            s_w = nx;
         }
         __syncthreads();
     }
@@ -686,6 +715,11 @@ __global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64
 }
 
 __global__ void k_fail_reset(unsigned long long* f) { *f = ~0ull; }
+
+__global__ void k_eval_reset(unsigned long long* f, int* ctr, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ctr[i] = 0;
+    if (threadIdx.x == 0) *f = ~0ull;
+}
 
 __global__ void k_exp_check(const double* x, double* out, int64_t n, ExpConsts ex) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -794,6 +828,7 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     LLArgs a = a0;
     a.work = bp.d_work;
     a.nwork = bp.nwork;
+    a.ctr = bp.d_ctr;
     switch (bp.threads) {
         case 64: return launch_kind<64>(bp.kind, bp.grid, bp.smem, a, s);
         case 128: return launch_kind<128>(bp.kind, bp.grid, bp.smem, a, s);
@@ -831,11 +866,17 @@ cudaError_t bv_launch_fallback(const LLArgs& a0, int grid, cudaStream_t s) {
     LLArgs a = a0;
     a.dyn = 1;
     a.fb = a0.fb;
+    a.ctr = nullptr;
     return a.gen ? launch_kind_g<256, true>(2, grid, 0, a, s) : launch_kind_g<256, false>(2, grid, 0, a, s);
 }
 
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {
     k_fail_reset<<<1, 1, 0, s>>>(fail);
+    return cudaGetLastError();
+}
+
+cudaError_t bv_launch_eval_reset(unsigned long long* fail, int* ctr, int n, cudaStream_t s) {
+    k_eval_reset<<<1, 64, 0, s>>>(fail, ctr, n);
     return cudaGetLastError();
 }
 

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NT) k_na_ll(const double* __restrict__ locs, i
             na_tri(f, r, c);
             double acc = 0.0;
             for (int k = 0; k < d; ++k) {
-                const double t = (px[k * N + r] - px[k * N + c]) * th.inv_range[k];
+                const double t = (px[k * N + r] - px[k * N + c]) * inv_range_k(th, k);
                 acc = fma(t, t, acc);
             }
             double v = na_matern(th, sqrt(acc));

@@ -132,6 +132,9 @@ __host__ __device__ inline int64_t pred_doubles(int64_t N) { return (N + 1) * (N
 // right-looking with look-ahead: warp 0 finishes column k+1 (update by column k, pivot,
 // scale into a column buffer) while the other warps apply column k to the rest of the
 // trailing triangle, one barrier per column; a last pass applies column m-1 everywhere.
+// GEN: general smoothness (series / continued-fraction Bessel function), instantiated
+// apart so that the closed-form path keeps its small register footprint.
+template <bool GEN>
 __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
     constexpr int NT = kPredNT, NU = NT - 32;
     extern __shared__ __align__(16) double sm[];
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
             const bool obs = t < m;
             const int64_t g = obs ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
             for (int k = 0; k < d; ++k)
-                px[k * N + t] = (obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g]) * th.inv_range[k];
+                px[k * N + t] = (obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g]) * inv_range_k(th, k);
             A[pk(N, t)] = obs ? a.y[g] : 0.0;  // data row: [y_NN, 0]
         }
         if (tid == 0) {
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
                 acc = fma(t, t, acc);
             }
             const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
-            double v = (th.nu_code == NU_GENERAL ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2));
+            double v = GEN ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
         }
@@ -459,7 +462,7 @@ extern "C" int bv_select_pred_neighbors(bv_ctx* c, int32_t m, int64_t* nn_ptr, i
     while (pred_doubles(smem_n + 1) * 8 <= (int64_t)kPredSmemCap) ++smem_n;
     if (maxN > smem_n) {
         int grid = 0;
-        BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_pred, kPredNT, 0));
+        BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_pred<false>, kPredNT, 0));
         p->ws_slots = std::max(1, std::min<int>(grid * c->num_sms, 2 * c->num_sms));
         p->ws_stride = (pred_doubles(maxN) + 31) / 32 * 32;
         BV_CUDA(cudaMalloc(&p->d_ws, sizeof(double) * p->ws_stride * p->ws_slots));
@@ -492,9 +495,11 @@ static int pred_launch(bv_ctx* c, const DevTheta& th, bool with_cov) {
     while (pred_doubles(smem_n + 1) * 8 <= (int64_t)kPredSmemCap) ++smem_n;
     const int64_t nsm = std::min<int64_t>(maxN, smem_n);
     const size_t smem = (size_t)pred_doubles(nsm) * 8;
-    BV_CUDA(cudaFuncSetAttribute(k_pred, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPredSmemCap));
+    const bool gen = th.nu_code == NU_GENERAL;
+    auto kern = gen ? k_pred<true> : k_pred<false>;
+    BV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPredSmemCap));
     int per_sm = 0;
-    BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pred, kPredNT, smem));
+    BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPredNT, smem));
     int64_t grid = std::max(1, per_sm) * (int64_t)c->num_sms;
     grid = std::min<int64_t>(grid, p->nblk);
     if (maxN > smem_n) grid = std::min<int64_t>(grid, p->ws_slots);
@@ -521,7 +526,7 @@ static int pred_launch(bv_ctx* c, const DevTheta& th, bool with_cov) {
     a.nblk = p->nblk;
     a.fail = p->d_fail;
     BV_CUDA(cudaMemsetAsync(p->d_fail, 0xff, sizeof(unsigned long long), c->stream));
-    k_pred<<<(unsigned)grid, kPredNT, smem, c->stream>>>(a);
+    kern<<<(unsigned)grid, kPredNT, smem, c->stream>>>(a);
     BV_CUDA(cudaGetLastError());
     return BV_OK;
 }

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_sim_factor(SimArgs a) {
             for (int c = lane; c <= r; c += 32) {
                 double acc = 0.0;
                 for (int k = 0; k < a.d; ++k) {
-                    const double t = (px[k * N + r] - px[k * N + c]) * a.th.inv_range[k];
+                    const double t = (px[k * N + r] - px[k * N + c]) * inv_range_k(a.th, k);
                     acc = fma(t, t, acc);
                 }
                 double v = matern64s(a.th, sqrt(acc));
