@@ -703,6 +703,9 @@ int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
     }
     o->sigma2 = t->sigma2;
     o->nugget = t->nugget;
+    o->sigma2_f = (float)o->sigma2;
+    o->nugget_f = (float)o->nugget;
+    for (int k = 0; k < 3; ++k) o->inv_range_f[k] = (float)o->inv_range[k];
     return BV_OK;
 }
 

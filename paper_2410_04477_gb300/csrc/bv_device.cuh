@@ -32,8 +32,9 @@ __device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
 // e^{-x} for x >= 0 by Tang's table-driven method (see ExpConsts): reduction to
 // |r| <= ln2/512, e^r - 1 by its Taylor polynomial through r^4 (truncation below 4e-17
 // relative), one table multiply and an exponent-field scaling.  9 FP64 operations.
-// Results below e^{-700} are flushed to zero (a covariance entry that small is irrelevant
-// next to the diagonal).  Accuracy: within 2 ulp of e^{-x} (checked against libm in the
+// Results below about e^{-700} are flushed to zero (a covariance entry that small is
+// irrelevant next to the diagonal); the test is an integer compare of the high word
+// (x >= 0, so its bit pattern orders like the value), off the FP64 pipe.  Accuracy: within 2 ulp of e^{-x} (checked against libm in the
 // tests).
 __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ tab, double K, double L1,
                                           double L2) {
@@ -50,7 +51,7 @@ __device__ __forceinline__ double exp_neg(double x, const double* __restrict__ t
     const double v = fma(t, p, t);             // 2^{j/256} e^r in [0.99, 2)
     const int hi = __double2hiint(v) + ((n >> 8) << 20);
     const double res = __hiloint2double(hi, __double2loint(v));
-    return x > 700.0 ? 0.0 : res;
+    return __double2hiint(x) > 0x4085E000 ? 0.0 : res;  // high word of 700.0
 }
 
 // Matern correlation rho(x) = 2^{1-nu}/G(nu) x^nu K_nu(x) of Eq. 5 for any nu > 0.
@@ -174,10 +175,16 @@ __device__ __forceinline__ double matern_gen_tab(const double* __restrict__ tab,
 // through the table-driven exponential).
 __device__ __forceinline__ double matern64t(int nu, double sigma2, double x, const double* tab, double K,
                                             double L1, double L2) {
-    const double e = exp_neg(x, tab, K, L1, L2);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0 + x) * e);
-    return sigma2 * ((1.0 + x * (1.0 + x * (1.0 / 3.0))) * e);
+    const double se = sigma2 * exp_neg(x, tab, K, L1, L2);
+    if (nu == NU_HALF) return se;
+    if (nu == NU_3HALF) return fma(x, se, se);                       // sigma^2 (1 + x) e^{-x}
+    return fma(x * fma(x, 1.0 / 3.0, 1.0), se, se);                  // sigma^2 (1 + x + x^2/3) e^{-x}
+}
+
+// Scaled distance sqrt(acc) for acc >= 0 through the reciprocal square root (within
+// 2 ulp); acc == 0 (and subnormal acc) gives 0, tested on the high word off the FP64 pipe.
+__device__ __forceinline__ double dist_of(double acc) {
+    return __double2hiint(acc) > 0 ? acc * rsqrt(acc) : 0.0;
 }
 
 // FP32 evaluation of the same table (mixed precision: covariance entries are FP32).

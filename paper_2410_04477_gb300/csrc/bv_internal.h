@@ -50,6 +50,8 @@ struct DevTheta {
     int32_t nu_code;
     int32_t nrec;
     double nu, mu, gam1, gam2, gampl, gammi, lognorm;
+    // FP32 copies for the mixed-precision kernels (converted once on the host)
+    float sigma2_f, nugget_f, inv_range_f[3];
 };
 
 // Constants of the table-driven FP64 exponential (Tang, "Table-driven implementation of

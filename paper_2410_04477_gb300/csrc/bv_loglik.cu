@@ -45,25 +45,23 @@ __device__ __forceinline__ float matern32(int nu, float sigma2, float x) {
     return sigma2 * ((1.0f + x * (1.0f + x * (1.0f / 3.0f))) * e);
 }
 
-// Block-wide sums of two values at once (one pair of barriers); valid in thread 0.
-template <int NT>
-__device__ __forceinline__ double2 block_sum2(double v, double w, double2* red2) {
+// Sums of the block columns' terms z_k^2 + log L_kk (Algorithm 1's quadratic form and
+// log-determinant) and of z_k^2 alone, k = m..N-1, taken by the 32 lanes of one warp
+// (a block has few columns, b = N - m); the totals are valid in lane 0.
+template <typename ZF, typename LF>
+__device__ __forceinline__ double2 warp_terms(int m, int N, int lane, ZF zk, LF logk) {
+    double part = 0.0, partu = 0.0;
+    for (int k = m + lane; k < N; k += 32) {
+        const double z = zk(k);
+        partu += z * z;
+        part += z * z + logk(k);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-        w += __shfl_xor_sync(0xffffffffu, w, o);
+        part += __shfl_xor_sync(0xffffffffu, part, o);
+        partu += __shfl_xor_sync(0xffffffffu, partu, o);
     }
-    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red2[wp] = make_double2(v, w);
-    __syncthreads();
-    double2 s = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0)
-        for (int i = 0; i < NT / 32; ++i) {
-            s.x += red2[i].x;
-            s.y += red2[i].y;
-        }
-    __syncthreads();
-    return s;
+    return make_double2(part, partu);
 }
 
 __device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
@@ -86,7 +84,6 @@ template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double* sm = reinterpret_cast<double*>(smraw);
-    __shared__ double2 red2[NT / 32];
     __shared__ double etab[BV_EXP_TAB];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -132,7 +129,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                 acc = fma(t, t, acc);
             }
             // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
-            const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
+            const double x = dist_of(acc);
             double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
                                        th.sigma2, x, etab, eK, eL1, eL2)
                            : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
@@ -194,24 +191,21 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             __syncthreads();
         }
 
-        // u + d over the block columns
-        double part = 0.0, partu = 0.0;
-        for (int k = m + tid; k < N; k += NT) {
-            const double z = A[pk(N, k)];
-            partu += z * z;
-            part += z * z + log(A[pk(k, k)]);
-        }
-        const double2 s2 = block_sum2<NT>(part, partu, red2);
-        const double s = s2.x, su = s2.y;
-        if (tid == 0) {
-            double ell = -0.5 * (s + (double)b * kLog2Pi);
-            if (s_fail || !(ell == ell)) {
-                ell = -INFINITY;
-                record_fail(a.fail, blk);
+        // u + d over the block columns (warp 0)
+        if (warp == 0) {
+            const double2 s2 = warp_terms(m, N, lane, [&](int k) { return A[pk(N, k)]; },
+                                          [&](int k) { return log(A[pk(k, k)]); });
+            const double s = s2.x, su = s2.y;
+            if (lane == 0) {
+                double ell = -0.5 * (s + (double)b * kLog2Pi);
+                if (s_fail || !(ell == ell)) {
+                    ell = -INFINITY;
+                    record_fail(a.fail, blk);
+                }
+                a.ell_blk[blk] = ell;
+                a.u_blk[blk] = su;
+                s_w = nx;
             }
-            a.ell_blk[blk] = ell;
-            a.u_blk[blk] = su;
-            s_w = nx;
         }
         __syncthreads();
     }
@@ -314,15 +308,18 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
     float* dfac = sm + ((((((T * (T + 1)) >> 1) * kTS + 5 * N) + 3) & ~3));  // 16-byte aligned
     float* ydiag = dfac + 24;
     const int d = a.d;
-    const float s2 = (float)th.sigma2, tau2 = (float)th.nugget;
-    const double ir0 = th.inv_range[0], ir1 = th.inv_range[1], ir2 = th.inv_range[2];
+    const float s2 = th.sigma2_f, tau2 = th.nugget_f;
+    // offsets from the block centroid in FP64 (exact enough to keep the block-local
+    // coordinates accurate), rounded to FP32 and scaled by 1/beta in FP32: the FP64 pipe,
+    // 1/64 of the FP32 rate on this part, does only the subtraction and the conversion
+    const float ir0 = th.inv_range_f[0], ir1 = th.inv_range_f[1], ir2 = th.inv_range_f[2];
 
     for (int t = tid; t < N; t += NG) {
         const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
         const double* cb = a.cent + (int64_t)blk * d;
-        px[t] = (float)((a.locs[g] - cb[0]) * ir0);
-        px[N + t] = d > 1 ? (float)((a.locs[a.n_tot + g] - cb[1]) * ir1) : 0.0f;
-        px[2 * N + t] = d > 2 ? (float)((a.locs[2 * a.n_tot + g] - cb[2]) * ir2) : 0.0f;
+        px[t] = (float)(a.locs[g] - cb[0]) * ir0;
+        px[N + t] = d > 1 ? (float)(a.locs[a.n_tot + g] - cb[1]) * ir1 : 0.0f;
+        px[2 * N + t] = d > 2 ? (float)(a.locs[2 * a.n_tot + g] - cb[2]) * ir2 : 0.0f;
         yv[t] = (float)a.y[g];
     }
     gsync<WARP>();
@@ -446,14 +443,15 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
     // quadratic form and log-determinant terms of the block columns, accumulated in FP64
     // (the logarithm of an FP32 pivot is taken in FP32: its 1-ulp error is far below the
     // pivot's own FP32 rounding)
-    double part = 0.0, partu = 0.0;
-    for (int k = m + tid; k < N; k += NG) {
-        const double z = (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
-                                              : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
-        partu += z * z;
-        part += z * z + (double)logf(piv[k]);
-    }
-    return make_double2(part, partu);
+    // by the first warp only; the totals are valid in thread 0
+    if (tid >= 32) return make_double2(0.0, 0.0);
+    return warp_terms(
+        m, N, tid,
+        [&](int k) {
+            return (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
+                                        : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
+        },
+        [&](int k) { return (double)logf(piv[k]); });
 }
 
 // A block whose FP32 factorisation breaks down (non-positive pivot) is queued for the FP64
@@ -474,7 +472,6 @@ template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* sm = reinterpret_cast<float*>(smraw);
-    __shared__ double2 red2[NT / 32];
     __shared__ int s_fail;
     __shared__ int s_w;
     const int tid = threadIdx.x;
@@ -485,11 +482,9 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
         const int blk = a.work[w];
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        const double2 part = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail);
-        const double2 sr = block_sum2<NT>(part.x, part.y, red2);
-        const double sres = sr.x, sresu = sr.y;
+        const double2 sr = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail);
         if (tid == 0) {
-            finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sres, sresu, s_fail);
+            finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sr.x, sr.y, s_fail);
             s_w = nx;
         }
         __syncthreads();
@@ -511,12 +506,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
         const int blk = a.work[w];
         if (lane == 0) s_fail[warp] = 0;
         __syncwarp();
-        double2 part = mixed_block<32, true, GEN>(a, blk, sm, lane, &s_fail[warp]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
-            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
-        }
+        const double2 part = mixed_block<32, true, GEN>(a, blk, sm, lane, &s_fail[warp]);
         __syncwarp();
         if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part.x, part.y, s_fail[warp]);
         __syncwarp();
@@ -530,7 +520,6 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
 // ---------------------------------------------------------------------------------
 template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
-    __shared__ double2 red2[NT / 32];
     __shared__ double etab[BV_EXP_TAB];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -619,23 +608,20 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
             }
             __syncthreads();
         }
-        double part = 0.0, partu = 0.0;
-        for (int k = m + tid; k < N; k += NT) {
-            const double z = A[pk(N, k)];
-            partu += z * z;
-            part += z * z + log(A[pk(k, k)]);
-        }
-        const double2 s2 = block_sum2<NT>(part, partu, red2);
-        const double s = s2.x, su = s2.y;
-        if (tid == 0) {
-            double ell = -0.5 * (s + (double)b * kLog2Pi);
-            if (s_fail || !(ell == ell)) {
-                ell = -INFINITY;
-                record_fail(a.fail, blk);
+        if (warp == 0) {
+            const double2 s2 = warp_terms(m, N, lane, [&](int k) { return A[pk(N, k)]; },
+                                          [&](int k) { return log(A[pk(k, k)]); });
+            const double s = s2.x, su = s2.y;
+            if (lane == 0) {
+                double ell = -0.5 * (s + (double)b * kLog2Pi);
+                if (s_fail || !(ell == ell)) {
+                    ell = -INFINITY;
+                    record_fail(a.fail, blk);
+                }
+                a.ell_blk[blk] = ell;
+                a.u_blk[blk] = su;
+                s_w = nx;
             }
-            a.ell_blk[blk] = ell;
-            a.u_blk[blk] = su;
-            s_w = nx;
         }
         __syncthreads();
     }
@@ -904,7 +890,7 @@ int bv_occupancy(int kind, int threads, size_t smem) {
     return nb;
 }
 
-void bv_exp_consts(ExpConsts* o) {
+static void fill_exp_consts(ExpConsts* o) {
     const long double ln2 = 0.693147180559945309417232121458176568L;
     for (int j = 0; j < BV_EXP_TAB; ++j) o->tab[j] = (double)exp2l((long double)j / (long double)BV_EXP_TAB);
     const long double L = ln2 / (long double)BV_EXP_TAB;
@@ -916,6 +902,17 @@ void bv_exp_consts(ExpConsts* o) {
     o->l1 = l1;
     o->l2 = (double)(L - (long double)l1);
     o->k = (double)((long double)BV_EXP_TAB / ln2);
+}
+
+// The table is computed once per process (long double is a software type on some hosts,
+// which makes 256 exp2l calls cost a fraction of a millisecond).
+void bv_exp_consts(ExpConsts* o) {
+    static const ExpConsts cached = [] {
+        ExpConsts e;
+        fill_exp_consts(&e);
+        return e;
+    }();
+    *o = cached;
 }
 
 // Diagnostic: the library's FP64 exp(-x) on the device for host inputs x[n].

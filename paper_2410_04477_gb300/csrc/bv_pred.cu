@@ -60,6 +60,10 @@ struct PredState {
     int64_t ws_stride = 0;
     int ws_slots = 0;
     bool have_blocks = false, have_nn = false, have_pred = false;
+    // launch shape of k_pred per instantiation (closed-form / general nu), set on first use
+    int64_t launch_grid[2] = {0, 0};
+    size_t launch_smem = 0;
+    int launch_nsm = 0;
 };
 
 namespace {
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
                 const double t = px[k * N + r] - px[k * N + c];
                 acc = fma(t, t, acc);
             }
-            const double x = acc > 0.0 ? acc * rsqrt(acc) : 0.0;
+            const double x = dist_of(acc);
             double v = GEN ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
             if (r == c) v += th.nugget;
             A[f] = v;
@@ -467,6 +471,7 @@ extern "C" int bv_select_pred_neighbors(bv_ctx* c, int32_t m, int64_t* nn_ptr, i
         p->ws_stride = (pred_doubles(maxN) + 31) / 32 * 32;
         BV_CUDA(cudaMalloc(&p->d_ws, sizeof(double) * p->ws_stride * p->ws_slots));
     }
+    p->launch_grid[0] = p->launch_grid[1] = 0;
     p->have_nn = true;
     if (nn_ptr) memcpy(nn_ptr, p->h_nptr.data(), sizeof(int64_t) * (p->nblk + 1));
     if (nn_idx && p->h_nptr.back() > 0)
@@ -488,21 +493,29 @@ extern "C" int bv_get_pred_sizes(bv_ctx* c, int64_t* n_star, int64_t* nblk, int6
 // dynamic shared memory for the largest block that fits.
 static int pred_launch(bv_ctx* c, const DevTheta& th, bool with_cov) {
     PredState* p = c->pred;
-    int64_t maxN = 0;
-    for (int64_t i = 0; i < p->nblk; ++i)
-        maxN = std::max(maxN, (p->h_nptr[i + 1] - p->h_nptr[i]) + (p->h_bptr[i + 1] - p->h_bptr[i]));
-    int smem_n = 0;
-    while (pred_doubles(smem_n + 1) * 8 <= (int64_t)kPredSmemCap) ++smem_n;
-    const int64_t nsm = std::min<int64_t>(maxN, smem_n);
-    const size_t smem = (size_t)pred_doubles(nsm) * 8;
     const bool gen = th.nu_code == NU_GENERAL;
     auto kern = gen ? k_pred<true> : k_pred<false>;
-    BV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPredSmemCap));
-    int per_sm = 0;
-    BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPredNT, smem));
-    int64_t grid = std::max(1, per_sm) * (int64_t)c->num_sms;
-    grid = std::min<int64_t>(grid, p->nblk);
-    if (maxN > smem_n) grid = std::min<int64_t>(grid, p->ws_slots);
+    if (p->launch_grid[gen] == 0) {
+        int64_t maxN = 0;
+        for (int64_t i = 0; i < p->nblk; ++i)
+            maxN = std::max(maxN, (p->h_nptr[i + 1] - p->h_nptr[i]) + (p->h_bptr[i + 1] - p->h_bptr[i]));
+        int smem_n = 0;
+        while (pred_doubles(smem_n + 1) * 8 <= (int64_t)kPredSmemCap) ++smem_n;
+        const int64_t nsm = std::min<int64_t>(maxN, smem_n);
+        const size_t smem = (size_t)pred_doubles(nsm) * 8;
+        BV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPredSmemCap));
+        int per_sm = 0;
+        BV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPredNT, smem));
+        int64_t grid = std::max(1, per_sm) * (int64_t)c->num_sms;
+        grid = std::min<int64_t>(grid, p->nblk);
+        if (maxN > smem_n) grid = std::min<int64_t>(grid, p->ws_slots);
+        p->launch_grid[gen] = std::max<int64_t>(1, grid);
+        p->launch_smem = smem;
+        p->launch_nsm = (int)nsm;
+    }
+    const int64_t grid = p->launch_grid[gen];
+    const size_t smem = p->launch_smem;
+    const int64_t nsm = p->launch_nsm;
     PredArgs a;
     a.locs = c->d_locs;
     a.n_obs = c->n_tot;
