@@ -20,6 +20,12 @@ __device__ __forceinline__ double inv_range_k(const DevTheta& th, int k) {
     return k == 0 ? th.inv_range[0] : (k == 1 ? th.inv_range[1] : th.inv_range[2]);
 }
 
+// A Cholesky pivot that is not a positive, finite, (nearly) normal number -- zero, negative,
+// infinite or NaN -- tested on the high word with integer operations (off the FP64 pipe).
+__device__ __forceinline__ bool bad_pivot(double p) {
+    return (unsigned)(__double2hiint(p) - 1) >= 0x7FEFFFFFu;
+}
+
 // Inverse of pk over a full triangle: flat index f -> (r, c).
 __device__ __forceinline__ void tri_rc(int f, int& r, int& c) {
     int rr = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
             for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * inv_range_k(th, k);
             A[pk(N, t)] = a.y[g];
+            A[pk(t, t)] = th.sigma2 + th.nugget;  // diagonal of Eq. 5 + nugget: rho(0) = 1
         }
         if (tid == 0) {
             A[pk(N, N)] = 0.0;
@@ -118,11 +119,13 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         }
         __syncthreads();
 
-        // covariance (Eq. 5 + nugget), lower triangle rows 0..N-1: packed index == flat index
-        const int T = (N * (N + 1)) >> 1;
+        // covariance (Eq. 5), strictly lower triangle of rows 1..N-1: flat index f over that
+        // triangle maps to (r' + 1, c) with (r', c) = tri_rc(f), packed index f + r' + 1
+        const int T = (N * (N - 1)) >> 1;
         for (int f = tid; f < T; f += NT) {
             int r, c;
             tri_rc(f, r, c);
+            ++r;
             double acc = 0.0;
             for (int k = 0; k < d; ++k) {
                 const double t = px[k * N + r] - px[k * N + c];
@@ -130,18 +133,17 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
             }
             // x = acc / sqrt(acc) through the reciprocal square root (within 2 ulp)
             const double x = dist_of(acc);
-            double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
-                                       th.sigma2, x, etab, eK, eL1, eL2)
-                           : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
-            if (r == c) v += th.nugget;
-            A[f] = v;
+            const double v = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk],
+                                             th.nu_code, th.sigma2, x, etab, eK, eL1, eL2)
+                                 : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
+            A[f + r] = v;
         }
         __syncthreads();
 
         // column 0
         if (warp == 0) {
             const double p = A[0];
-            if (!(p > 0.0) && lane == 0) s_fail = 1;
+            if (bad_pivot(p) && lane == 0) s_fail = 1;
             const double rs = rsqrt(p);
             for (int j = 1 + lane; j <= N; j += 32) {
                 const double v = A[pk(j, 0)] * rs;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
                 for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
                 __syncwarp();
                 const double p = A[pk(kk, kk)];
-                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                if (bad_pivot(p) && lane == 0) s_fail = 1;
                 const double rs = rsqrt(p);
                 for (int j = kk + 1 + lane; j <= N; j += 32) {
                     const double v = A[pk(j, kk)] * rs;
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
         __syncthreads();
         if (warp == 0) {
             const double p = A[0];
-            if (!(p > 0.0) && lane == 0) s_fail = 1;
+            if (bad_pivot(p) && lane == 0) s_fail = 1;
             const double rs = rsqrt(p);
             for (int j = 1 + lane; j <= N; j += 32) {
                 const double v = A[pk(j, 0)] * rs;
@@ -592,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
                 for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
                 __syncwarp();
                 const double p = A[pk(kk, kk)];
-                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                if (bad_pivot(p) && lane == 0) s_fail = 1;
                 const double rs = rsqrt(p);
                 for (int j = kk + 1 + lane; j <= N; j += 32) {
                     const double v = A[pk(j, kk)] * rs;

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NT) k_na_ll(const double* __restrict__ locs, i
         __syncthreads();
         if (warp == 0) {
             const double p = A[0];
-            if (!(p > 0.0) && lane == 0) s_fail = 1;
+            if (bad_pivot(p) && lane == 0) s_fail = 1;
             const double rs = rsqrt(p);
             for (int j = 1 + lane; j <= N; j += 32) {
                 const double v = A[na_pk(j, 0)] * rs;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NT) k_na_ll(const double* __restrict__ locs, i
                 for (int j = kk + lane; j <= N; j += 32) A[na_pk(j, kk)] = fma(-cur[j], ck, A[na_pk(j, kk)]);
                 __syncwarp();
                 const double p = A[na_pk(kk, kk)];
-                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                if (bad_pivot(p) && lane == 0) s_fail = 1;
                 const double rs = rsqrt(p);
                 for (int j = kk + 1 + lane; j <= N; j += 32) {
                     const double v = A[na_pk(j, kk)] * rs;

@@ -163,32 +163,33 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
             for (int k = 0; k < d; ++k)
                 px[k * N + t] = (obs ? a.locs[(int64_t)k * a.n_obs + g] : a.plocs[(int64_t)k * a.n_star + g]) * inv_range_k(th, k);
             A[pk(N, t)] = obs ? a.y[g] : 0.0;  // data row: [y_NN, 0]
+            A[pk(t, t)] = th.sigma2 + th.nugget; // every row is its own point: rho(0) = 1 + nugget
         }
         if (tid == 0) {
             A[pk(N, N)] = 0.0;
             s_fail = 0;
         }
         __syncthreads();
-        // covariance rows 0..N-1 (Eq. 5; nugget on the diagonal: every row is its own point)
-        const int T = (N * (N + 1)) >> 1;
+        // covariance (Eq. 5), strictly lower triangle of rows 1..N-1 (flat index f -> row
+        // r' + 1, column c with (r', c) = tri_rc(f); packed index f + r' + 1)
+        const int T = (N * (N - 1)) >> 1;
         for (int f = tid; f < T; f += NT) {
             int r, c;
             tri_rc(f, r, c);
+            ++r;
             double acc = 0.0;
             for (int k = 0; k < d; ++k) {
                 const double t = px[k * N + r] - px[k * N + c];
                 acc = fma(t, t, acc);
             }
             const double x = dist_of(acc);
-            double v = GEN ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
-            if (r == c) v += th.nugget;
-            A[f] = v;
+            A[f + r] = GEN ? th.sigma2 * matern_gen_corr(th, x) : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
         }
         __syncthreads();
         if (m > 0) {
             if (warp == 0) {
                 const double p = A[0];
-                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                if (bad_pivot(p) && lane == 0) s_fail = 1;
                 const double rs = rsqrt(p);
                 for (int j = 1 + lane; j <= N; j += 32) {
                     const double v = A[pk(j, 0)] * rs;
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kPredNT) k_pred(PredArgs a) {
                     for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
                     __syncwarp();
                     const double p = A[pk(kk, kk)];
-                    if (!(p > 0.0) && lane == 0) s_fail = 1;
+                    if (bad_pivot(p) && lane == 0) s_fail = 1;
                     const double rs = rsqrt(p);
                     for (int j = kk + 1 + lane; j <= N; j += 32) {
                         const double v = A[pk(j, kk)] * rs;

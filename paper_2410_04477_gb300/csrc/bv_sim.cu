@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_sim_factor(SimArgs a) {
         for (int k = 0; k < N; ++k) {
             if (warp == 0) {
                 const double p = A[pk64(k, k)];
-                if (!(p > 0.0) && lane == 0) s_fail = 1;
+                if (bad_pivot(p) && lane == 0) s_fail = 1;
                 const double l = sqrt(p), rl = 1.0 / l;
                 if (lane == 0) A[pk64(k, k)] = l;
                 for (int j = k + 1 + lane; j < N; j += 32) A[pk64(j, k)] *= rl;

@@ -1,0 +1,87 @@
+"""GPU: work distribution of the likelihood kernels.  The CTAs (or warps) of every size bin
+take their blocks from an atomic work counter that the evaluation's first kernel zeroes, so
+each evaluation must process every block exactly once whatever ran before it: these tests
+interleave parameter vectors, precisions and re-tuned launch plans on one context and check
+every result against the FP64 oracle on the same structure, and that repeats agree bit for
+bit (the per-block arithmetic does not depend on which CTA, or which CTA size, computes it).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def bv():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2410_04477_gb300 import bv as _bv
+    return _bv
+
+
+THETAS = [(1.0, 0.08, 1.5, 1e-3), (0.7, 0.03, 0.5, 1e-2), (1.4, 0.15, 2.5, 1e-4)]
+
+
+def _setup(bv, n=3000, seed=11, bc=150, m=40):
+    locs = synth.locs_uniform(n, 2, seed)
+    y = oracle.exact_draw(oracle.theta(*THETAS[0]), locs, synth.normal(seed, 20, n))
+    ctx = bv.Context()
+    ctx.set_data(locs, y)
+    bp, pi = ctx.build_blocks(bc, seed=seed, iters=20)
+    nnp, nni = ctx.select_neighbors(m)
+    ref = [oracle.loglik(oracle.theta(*t), locs, y, bp, pi, nnp, nni)[0] for t in THETAS]
+    return ctx, ref
+
+
+def test_interleaved_evaluations_cover_every_block(bv):
+    ctx, ref = _setup(bv)
+    seq = [(0, bv.BV_FP64), (1, bv.BV_FP64), (0, bv.BV_MIXED), (2, bv.BV_FP64), (0, bv.BV_FP64),
+           (1, bv.BV_MIXED), (1, bv.BV_FP64), (2, bv.BV_MIXED), (0, bv.BV_MIXED), (2, bv.BV_FP64)]
+    seen = {}
+    with ctx:
+        for i, prec in seq:
+            ll = ctx.loglik(bv.theta(*THETAS[i]), prec)
+            if prec == bv.BV_FP64:
+                assert abs(ll - ref[i]) <= REL64 * abs(ref[i]), (i, ll, ref[i])
+            else:
+                assert abs(ll - ref[i]) <= 1e-5 * abs(ref[i]), (i, ll, ref[i])
+            key = (i, prec)
+            if key in seen:
+                assert ll == seen[key], (key, ll, seen[key])
+            seen[key] = ll
+
+
+def test_retuned_plan_gives_identical_fp64_result(bv):
+    ctx, ref = _setup(bv, n=2500, seed=12, bc=100, m=60)
+    with ctx:
+        th = bv.theta(*THETAS[0])
+        first = ctx.loglik(th, bv.BV_FP64)
+        assert abs(first - ref[0]) <= REL64 * abs(ref[0])
+        for _ in range(2):
+            ctx.autotune(bv.BV_FP64)     # new timings, possibly other CTA sizes; new graph
+            assert ctx.loglik(th, bv.BV_FP64) == first
+
+
+def test_asynchronous_back_to_back_evaluations(bv):
+    # several evaluations queued on the stream before any synchronisation: each one's
+    # counters are zeroed in stream order, so every queued result is complete
+    import torch
+    ctx, ref = _setup(bv, n=2000, seed=13, bc=100, m=30)
+    outs = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(6)]
+    torch.cuda.synchronize()    # the context's stream does not order against torch's
+    with ctx:
+        ctx.loglik(bv.theta(*THETAS[0]), bv.BV_FP64)        # plan, tuning and graph first
+        for k, o in enumerate(outs):
+            ctx.loglik_async([bv.theta(*THETAS[k % 3])], bv.BV_FP64, o.data_ptr())
+        st, _ = ctx.sync()
+        assert st == 0
+        got = [float(o.item()) for o in outs]
+    for k, g in enumerate(got):
+        r = ref[k % 3]
+        assert abs(g - r) <= REL64 * abs(r), (k, g, r)
+    assert got[0] == got[3] and got[1] == got[4] and got[2] == got[5]
