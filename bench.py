@@ -37,9 +37,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5 at max clock
 
 # DRAM bytes (read + write) of one evaluation's likelihood-kernel launches, summed over
-# the size bins, from an ncu capture of the same command (profiles/k_ll_fp64_c2_m60.md);
-# reported as roofline.traffic for that workload and precision only.
-NCU_TRAFFIC = {("c2_m60", "fp64"): 18_500_864 + 256}
+# the six size bins, from an ncu capture of the same command (profiles/k_ll_fp64_c2_m60.md:
+# 14.16 MB read, nothing written); reported as roofline.traffic for that workload and
+# precision only.
+NCU_TRAFFIC = {("c2_m60", "fp64"): 40_704 + 36_864 + 632_576 + 10_817_280 + 2_585_856 + 42_240}
 
 WORKLOADS = {
     # batched plain FP64: 2e5 uniform points, bc 2e4, m 60 / 120, y from BV at m=400
@@ -509,7 +510,8 @@ def run_pred(args, w, log):
             dist.barrier()
 
     def step(k, timing):
-        flush.zero_()
+        with torch.cuda.stream(stream):   # the flush finishes before the timed calls start
+            flush.zero_()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
         ctx.predict(th, want=())
