@@ -215,35 +215,43 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
 
 // ---------------------------------------------------------------------------------
 // Mixed: FP32 covariance and updates, FP64 log-determinant and quadratic form.
-// The augmented matrix is held as 4x4 tiles (lower tile triangle; tile (I,J) starts at
-// (I(I+1)/2 + J) * kTS floats, row-major inside the tile; kTS = 20 pads each tile to 80
-// bytes so that eight consecutive tiles fall on distinct 16-byte bank groups), factored
-// by 4-column panels:
+// The augmented matrix is held as 4x4 tiles (lower tile triangle; tile q = I(I+1)/2 + J
+// starts at 16 q floats; row r of a tile, 16 bytes, is stored at row slot r ^ ((q >> 1) & 3),
+// so that the same row of eight consecutive tiles falls on eight distinct 16-byte bank
+// groups without padding), factored by 4-column panels:
 //   panel p:  every thread solves its rows of tile column p against the factored 4x4
-//             diagonal tile (read from `dfac`, one barrier);
+//             diagonal tile (read from `dfac`) and stores them, contiguous and swizzled
+//             the same way, in `pbuf` (in place only for the tile holding row N, whose
+//             z entries are read at the end; one barrier);
 //   update:   every trailing tile (I,J), p < J <= I, is updated by one thread,
-//             A_IJ -= P_I P_J^T with 128-bit shared-memory accesses; the thread that
-//             updates the next diagonal tile (always thread 0) factors it at once into
-//             `dfac` (look-ahead), so the pivots never sit on every thread's path.
+//             A_IJ -= P_I P_J^T with 128-bit shared-memory accesses, P_I and P_J read
+//             from `pbuf` (consecutive threads take consecutive J: conflict-free); the
+//             thread that updates the next diagonal tile (always thread 0) factors it at
+//             once into `dfac` (look-ahead), so the pivots never sit on every thread's path.
 // Coordinates are taken relative to the block centroid in FP64 and rounded to FP32, so
 // FP32 differences keep their relative accuracy for nearby points.
 // ---------------------------------------------------------------------------------
-constexpr int kTS = 20;  // floats per stored 4x4 tile (16 + 4 padding)
+constexpr int kTS = 16;  // floats per stored 4x4 tile
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ float* tile_at(float* t, int I, int J) { return t + (((I * (I + 1)) >> 1) + J) * kTS; }
+__device__ __forceinline__ int tile_index(int I, int J) { return ((I * (I + 1)) >> 1) + J; }
+// Row r (4 floats, 16-byte aligned) of tile q in a swizzled tile array.
+__device__ __forceinline__ float* tile_row(float* t, int q, int r) { return t + q * kTS + 4 * (r ^ ((q >> 1) & 3)); }
+__device__ __forceinline__ const float* tile_row(const float* t, int q, int r) {
+    return t + q * kTS + 4 * (r ^ ((q >> 1) & 3));
+}
 
-// Factor the 4x4 diagonal tile at `tp` (pivot columns c < nc) into dfac:
+// Factor the 4x4 diagonal tile q of `tiles` (pivot columns c < nc) into dfac:
 // dfac[0..15] = L (strictly lower part), dfac[16..19] = 1/sqrt(pivot), dfac[20..23] = pivot.
 // Writes the pivots of global columns k0.. to piv, row N's entries (if row N lies in this
 // tile) to ydiag, and raises *fail on a non-positive pivot.
-__device__ __forceinline__ void factor_diag(const float* tp, int nc, int k0, int N, float* dfac, float* piv,
-                                            float* ydiag, int* fail) {
+__device__ __forceinline__ void factor_diag(const float* tiles, int qd, int nc, int k0, int N, float* dfac,
+                                            float* piv, float* ydiag, int* fail) {
     float D[16];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const float4 q = ld4(tp + 4 * r);
+        const float4 q = ld4(tile_row(tiles, qd, r));
         D[4 * r] = q.x;
         D[4 * r + 1] = q.y;
         D[4 * r + 2] = q.z;
@@ -288,9 +296,10 @@ __device__ __forceinline__ void gsync() {
 }
 
 // Floats of shared memory one mixed-precision block of augmented size <= nmax needs.
+// Layout: tiles (T(T+1)/2 x 16) | pbuf (T x 16) | px (3 N) | y (N) | pivots (N) | dfac (28).
 __host__ __device__ __forceinline__ int mixed_floats(int nmax) {
     const int T = (nmax + 1 + 3) >> 2;
-    return ((((T * (T + 1)) >> 1) * kTS + 5 * nmax + 28) + 3) & ~3;
+    return ((((T * (T + 1)) >> 1) * kTS + T * kTS + 5 * nmax + 28) + 3) & ~3;
 }
 
 // One block, mixed precision, by a group of NG threads (tid in [0, NG)).  sm: the
@@ -304,10 +313,11 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
     const int N = m + b, R = N + 1, T = (R + 3) >> 2;
     const DevTheta th = a.theta[a.bds[blk]];
     float* tiles = sm;
-    float* px = tiles + ((T * (T + 1)) >> 1) * kTS;
+    float* pbuf = tiles + ((T * (T + 1)) >> 1) * kTS;
+    float* px = pbuf + T * kTS;
     float* yv = px + 3 * N;
     float* piv = yv + N;
-    float* dfac = sm + ((((((T * (T + 1)) >> 1) * kTS + 5 * N) + 3) & ~3));  // 16-byte aligned
+    float* dfac = sm + ((((((T * (T + 1)) >> 1) * kTS + T * kTS + 5 * N) + 3) & ~3));  // 16-byte aligned
     float* ydiag = dfac + 24;
     const int d = a.d;
     const float s2 = th.sigma2_f, tau2 = th.nugget_f;
@@ -332,7 +342,6 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
     for (int q = tid; q < NTL; q += NG) {
         int I, J;
         tri_rc(q, I, J);
-        float* tp = tiles + q * kTS;
         float cx[4], cy[4], cz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -367,11 +376,11 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                     o[e] = (r == N && c < N) ? yv[c] : 0.0f;
                 }
             }
-            st4(tp + 4 * rr, make_float4(o[0], o[1], o[2], o[3]));
+            st4(tile_row(tiles, q, rr), make_float4(o[0], o[1], o[2], o[3]));
         }
     }
     gsync<WARP>();
-    if (tid == 0) factor_diag(tiles, min(4, N), 0, N, dfac, piv, ydiag, fail);
+    if (tid == 0) factor_diag(tiles, 0, min(4, N), 0, N, dfac, piv, ydiag, fail);
     gsync<WARP>();
 
     for (int p = 0; (p << 2) < N; ++p) {
@@ -395,7 +404,7 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                 rs[3] = q.w;
             }
             for (int r = k0 + 4 + tid; r < (T << 2); r += NG) {
-                float* rowp = tile_at(tiles, r >> 2, p) + 4 * (r & 3);
+                float* rowp = tile_row(tiles, tile_index(r >> 2, p), r & 3);
                 const float4 q = ld4(rowp);
                 float x[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -405,7 +414,10 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                     for (int q2 = 0; q2 < c; ++q2) v = fmaf(-x[q2], L[4 * c + q2], v);
                     x[c] = c < nc ? v * rs[c] : 0.0f;
                 }
-                st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
+                // the trailing update reads the solved column from pbuf; of tile column p
+                // only the tile holding row N (its z entries) is read again in place
+                if ((r >> 2) == (N >> 2)) st4(rowp, make_float4(x[0], x[1], x[2], x[3]));
+                st4(tile_row(pbuf, (r >> 2) - p - 1, r & 3), make_float4(x[0], x[1], x[2], x[3]));
             }
         }
         gsync<WARP>();
@@ -415,29 +427,27 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
         for (int q = tid; q < cnt; q += NG) {
             int ii, jj;
             tri_rc(q, ii, jj);
-            const int I = p + 1 + ii, J = p + 1 + jj;
-            const float* PI = tile_at(tiles, I, p);
-            const float* PJ = tile_at(tiles, J, p);
-            float* At = tile_at(tiles, I, J);
+            const int I = p + 1 + ii, J = p + 1 + jj, qa = tile_index(I, J);
             float pi[16], pj[16];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float4 u = ld4(PI + 4 * r), v = ld4(PJ + 4 * r);
+                const float4 u = ld4(tile_row(pbuf, ii, r)), v = ld4(tile_row(pbuf, jj, r));
                 pi[4 * r] = u.x; pi[4 * r + 1] = u.y; pi[4 * r + 2] = u.z; pi[4 * r + 3] = u.w;
                 pj[4 * r] = v.x; pj[4 * r + 1] = v.y; pj[4 * r + 2] = v.z; pj[4 * r + 3] = v.w;
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float4 acc = ld4(At + 4 * r);
+                float* at = tile_row(tiles, qa, r);
+                const float4 acc = ld4(at);
                 float o[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) o[c] = fmaf(-pi[4 * r + k], pj[4 * c + k], o[c]);
-                st4(At + 4 * r, make_float4(o[0], o[1], o[2], o[3]));
+                st4(at, make_float4(o[0], o[1], o[2], o[3]));
             }
             if (q == 0 && ((p + 1) << 2) < N)
-                factor_diag(At, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, fail);
+                factor_diag(tiles, qa, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, fail);
         }
         gsync<WARP>();
     }
@@ -451,7 +461,7 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
         m, N, tid,
         [&](int k) {
             return (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
-                                        : (double)tile_at(tiles, N >> 2, k >> 2)[((N & 3) << 2) + (k & 3)];
+                                        : (double)tile_row(tiles, tile_index(N >> 2, k >> 2), N & 3)[k & 3];
         },
         [&](int k) { return (double)logf(piv[k]); });
 }

@@ -58,7 +58,7 @@ def test_tiny_problems(bv, n, bc, m):
 
 
 def test_single_block_is_exact_through_the_global_kernel(bv):
-    n = 300                                   # N = 300 > the shared-memory limit
+    n = 400                                   # N = 400: above both shared-memory limits
     locs = synth.locs_uniform(n, 2, 122)
     th = (1.0, 0.1, 2.5, 1e-2)
     y = oracle.exact_draw(oracle.theta(*th), locs, synth.normal(122, 20, n))
