@@ -303,9 +303,8 @@ __host__ __device__ __forceinline__ int mixed_floats(int nmax) {
 }
 
 // One block, mixed precision, by a group of NG threads (tid in [0, NG)).  sm: the
-// group's shared region (mixed_floats(N) floats, 16-byte aligned).  Returns the group's
-// partial sum of z^2 + log pivot over the block columns in every thread (valid after the
-// caller reduces it) and sets *fail.
+// group's shared region (mixed_floats(N) floats, 16-byte aligned).  Returns (sum of
+// z^2 + log pivot, sum of z^2) over the block columns, valid in thread 0, and sets *fail.
 template <int NG, bool WARP, bool GEN>
 __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
     const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];

@@ -131,8 +131,9 @@ struct PredArgs {
 // N+1 and d x N coordinates (d <= 3).
 __host__ __device__ inline int64_t pred_doubles(int64_t N) { return (N + 1) * (N + 2) / 2 + 2 * (N + 1) + 3 * N; }
 
-// One CTA per prediction block (grid-stride).  Gather, covariance into the packed
-// triangle (flat index, table-driven exponential), then the first m columns eliminated
+// One CTA per prediction block (grid-stride).  Gather (with the diagonal sigma^2 + nugget),
+// covariance of the strictly lower triangle (flat index, table-driven exponential), then
+// the first m columns eliminated
 // right-looking with look-ahead: warp 0 finishes column k+1 (update by column k, pivot,
 // scale into a column buffer) while the other warps apply column k to the rest of the
 // trailing triangle, one barrier per column; a last pass applies column m-1 everywhere.
