@@ -757,7 +757,7 @@ static int set_grid(bv_ctx* c, BinPlan& bp) {
     }
     const int occ = bv_occupancy(bp.kind, bp.threads, bp.smem);
     if (occ <= 0) return BV_EINTERNAL;
-    const int64_t per_cta = bp.kind == 3 ? bp.threads / 32 : 1;  // blocks in flight per CTA
+    const int64_t per_cta = (bp.kind == 3 || bp.kind == 4) ? bp.threads / 32 : 1;  // blocks in flight per CTA
     bp.grid = (int)std::min<int64_t>((bp.nwork + per_cta - 1) / per_cta, (int64_t)occ * c->num_sms);
     return BV_OK;
 }
@@ -882,11 +882,14 @@ static int autotune(bv_ctx* c, int prec) {
     for (auto& bp : c->plan[prec]) {
         if (bp.kind == 2) continue;
         // candidates: CTA per block with 1 panel warp + 2/4/8/16 update warps; for small
-        // mixed-precision blocks also a warp per block with 2/4/8 warps per CTA
+        // blocks also a warp per block with 2/4/8 warps per CTA (mixed up to N = 128,
+        // FP64 up to N = 64)
         std::vector<std::pair<int, int>> cands;
         for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
         if (bp.kind == 1 && bp.nmax <= 128)
             for (int t : {64, 128, 256}) cands.push_back({3, t});
+        if (bp.kind == 0 && bp.nmax <= 64)
+            for (int t : {64, 128, 256}) cands.push_back({4, t});
         int best_k = bp.kind, best_t = bp.threads;
         float best_ms = 1e30f;
         for (auto kt : cands) {

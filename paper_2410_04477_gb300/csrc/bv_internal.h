@@ -102,7 +102,7 @@ struct LLArgs {
 // Per-size-bin launch plan entry.
 struct BinPlan {
     int kind;            // 0: FP64 shared-memory, 1: mixed (CTA per block), 2: large (global),
-                         // 3: mixed (warp per block)
+                         // 3: mixed (warp per block), 4: FP64 (warp per block)
     int nmax;            // largest augmented size N = m + b in the bin
     int threads;         // CTA size (autotuned)
     int grid;            // CTAs launched

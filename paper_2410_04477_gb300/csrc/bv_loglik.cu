@@ -526,6 +526,99 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
 }
 
 // ---------------------------------------------------------------------------------
+// FP64, one warp per block (several blocks per CTA): for small blocks, where a CTA's
+// barriers and partly filled update warps cost more than the work.  Same arithmetic as
+// k_ll_fp64 (gather with the diagonal, strictly-lower covariance, right-looking Cholesky
+// of the augmented matrix, Algorithm 1 order); every column's pivot, scaling and trailing
+// update by the warp's 32 lanes with warp synchronisation only.  Layout per warp
+// (doubles, region_doubles each): A packed (N+1)(N+2)/2 | col[N+1] | pts[d][N].
+// ---------------------------------------------------------------------------------
+template <int NT, bool GEN>
+__global__ void __launch_bounds__(NT) k_ll_fp64_w(LLArgs a, int region_doubles) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int WPB = NT / 32;
+    __shared__ double etab[BV_EXP_TAB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
+    __syncthreads();
+    const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
+    double* A = reinterpret_cast<double*>(smraw) + (size_t)warp * region_doubles;
+    int w = __shfl_sync(0xffffffffu, lane == 0 ? take_work(a.ctr, blockIdx.x * WPB + warp) : 0, 0);
+    while (w < a.nwork) {
+        const int nx = lane == 0 ? take_work(a.ctr, w + gridDim.x * WPB) : 0;
+        const int blk = a.work[w];
+        const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
+        const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
+        const int N = m + b, R = N + 1;
+        const DevTheta th = a.theta[a.bds[blk]];
+        double* col = A + ((R * (R + 1)) >> 1);
+        double* px = col + R;
+        const int d = a.d;
+
+        for (int t = lane; t < N; t += 32) {
+            const int g = t < m ? a.nidx[n0 + t] : a.pidx[b0 + (t - m)];
+            for (int k = 0; k < d; ++k) px[k * N + t] = a.locs[(int64_t)k * a.n_tot + g] * inv_range_k(th, k);
+            A[pk(N, t)] = a.y[g];
+            A[pk(t, t)] = th.sigma2 + th.nugget;
+        }
+        if (lane == 0) A[pk(N, N)] = 0.0;
+        __syncwarp();
+        const int T = (N * (N - 1)) >> 1;
+        for (int f = lane; f < T; f += 32) {
+            int r, c;
+            tri_rc(f, r, c);
+            ++r;
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double t = px[k * N + r] - px[k * N + c];
+                acc = fma(t, t, acc);
+            }
+            const double x = dist_of(acc);
+            A[f + r] = GEN ? matern64g(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], th.nu_code,
+                                       th.sigma2, x, etab, eK, eL1, eL2)
+                           : matern64t(th.nu_code, th.sigma2, x, etab, eK, eL1, eL2);
+        }
+        __syncwarp();
+
+        bool bad = false;  // the same pivot in every lane: warp-uniform
+        for (int k = 0; k < N; ++k) {
+            const double p = A[pk(k, k)];
+            bad = bad || bad_pivot(p);
+            const double rs = rsqrt(p);
+            for (int j = k + 1 + lane; j <= N; j += 32) {
+                const double v = A[pk(j, k)] * rs;
+                A[pk(j, k)] = v;
+                col[j] = v;
+            }
+            __syncwarp();
+            // trailing triangle, rows and columns k+1..N (row N: the forward solve of y)
+            const int S = N - k;
+            const int TS = (S * (S + 1)) >> 1;
+            for (int f = lane; f < TS; f += 32) {
+                int r, c;
+                tri_rc(f, r, c);
+                const int j = k + 1 + r, i = k + 1 + c;
+                A[pk(j, i)] = fma(-col[j], col[i], A[pk(j, i)]);
+            }
+            __syncwarp();
+        }
+        const double2 s2 = warp_terms(m, N, lane, [&](int k) { return A[pk(N, k)]; },
+                                      [&](int k) { return log(A[pk(k, k)]); });
+        if (lane == 0) {
+            double ell = -0.5 * (s2.x + (double)b * kLog2Pi);
+            if (bad || !(ell == ell)) {
+                ell = -INFINITY;
+                record_fail(a.fail, blk);
+            }
+            a.ell_blk[blk] = ell;
+            a.u_blk[blk] = s2.y;
+        }
+        __syncwarp();
+        w = __shfl_sync(0xffffffffu, nx, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Large blocks: same algorithm in FP64 with the packed triangle in a global workspace
 // slot (one slot per CTA; the grid never exceeds the number of slots).
 // ---------------------------------------------------------------------------------
@@ -767,6 +860,8 @@ cudaError_t set_smem_cap_g() {
         e = cudaFuncSetAttribute(k_ll_mixed<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ll_mixed_w<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_fp64_w<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     return e;
 }
 
@@ -783,6 +878,7 @@ cudaError_t launch_kind_g(int kind, int grid, size_t smem, const LLArgs& a, cuda
     if (kind == 0) k_ll_fp64<NT, GEN><<<grid, NT, smem, s>>>(a);
     else if (kind == 1) k_ll_mixed<NT, GEN><<<grid, NT, smem, s>>>(a);
     else if (kind == 3) k_ll_mixed_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
+    else if (kind == 4) k_ll_fp64_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(double) / (NT / 32)));
     else k_ll_large<NT, GEN><<<grid, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -806,6 +902,10 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
     if (kind == 2) return 0;
     if (kind == 1) return sizeof(float) * (size_t)mixed_floats(nmax);
     if (kind == 3) return sizeof(float) * (size_t)mixed_floats(nmax) * (size_t)(threads / 32);
+    if (kind == 4) {  // one region per warp, each a multiple of 16 bytes
+        const size_t region = (R * (R + 1) / 2 + R + (size_t)d * nmax + 1) & ~(size_t)1;
+        return sizeof(double) * region * (size_t)(threads / 32);
+    }
     size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
     return (bytes + 15) & ~(size_t)15;
 }
@@ -891,6 +991,8 @@ int bv_occupancy(int kind, int threads, size_t smem) {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT, false>, NT, smem); \
             else if (kind == 3)                                                               \
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed_w<NT, false>, NT, smem); \
+            else if (kind == 4)                                                               \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64_w<NT, false>, NT, smem); \
             else                                                                              \
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_large<NT, false>, NT, 0);    \
         }                                                                                     \
