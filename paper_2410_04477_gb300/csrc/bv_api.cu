@@ -884,12 +884,17 @@ static int autotune(bv_ctx* c, int prec) {
         // candidates: CTA per block with 1 panel warp + 2/4/8/16 update warps; for small
         // blocks also a warp per block with 2/4/8 warps per CTA (mixed up to N = 128,
         // FP64 up to N = 64)
+        // BV_KERNEL_FORM=cta or =warp restricts the choice to one form where both exist
+        // (tests use it to check each kernel against the oracle)
+        const char* form = getenv("BV_KERNEL_FORM");
+        const bool only_cta = form && strcmp(form, "cta") == 0;
+        const bool only_warp = form && strcmp(form, "warp") == 0;
         std::vector<std::pair<int, int>> cands;
-        for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
-        if (bp.kind == 1 && bp.nmax <= 128)
-            for (int t : {64, 128, 256}) cands.push_back({3, t});
-        if (bp.kind == 0 && bp.nmax <= 64)
-            for (int t : {64, 128, 256}) cands.push_back({4, t});
+        const bool warp_ok = (bp.kind == 1 && bp.nmax <= 128) || (bp.kind == 0 && bp.nmax <= 64);
+        if (!(only_warp && warp_ok))
+            for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
+        if (!only_cta && warp_ok)
+            for (int t : {64, 128, 256}) cands.push_back({bp.kind == 1 ? 3 : 4, t});
         int best_k = bp.kind, best_t = bp.threads;
         float best_ms = 1e30f;
         for (auto kt : cands) {
