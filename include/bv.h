@@ -258,7 +258,13 @@ int bv_loglik_noalloc(const bv_theta* theta, const double* d_locs, const double*
                       double* d_out_per_block, void* cuda_stream);
 
 /* Run the launch-shape autotuner for `precision` now (otherwise it runs on first use).
- * Times each candidate shape of every size bin on the current structure. */
+ * Times each candidate of every size bin on the current structure and the current
+ * parameters: one CTA per block with 96, 160, 288 or 544 threads, and for small blocks
+ * (FP64 N <= 64, mixed N <= 128) one warp per block with 2, 4 or 8 warps per CTA.  The
+ * environment variable BV_KERNEL_FORM=cta or =warp restricts the candidates to one form.
+ * Every form does the same per-block arithmetic, so the choice changes speed only (the
+ * FP64 result is bit-identical across re-tuned plans).  Errors: BV_EINVAL (precision),
+ * BV_ESTATE (no neighbours selected yet), BV_ECUDA. */
 int bv_autotune(bv_ctx* ctx, int32_t precision);
 
 /* Launch plan of one evaluation at `precision` (built on demand): number of kernel
