@@ -135,6 +135,7 @@ int bv_refresh_layout_y(bv_ctx* c) { return refresh_layout_y(c); }
 // kernel reads the same values, only from other addresses.
 static int build_layout(bv_ctx* c) {
     if (c->have_layout) return BV_OK;
+    free_layout(c);  // whatever an earlier attempt that failed part-way allocated
     const int64_t n = c->n_tot;
     const int d = c->d;
     std::vector<int32_t> inv;
@@ -144,9 +145,15 @@ static int build_layout(bv_ctx* c) {
         bv_hilbert_order(c->h_locs.data(), c->pt_off[ds], c->pt_off[ds + 1] - c->pt_off[ds], d, o);
         inv.insert(inv.end(), o.begin(), o.end());
     }
-    int32_t* d_pos = nullptr;
+    struct DevBuf {  // scratch freed on every return path
+        int32_t* p = nullptr;
+        ~DevBuf() {
+            if (p) cudaFree(p);
+        }
+    } pos;
     BV_CUDA(cudaMalloc(&c->d_inv, sizeof(int32_t) * n));
-    BV_CUDA(cudaMalloc(&d_pos, sizeof(int32_t) * n));
+    BV_CUDA(cudaMalloc(&pos.p, sizeof(int32_t) * n));
+    int32_t* d_pos = pos.p;
     BV_CUDA(cudaMalloc(&c->d_locs_int, sizeof(double) * n * d));
     BV_CUDA(cudaMalloc(&c->d_y_int, sizeof(double) * n));
     BV_CUDA(cudaMalloc(&c->d_pidx_int, sizeof(int32_t) * n));
@@ -162,7 +169,6 @@ static int build_layout(bv_ctx* c) {
                                                                                      d_pos, c->d_nidx_int);
     BV_CUDA(cudaGetLastError());
     BV_CUDA(cudaStreamSynchronize(c->stream));
-    cudaFree(d_pos);
     c->have_layout = true;
     return refresh_layout_y(c);
 }
@@ -853,8 +859,8 @@ static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     cudaEventCreate(&e1);
     const LLArgs a = make_args(c);
     float best = 1e30f;
-    if (c->cur_gen && bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream) != cudaSuccess) return best;
-    for (int r = 0; r < reps + 1; ++r) {
+    const bool ok = !c->cur_gen || bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream) == cudaSuccess;
+    for (int r = 0; ok && r < reps + 1; ++r) {
         if (bv_launch_eval_reset(c->d_fail, c->d_wctr, 2 * BV_WCTR_PER_PREC, c->stream) != cudaSuccess) break;
         cudaEventRecord(e0, c->stream);
         cudaError_t e = bv_launch_bin(bp, a, c->stream);
