@@ -54,7 +54,9 @@ typedef enum bv_status {
     BV_ENOMEM = 2,    /* device or host allocation failed                                 */
     BV_ECUDA = 3,     /* a CUDA runtime call failed (bv_last_cuda_error has the text)     */
     BV_ENOTPD = 4,    /* a block's covariance was not positive definite; ell = -inf       */
-    BV_ETIMEOUT = 5,  /* a bounded device wait gave up                                    */
+    BV_ETIMEOUT = 5,  /* reserved: no entry point waits on the device with a time limit,
+                         so none returns it; the value stays assigned so that codes keep
+                         their meaning                                                    */
     BV_ESTATE = 6,    /* call out of order (e.g. no data, no blocks, no neighbours yet)   */
     BV_EINTERNAL = 7  /* internal consistency check failed                                */
 } bv_status;
@@ -90,7 +92,11 @@ int bv_set_datasets(bv_ctx* ctx, int32_t ndatasets, const int64_t* n_per,
                     const double* locs, const double* y, int32_t d);
 
 /* Replace the observations (all datasets, concatenated).  `y` is a host pointer, or a
- * device pointer when y_on_device != 0 (then the copy is asynchronous on the stream). */
+ * device pointer when y_on_device != 0 (then the copy is asynchronous on the stream).
+ * A host y with a NaN or infinite entry returns BV_EINVAL and leaves the observations
+ * unchanged (bv_set_data / bv_set_datasets check y and the locations the same way); a
+ * device y is not inspected, and a non-finite entry there makes the evaluation's ell
+ * -inf with BV_ENOTPD. */
 int bv_set_observations(bv_ctx* ctx, const double* y, int32_t y_on_device);
 
 /* ---- preprocessing (one-time; excluded from the timed evaluation, Sec. 3.1) ------ */
@@ -244,8 +250,13 @@ int bv_sync(bv_ctx* ctx, int64_t* failed_block);
  *   bv_select_neighbors; d_out_loglik[1] receives ell; d_out_per_block[bc] (may be NULL)
  *   the per-block terms.  cuda_stream: the stream to use (NULL = legacy default stream).
  * Limits: bc <= BV_NOALLOC_MAX_BLOCKS, and every block's m_i + b_i at most 235 (d = 1),
- * 234 (d = 2) or 233 (d = 3); larger sizes return BV_EINVAL before any kernel reads the
- * structure.  Returns after the stream drains; BV_ENOTPD as bv_loglik.
+ * 234 (d = 2) or 233 (d = 3).  A first small kernel reads the two pointer arrays to find
+ * the largest m_i + b_i and to check them (both start at 0, neither decreases,
+ * d_block_ptr[bc] <= n); a size beyond the limit or a malformed structure returns
+ * BV_EINVAL before the likelihood kernel runs.  A point or neighbour index outside
+ * [0, n) is recorded by the likelihood kernel without being read and also returns
+ * BV_EINVAL.  Every call waits for its stream to drain (it reads these checks and the
+ * failure word back to the host) and returns BV_ENOTPD as bv_loglik does.
  * The first call made with a device current looks up the array's device address for
  * that device: make that first call outside any stream capture.  Every call reuses the
  * same array (its status words are reset at the start of each call, its per-block

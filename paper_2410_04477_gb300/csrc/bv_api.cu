@@ -34,11 +34,20 @@ extern "C" const char* bv_strerror(int s) {
         case BV_ENOMEM: return "out of memory";
         case BV_ECUDA: return "CUDA error";
         case BV_ENOTPD: return "covariance matrix not positive definite";
-        case BV_ETIMEOUT: return "device wait timed out";
+        case BV_ETIMEOUT: return "device wait timed out (reserved: no call returns it)";
         case BV_ESTATE: return "call out of order (missing data, blocks or neighbours)";
         case BV_EINTERNAL: return "internal consistency check failed";
         default: return "unknown status";
     }
+}
+
+cudaError_t bv_plan_malloc(void** p, size_t bytes) {
+    const char* f = getenv("BV_FAULT_ALLOC");
+    if (f && *f && strcmp(f, "0") != 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 template <class T>
@@ -151,14 +160,14 @@ static int build_layout(bv_ctx* c) {
             if (p) cudaFree(p);
         }
     } pos;
-    BV_CUDA(cudaMalloc(&c->d_inv, sizeof(int32_t) * n));
-    BV_CUDA(cudaMalloc(&pos.p, sizeof(int32_t) * n));
+    BV_CUDA(bv_plan_malloc(&c->d_inv, sizeof(int32_t) * n));
+    BV_CUDA(bv_plan_malloc(&pos.p, sizeof(int32_t) * n));
     int32_t* d_pos = pos.p;
-    BV_CUDA(cudaMalloc(&c->d_locs_int, sizeof(double) * n * d));
-    BV_CUDA(cudaMalloc(&c->d_y_int, sizeof(double) * n));
-    BV_CUDA(cudaMalloc(&c->d_pidx_int, sizeof(int32_t) * n));
+    BV_CUDA(bv_plan_malloc(&c->d_locs_int, sizeof(double) * n * d));
+    BV_CUDA(bv_plan_malloc(&c->d_y_int, sizeof(double) * n));
+    BV_CUDA(bv_plan_malloc(&c->d_pidx_int, sizeof(int32_t) * n));
     const int64_t nn = std::max<int64_t>(c->h_nptr.back(), 1);
-    BV_CUDA(cudaMalloc(&c->d_nidx_int, sizeof(int32_t) * nn));
+    BV_CUDA(bv_plan_malloc(&c->d_nidx_int, sizeof(int32_t) * nn));
     BV_CUDA(cudaMemcpyAsync(c->d_inv, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
     const unsigned g = (unsigned)((n + 255) / 256);
     k_inverse_perm<<<g, 256, 0, c->stream>>>(c->d_inv, n, d_pos);
@@ -311,6 +320,8 @@ extern "C" int bv_set_observations(bv_ctx* c, const double* y, int32_t on_device
     if (on_device) {
         BV_CUDA(cudaMemcpyAsync(c->d_y, y, sizeof(double) * c->n_tot, cudaMemcpyDeviceToDevice, c->stream));
     } else {
+        for (int64_t i = 0; i < c->n_tot; ++i)
+            if (!std::isfinite(y[i])) return BV_EINVAL;
         BV_CUDA(cudaMemcpyAsync(c->d_y, y, sizeof(double) * c->n_tot, cudaMemcpyHostToDevice, c->stream));
         BV_CUDA(cudaStreamSynchronize(c->stream));
     }
@@ -802,9 +813,11 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
         int slots = (int)std::min<int64_t>(nlarge, 2 * (int64_t)c->num_sms);
         // keep the workspace within a few GB
         while (slots > 1 && (double)slots * stride * 8.0 > 8e9) --slots;
-        if (stride > c->ws_stride || slots > c->ws_slots) {
+        if (!c->d_ws || stride > c->ws_stride || slots > c->ws_slots) {
             dfree(c->d_ws);
-            BV_CUDA(cudaMalloc(&c->d_ws, sizeof(double) * stride * slots));
+            c->ws_stride = 0;
+            c->ws_slots = 0;
+            BV_CUDA(bv_plan_malloc(&c->d_ws, sizeof(double) * stride * slots));
             c->ws_stride = stride;
             c->ws_slots = slots;
         }
@@ -819,8 +832,9 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
         while (slots > 1 && (double)slots * stride * 8.0 > 2e9) --slots;
         dfree(c->d_fb_ws);
         dfree(c->d_fb);
-        BV_CUDA(cudaMalloc(&c->d_fb_ws, sizeof(double) * stride * slots));
-        BV_CUDA(cudaMalloc(&c->d_fb, sizeof(int) * (c->nblk + 1)));
+        c->fb_slots = 0;
+        BV_CUDA(bv_plan_malloc(&c->d_fb_ws, sizeof(double) * stride * slots));
+        BV_CUDA(bv_plan_malloc(&c->d_fb, sizeof(int) * (c->nblk + 1)));
         BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));
         c->fb_stride = stride;
         c->fb_slots = slots;
@@ -837,10 +851,11 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
         bp.nwork = (int32_t)L.size();
         bp.h_work = L;
         bp.d_work = nullptr;
-        BV_CUDA(cudaMalloc(&bp.d_work, sizeof(int32_t) * L.size()));
-        BV_CUDA(cudaMemcpyAsync(bp.d_work, L.data(), sizeof(int32_t) * L.size(), cudaMemcpyHostToDevice, c->stream));
-        BV_TRY(set_grid(c, bp));
-        c->plan[prec].push_back(bp);
+        BV_CUDA(bv_plan_malloc(&bp.d_work, sizeof(int32_t) * L.size()));
+        c->plan[prec].push_back(bp);  // owned by the plan from here on (freed with it on any failure)
+        BinPlan& pb = c->plan[prec].back();
+        BV_CUDA(cudaMemcpyAsync(pb.d_work, L.data(), sizeof(int32_t) * L.size(), cudaMemcpyHostToDevice, c->stream));
+        BV_TRY(set_grid(c, pb));
     }
     // largest bins first so the long blocks start early
     std::stable_sort(c->plan[prec].begin(), c->plan[prec].end(),

@@ -23,6 +23,17 @@ void bv_record_cuda_error(cudaError_t e, const char* expr, const char* file, int
         }                                                                    \
     } while (0)
 
+// Device allocation of an evaluation's buffers (the plan, the evaluation layout).  Test
+// support: while the environment variable BV_FAULT_ALLOC is set to a non-zero value it
+// fails as the runtime does when device memory is exhausted (cudaErrorMemoryAllocation)
+// without calling the runtime, so that a caller can exercise the BV_ENOMEM path, and the
+// context's recovery from it, with no real exhaustion of the device.
+cudaError_t bv_plan_malloc(void** p, size_t bytes);
+template <class T>
+inline cudaError_t bv_plan_malloc(T** p, size_t bytes) {
+    return bv_plan_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
 #define BV_TRY(expr)                    \
     do {                                \
         int bv_s_ = (expr);             \

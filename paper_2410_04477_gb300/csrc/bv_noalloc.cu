@@ -8,20 +8,27 @@
 // allocation's implicit synchronisation is unacceptable.  Such a caller already holds
 // its inputs and outputs on the device; this entry point only launches kernels.
 //
-// The per-block partial results and the two status words live in one file-scope device
+// The per-block partial results and three status words live in one file-scope device
 // array (g_na_scratch, BV_NOALLOC_MAX_BLOCKS + 32 doubles, about 8 MiB), which every GPU
 // that loads the library keeps until the process exits.  Its device address is looked
 // up once per device with cudaGetSymbolAddress on the first call made with that device
 // current (host code may not use the array's name as a device pointer).
 //
 // Rules for callers:
-//   - Make the first call on each device outside any CUDA stream capture (the set-up
-//     call is not capturable).
+//   - Make the first call on each device outside any CUDA stream capture: that call looks
+//     up the array's device address.
+//   - Every call returns only after its stream has drained: it reads the largest block
+//     size and a structure check back to the host before the likelihood kernel runs, and
+//     the failure word after it.
 //   - All calls share the array: two calls whose kernels overlap on the GPU (different
 //     streams, or concurrent host threads) race on it and give wrong results.  Order
 //     them on one stream or synchronise between them.
 //   - The status words are reset at the start of every call; the per-block entries are
 //     all rewritten, so nothing from a previous call leaks into the result.
+//   - The caller's structure is checked on the device before any point is read: the
+//     pointer arrays must start at 0 and never decrease, the blocks must cover at most n
+//     points, and every point and neighbour index must lie in [0, n); a violation
+//     returns BV_EINVAL (an out-of-range index is recorded and never dereferenced).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -40,6 +47,7 @@ constexpr double kLog2PiNA = 1.8378770664093454835606594728112;
 // slots after the per-block entries
 constexpr int64_t kFailSlot = BV_NOALLOC_MAX_BLOCKS;
 constexpr int64_t kMaxNSlot = BV_NOALLOC_MAX_BLOCKS + 1;
+constexpr int64_t kBadSlot = BV_NOALLOC_MAX_BLOCKS + 2;   // nonzero: the structure is malformed
 
 static __device__ __align__(256) double g_na_scratch[BV_NOALLOC_MAX_BLOCKS + 32];
 
@@ -67,13 +75,24 @@ __device__ __forceinline__ double na_matern(const DevTheta& th, double x) {
 __global__ void k_na_init(double* s) {
     reinterpret_cast<unsigned long long*>(s)[kFailSlot] = ~0ull;
     reinterpret_cast<unsigned long long*>(s)[kMaxNSlot] = 0ull;
+    reinterpret_cast<unsigned long long*>(s)[kBadSlot] = 0ull;
 }
 
-__global__ void k_na_maxn(const int64_t* bptr, const int64_t* nptr, int64_t bc, double* s) {
+// Largest augmented size m_i + b_i, and the structure check of the pointer arrays
+// (both start at 0, neither decreases, the blocks cover at most n points).
+__global__ void k_na_maxn(const int64_t* bptr, const int64_t* nptr, int64_t bc, int64_t n, double* s) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= bc) return;
-    const int64_t N = (bptr[i + 1] - bptr[i]) + (nptr[i + 1] - nptr[i]);
-    atomicMax(reinterpret_cast<unsigned long long*>(s) + kMaxNSlot, (unsigned long long)(N > 0 ? N : 0));
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(s);
+    const int64_t b = bptr[i + 1] - bptr[i], m = nptr[i + 1] - nptr[i];
+    bool bad = b < 0 || m < 0;
+    if (i == 0) bad = bad || bptr[0] != 0 || nptr[0] != 0;
+    if (i == bc - 1) bad = bad || bptr[bc] > n;
+    if (bad) {
+        atomicOr(w + kBadSlot, 1ull);
+        return;
+    }
+    atomicMax(w + kMaxNSlot, (unsigned long long)(b + m));
 }
 
 // Same fused algorithm as the library's FP64 shared-memory kernel (augmented Cholesky
@@ -100,6 +119,12 @@ __global__ void __launch_bounds__(NT) k_na_ll(const double* __restrict__ locs, i
         double* px = col1 + R;
         for (int t = tid; t < N; t += NT) {
             const int g = t < m ? nidx[n0 + t] : pidx[b0 + (t - m)];
+            if (g < 0 || (int64_t)g >= n_tot) {  // recorded, never dereferenced
+                atomicOr(reinterpret_cast<unsigned long long*>(s) + kBadSlot, 1ull);
+                for (int k = 0; k < d; ++k) px[k * N + t] = 0.0;
+                A[na_pk(N, t)] = 0.0;
+                continue;
+            }
             for (int k = 0; k < d; ++k) px[k * N + t] = locs[(int64_t)k * n_tot + g];
             A[na_pk(N, t)] = y[g];
         }
@@ -259,13 +284,14 @@ extern "C" int bv_loglik_noalloc(const bv_theta* theta, const double* d_locs, co
     BV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     k_na_init<<<1, 1, 0, st>>>(s);
     BV_CUDA(cudaGetLastError());
-    k_na_maxn<<<(unsigned)((bc + 255) / 256), 256, 0, st>>>(d_block_ptr, d_nn_ptr, bc, s);
+    k_na_maxn<<<(unsigned)((bc + 255) / 256), 256, 0, st>>>(d_block_ptr, d_nn_ptr, bc, n, s);
     BV_CUDA(cudaGetLastError());
-    unsigned long long maxn = 0;
-    BV_CUDA(cudaMemcpyAsync(&maxn, reinterpret_cast<unsigned long long*>(s) + kMaxNSlot, sizeof(maxn),
+    unsigned long long chk[2] = {0, 0};  // largest m_i + b_i, structure flag
+    BV_CUDA(cudaMemcpyAsync(chk, reinterpret_cast<unsigned long long*>(s) + kMaxNSlot, sizeof(chk),
                             cudaMemcpyDeviceToHost, st));
     BV_CUDA(cudaStreamSynchronize(st));
-    if (maxn == 0 || maxn > (unsigned long long)na_max_n(d)) return BV_EINVAL;
+    const unsigned long long maxn = chk[0];
+    if (chk[1] != 0 || maxn == 0 || maxn > (unsigned long long)na_max_n(d)) return BV_EINVAL;
     const size_t smem = na_smem((int)maxn, d);
     BV_CUDA(cudaFuncSetAttribute(k_na_ll<kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -279,9 +305,10 @@ extern "C" int bv_loglik_noalloc(const bv_theta* theta, const double* d_locs, co
     BV_CUDA(cudaGetLastError());
     if (d_out_per_block)
         BV_CUDA(cudaMemcpyAsync(d_out_per_block, s, sizeof(double) * bc, cudaMemcpyDeviceToDevice, st));
-    unsigned long long fail = 0;
-    BV_CUDA(cudaMemcpyAsync(&fail, reinterpret_cast<unsigned long long*>(s) + kFailSlot, sizeof(fail),
+    unsigned long long fin[3] = {0, 0, 0};  // failure word, largest size, structure flag
+    BV_CUDA(cudaMemcpyAsync(fin, reinterpret_cast<unsigned long long*>(s) + kFailSlot, sizeof(fin),
                             cudaMemcpyDeviceToHost, st));
     BV_CUDA(cudaStreamSynchronize(st));
-    return fail != ~0ull ? BV_ENOTPD : BV_OK;
+    if (fin[2] != 0) return BV_EINVAL;  // a point or neighbour index outside [0, n)
+    return fin[0] != ~0ull ? BV_ENOTPD : BV_OK;
 }

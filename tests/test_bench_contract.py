@@ -22,9 +22,12 @@ def _reference_line(*extra):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("workload,unit", [("c2_m60", "evals/s"), ("pred_20k", "predictions/s")])
+@pytest.mark.parametrize("workload,unit", [("c3", "evals/s"), ("c2_m60", "evals/s"), ("c5_m60", "evals/s"),
+                                           ("pred_20k", "predictions/s")])
 def test_reference_arm_json(workload, unit):
     d = _reference_line("--workload", workload)
+    if workload == "c3":  # the default workload is the largest single-GPU configuration
+        assert _reference_line()["config"] == d["config"]
     assert d["impl"] == "reference"
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):

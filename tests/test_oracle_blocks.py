@@ -1,5 +1,7 @@
 """Pins for the oracle's preprocessing: K-means blocks, the block order and the block
 nearest-neighbour sets (Sec. 2.1-2.2, Algorithm 1)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -58,6 +60,82 @@ def test_kmeanspp_first_centre_and_distinct_seeds():
     _, c = oracle.kmeans(locs, 50, seed=77, iters=0)
     # k-means++ never picks an already chosen point while unchosen points have D2 > 0
     assert len({tuple(v) for v in c}) == 50
+
+
+def _ceil_log2(v):
+    e = 0
+    while (1 << e) < v:
+        e += 1
+    return e
+
+
+def kmeanspp_picks(locs, k, seed):
+    """The k-means++ seeding written out from its stated rule, in plain Python integers:
+    the first centre is point floor(r_0 n / 2^64); centre t is drawn with probability
+    proportional to D^2 on integer weights w_j = floor(D2_j 2^s), with s the largest
+    exponent that keeps n (d2max 2^s) below 2^61 (d2max: squared diagonal of the bounding
+    box); target = floor(r_t W / 2^64); the pick is the first j whose inclusive prefix sum
+    of w exceeds the target.  r_t = SplitMix64 draw t of the stream seed ^ "kmeans++"."""
+    n, d = locs.shape
+    lo, hi = locs.min(axis=0), locs.max(axis=0)
+    d2max = 0.0
+    for a in range(d):
+        d2max = d2max + (hi[a] - lo[a]) * (hi[a] - lo[a])
+    s = 61 - _ceil_log2(n) - (math.frexp(d2max)[1] + 1)
+    stream = seed ^ 0x6B6D65616E732B2B
+    picks = [(oracle.splitmix64(stream, 0) * n) >> 64]
+    D2 = _d2(locs, locs[picks[0]][None, :])
+    for t in range(1, k):
+        w = [int(math.ldexp(float(v), s)) for v in D2]
+        W = sum(w)
+        r = oracle.splitmix64(stream, t)
+        if W == 0:
+            pick = (r * n) >> 64
+        else:
+            target, pre, pick = (r * W) >> 64, 0, n - 1
+            for j, wj in enumerate(w):
+                pre += wj
+                if pre > target:
+                    pick = j
+                    break
+        picks.append(pick)
+        D2 = np.minimum(D2, _d2(locs, locs[pick][None, :]))
+    return picks
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(400, 2, 10, 3), (250, 3, 8, 41), (1000, 2, 6, 12345)])
+def test_kmeanspp_picks_follow_the_d2_rule(n, d, k, seed):
+    locs = synth.locs_uniform(n, d, seed=seed + 1)
+    _, cent = oracle.kmeans(locs, k, seed=seed, iters=0)
+    np.testing.assert_array_equal(cent, locs[kmeanspp_picks(locs, k, seed)])
+
+
+def test_kmeanspp_second_centre_is_drawn_proportional_to_d2():
+    # the law itself, independent of the integer weights: over many seeds the second
+    # centre is point j with probability D2_j / sum D2, D2 to the first centre
+    n, trials = 12, 6000
+    locs = synth.locs_uniform(n, 2, seed=5)
+    counts = np.zeros((n, n))
+    for seed in range(trials):
+        _, c = oracle.kmeans(locs, 2, seed=seed, iters=0)
+        i = int(np.flatnonzero((locs == c[0]).all(axis=1))[0])
+        j = int(np.flatnonzero((locs == c[1]).all(axis=1))[0])
+        counts[i, j] += 1
+    chi2, dof = 0.0, 0
+    for i in range(n):
+        tot = counts[i].sum()
+        if tot < 200:
+            continue
+        p = _d2(locs, locs[i][None, :])
+        p = p / p.sum()
+        e = tot * p
+        keep = e > 0
+        chi2 += (((counts[i] - e)[keep]) ** 2 / e[keep]).sum()
+        dof += int(keep.sum()) - 1
+        assert counts[i, i] == 0  # a chosen point has D2 = 0
+    assert dof > 20
+    # chi-square with dof degrees of freedom: mean dof, sd sqrt(2 dof); allow 5 sd
+    assert chi2 < dof + 5 * math.sqrt(2 * dof), (chi2, dof)
 
 
 @pytest.mark.parametrize("n,d,bc", [(2000, 2, 200), (900, 3, 90)])

@@ -44,14 +44,23 @@ MUTANTS = {
     "maxmin ties to the highest position": ("if (!used[p] && dmin[p] > far)", "if (!used[p] && dmin[p] >= far)"),
     "KD-tree split at the wrong axis": ("const int ax = depth % d;", "const int ax = (depth + 1) % d;"),
     "Morton with the axes' bits swapped": ("<< (b * d + a);", "<< (b * d + (d - 1 - a));"),
+    "k-means++ drawn proportional to D": [("W += (uint64_t)ldexp(D2[i], s);", "W += (uint64_t)ldexp(sqrt(D2[i]), s);"),
+                                          ("pre += (uint64_t)ldexp(D2[i], s);",
+                                           "pre += (uint64_t)ldexp(sqrt(D2[i]), s);")],
 }
+# Not planted: comparing the k-means++ prefix sum with >= instead of > changes a pick only
+# when the target equals a prefix sum exactly, which has probability about n / W with the
+# total weight W near 2^58 -- no input distinguishes the two rules.
 
 
-def _build(tmp_path, old, new):
+def _build(tmp_path, edits):
+    """Compile the oracle with the planted mistake: one (old, new) edit or a list of them."""
     src = open(SRC).read()
-    assert src.count(old) >= 1, old
+    for old, new in ([edits] if isinstance(edits, tuple) else edits):
+        assert src.count(old) >= 1, old
+        src = src.replace(old, new, 1)
     path = tmp_path / "mut.c"
-    path.write_text(src.replace(old, new, 1))
+    path.write_text(src)
     so = str(tmp_path / "libmut.so")
     subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
                     "-o", so, str(path), "-lm"], check=True)
@@ -191,10 +200,17 @@ def _pin_orders():
     return bool(np.all(first < 4) and np.all(second[:, 0] >= 4) and np.all(second[:, 1] < 4))
 
 
+def _pin_kmeanspp():
+    from tests.test_oracle_blocks import kmeanspp_picks
+    locs = synth.locs_uniform(300, 2, 4)
+    _, cent = oracle.kmeans(locs, 8, seed=21, iters=0)
+    return bool((cent == locs[kmeanspp_picks(locs, 8, 21)]).all())
+
+
 PINS = {"hilbert adjacency": _pin_hilbert, "orderings": _pin_orders, "kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
         "conditional-simulation normals": _pin_csim_normal, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
-        "K-means exact tie": _pin_kmeans_tie}
+        "K-means exact tie": _pin_kmeans_tie, "k-means++ seeding rule": _pin_kmeanspp}
 
 
 def _pins():
@@ -215,7 +231,6 @@ def test_real_oracle_passes_the_reduced_pins():
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(tmp_path, name):
-    old, new = MUTANTS[name]
-    with oracle.use_library(_build(tmp_path, old, new)):
+    with oracle.use_library(_build(tmp_path, MUTANTS[name])):
         res = _pins()
     assert not all(res.values()), f"mistake '{name}' passed every pin: {res}"
