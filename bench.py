@@ -830,6 +830,7 @@ def main():
         n2 = min(args.steps, 30) if other == bv.BV_MIXED or nd > 1 else min(args.steps, 5)
         ms2 = time_device(torch, bv, ctx, stream, thetas, other, 3, n2, flush)
         llm = ctx.loglik_multi(base, bv.BV_MIXED)
+        nb64, ntouched, est = ctx.mixed_check_info()
         rel = np.abs(llm - ll64) / np.abs(ll64)
         extras["other_precision"] = {
             "precision": "mixed" if other == bv.BV_MIXED else "fp64",
@@ -837,7 +838,23 @@ def main():
             "achieved_tflops": info["flops"] / (statistics.mean(ms2) / 1e3) / 1e12,
             "ell_fp64_at_truth": float(ll64.sum()), "ell_mixed_at_truth": float(llm.sum()),
             "rel_err_mixed_vs_fp64": float(abs(llm.sum() - ll64.sum()) / abs(ll64.sum())),
-            "max_rel_err_per_dataset": float(rel.max()), "abs_err": float(abs(llm.sum() - ll64.sum()))}
+            "max_rel_err_per_dataset": float(rel.max()), "abs_err": float(abs(llm.sum() - ll64.sum())),
+            "abs_err_per_dataset_max": float(np.abs(llm - ll64).max()),
+            "check": {"bound": 1e-6, "blocks_fp64": int(nb64), "blocks": int(ctx.sizes()[0]),
+                      "datasets_with_blocks_recomputed": int(ntouched), "datasets": int(nd),
+                      "est_rel_err_max": float(est.max())}}
+        if other == bv.BV_MIXED:
+            # the same without the check: FP32 throughout (bv_set_mixed_tolerance(0))
+            ctx.set_mixed_tolerance(0.0)
+            ms3 = time_device(torch, bv, ctx, stream, thetas, other, 3, n2, flush)
+            llu = ctx.loglik_multi(base, bv.BV_MIXED)
+            ctx.set_mixed_tolerance(1e-6)
+            relu = np.abs(llu - ll64) / np.abs(ll64)
+            extras["other_precision"]["unchecked_fp32"] = {
+                "evals_per_s": len(ms3) / (sum(ms3) / 1e3),
+                "achieved_tflops": info["flops"] / (statistics.mean(ms3) / 1e3) / 1e12,
+                "rel_err_vs_fp64": float(abs(llu.sum() - ll64.sum()) / abs(ll64.sum())),
+                "max_rel_err_per_dataset": float(relu.max()), "abs_err": float(abs(llu.sum() - ll64.sum()))}
         log(f"extras: {extras['other_precision']}")
         if args.workload == "c4_mle":
             extras["mle"] = run_mle(bv, ctx, w, log)

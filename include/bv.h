@@ -64,7 +64,10 @@ typedef enum bv_status {
 typedef enum bv_precision {
     BV_FP64 = 0,  /* every step in FP64                                                    */
     BV_MIXED = 1  /* covariance generation, triangular solves and Schur-complement updates
-                     in FP32; pivots, log-determinant and quadratic form in FP64           */
+                     in FP32; log-determinant and quadratic form accumulated in FP64; an
+                     FP64 check keeps every dataset's relative error within a stated
+                     bound by recomputing its worst-conditioned blocks in FP64
+                     (bv_mixed_check_info, bv_set_mixed_tolerance)                       */
 } bv_precision;
 
 /* ---- context -------------------------------------------------------------------- */
@@ -228,6 +231,39 @@ int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
  * a block that also fails in FP64 makes ell -inf. */
 int bv_mixed_fallbacks(bv_ctx* ctx, int64_t* count);
 
+/* The error check of the last mixed-precision evaluation.  The FP32 error of a block's
+ * term is modelled as r_i eps B_i: eps = 2^-24, B_i the block's conditioning indicator
+ * (bv_mixed_block_indicator) and r_i independent, zero-mean, of a scale rho that depends
+ * on the dataset.  Every dataset recomputes a fixed sample of its blocks in FP64 (all
+ * blocks of a dataset with fewer than 64; else max(64, ceil(B/256)) of its B blocks at
+ * evenly spaced positions of the random block order); the sample gives rho (the RMS of
+ * delta_i / (eps B_i), delta_i the FP32 minus FP64 term), a test for a systematic bias
+ * (|mean| over 4 standard errors: the whole dataset is recomputed in FP64) and the
+ * log-likelihood estimate L (B times the mean FP64 term).  The bound on the dataset's
+ * relative error is 3 x 1.2 rho eps sqrt(sum B_i^2) / |L| over the blocks still in FP32
+ * (three standard deviations, a 20% margin for the sampled rho); while it exceeds the
+ * tolerance (bv_set_mixed_tolerance, default 1e-6) the blocks with the largest B_i are
+ * recomputed in FP64 in the same evaluation.  The sampled blocks always keep their FP64
+ * terms.  Outputs: *blocks_fp64 = blocks whose terms came from FP64 (sampled and
+ * recomputed; not counting the FP32-breakdown fallback of bv_mixed_fallbacks);
+ * *datasets_touched (may be NULL) = datasets with any block recomputed beyond the
+ * sample; est_rel[ndatasets] (may be NULL) = each dataset's final bound (0 when every
+ * block was sampled, +inf when a sampled block failed in FP64 or a bias was found).
+ * Synchronous.  BV_ESTATE before the first mixed evaluation; all zero with the check off. */
+int bv_mixed_check_info(bv_ctx* ctx, int64_t* blocks_fp64, int32_t* datasets_touched, double* est_rel);
+
+/* The bound the mixed-precision check enforces (default 1e-6); 0 switches the check off
+ * (FP32 throughout, only blocks whose FP32 factorisation breaks down are recomputed in
+ * FP64).  Takes effect at the next evaluation.  BV_EINVAL unless 0 <= tol < 1. */
+int bv_set_mixed_tolerance(bv_ctx* ctx, double tol);
+
+/* Per-block conditioning indicator of the last mixed-precision evaluation (nblocks
+ * floats): the sum over the block's N = m_i + b_i pivots of its FP32 factorisation of
+ * (sigma^2 + tau^2) / pivot, i.e. of each point's variance over its conditional variance
+ * given the points before it.  The FP32 rounding error of the block's term grows with
+ * it.  Synchronous.  BV_ESTATE before the first mixed evaluation. */
+int bv_mixed_block_indicator(bv_ctx* ctx, float* out);
+
 /* First failing block (not positive definite) of the last synchronous evaluation, or -1. */
 int bv_last_error_block(bv_ctx* ctx, int64_t* block);
 
@@ -291,6 +327,12 @@ int bv_plan_info(bv_ctx* ctx, int32_t precision, int32_t* launches_per_eval, int
  * closed forms, any other nu the library's K_nu (Temme's series / continued fraction) or,
  * with tabulated != 0, the per-evaluation octave table the log-likelihood kernels use. */
 int bv_matern_check(double nu, int32_t tabulated, int64_t n, const double* x, double* out);
+
+/* Diagnostic: the tensor-core tile update of the mixed-precision kernel for large blocks,
+ * out = C - XI XJ^T for 16 x 16 FP32 tiles (host arrays, row-major): every operand split
+ * exactly into three BF16 parts, the six products of combined order <= 2 accumulated in
+ * FP32 by mma.sync m16n8k16 (one warp on the GPU). */
+int bv_tc_update_check(const float* C, const float* XI, const float* XJ, float* out);
 
 /* Diagnostic: the library's device FP64 exponential e^{-x} (x >= 0; Tang's table-driven
  * method, used for the Matern kernel in the FP64 path) evaluated on the GPU for host

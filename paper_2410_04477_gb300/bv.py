@@ -112,12 +112,16 @@ _SIGS = {
     "bv_sync": (_int, [_vp, _P(_i64)]),
     "bv_last_error_block": (_int, [_vp, _P(_i64)]),
     "bv_mixed_fallbacks": (_int, [_vp, _P(_i64)]),
+    "bv_mixed_check_info": (_int, [_vp, _P(_i64), _P(_i32), _P(_d)]),
+    "bv_set_mixed_tolerance": (_int, [_vp, _d]),
+    "bv_mixed_block_indicator": (_int, [_vp, _P(_f)]),
     "bv_loglik_noalloc": (_int, [_P(bv_theta), _vp, _vp, _i64, _i32, _i64, _vp, _vp, _vp, _vp,
                                  _vp, _vp, _vp]),
     "bv_autotune": (_int, [_vp, _i32]),
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
     "bv_matern_check": (_int, [_d, _i32, _i64, _P(_d), _P(_d)]),
     "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
+    "bv_tc_update_check": (_int, [_P(_f), _P(_f), _P(_f), _P(_f)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
                       _P(bv_theta), _P(_d), _P(_i32)]),
@@ -202,6 +206,14 @@ def matern_check(nu, x, tabulated=False):
     out = np.empty_like(xv)
     _check(_lib.bv_matern_check(float(nu), 1 if tabulated else 0, xv.size, _p(xv, _d), _p(out, _d)),
            "bv_matern_check")
+    return out
+
+
+def tc_update_check(C, XI, XJ):
+    """C - XI XJ^T (16 x 16 FP32 tiles) by the mixed kernel's tensor-core tile update."""
+    a = [_arr(v, np.float32).reshape(16, 16) for v in (C, XI, XJ)]
+    out = np.empty((16, 16), np.float32)
+    _check(_lib.bv_tc_update_check(_p(a[0], _f), _p(a[1], _f), _p(a[2], _f), _p(out, _f)), "bv_tc_update_check")
     return out
 
 
@@ -441,6 +453,25 @@ class Context:
         _check(_lib.bv_kl_divergence(self.h, ctypes.byref(th), precision, ctypes.byref(k), ctypes.byref(a),
                                      ctypes.byref(b)), "bv_kl_divergence")
         return k.value, a.value, b.value
+
+    def mixed_check_info(self):
+        """(blocks whose terms came from FP64, datasets with blocks recomputed beyond the
+        sample, per-dataset bound on the relative error) of the last mixed evaluation."""
+        nb = ctypes.c_int64(0)
+        nd = ctypes.c_int32(0)
+        est = np.zeros(max(self.ndata, 1), np.float64)
+        _check(_lib.bv_mixed_check_info(self.h, ctypes.byref(nb), ctypes.byref(nd), _p(est, _d)),
+               "bv_mixed_check_info")
+        return nb.value, nd.value, est[:self.ndata]
+
+    def set_mixed_tolerance(self, tol: float):
+        _check(_lib.bv_set_mixed_tolerance(self.h, float(tol)), "bv_set_mixed_tolerance")
+
+    def mixed_block_indicator(self):
+        nb, _ = self.sizes()
+        out = np.empty(nb, np.float32)
+        _check(_lib.bv_mixed_block_indicator(self.h, _p(out, _f)), "bv_mixed_block_indicator")
+        return out
 
     def mixed_fallbacks(self):
         """Blocks recomputed in FP64 in the last mixed-precision evaluation."""

@@ -56,13 +56,35 @@ static void dfree(T*& p) {
     p = nullptr;
 }
 
+static void free_check(bv_ctx* c) {
+    auto& k = c->chk;
+    for (auto& b : k.sbins) dfree(b.d_work);
+    k.sbins.clear();
+    k.rbins.clear();  // their lists live inside d_redo
+    dfree(k.d_samp);
+    dfree(k.d_samp_ptr);
+    dfree(k.d_blk_bin);
+    dfree(k.d_roff);
+    dfree(k.d_redo);
+    dfree(k.d_cnt);
+    dfree(k.d_ell);
+    dfree(k.d_u);
+    dfree(k.d_flag);
+    dfree(k.d_thr);
+    dfree(k.d_est);
+    k.nsamp = 0;
+}
+
 static void free_plan(bv_ctx* c, int prec) {
+    if (prec == BV_MIXED) free_check(c);
     for (auto& b : c->plan[prec]) dfree(b.d_work);
     c->plan[prec].clear();
     c->plan_valid[prec] = false;
     c->tuned[prec] = false;
-    if (c->graph[prec]) cudaGraphExecDestroy(c->graph[prec]);
-    c->graph[prec] = nullptr;
+    for (int slot : {prec, prec == BV_MIXED ? 2 : prec}) {
+        if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
+        c->graph[slot] = nullptr;
+    }
 }
 
 void bv_invalidate_plans(bv_ctx* c) {
@@ -100,6 +122,7 @@ static void free_blocks(bv_ctx* c) {
     dfree(c->d_red_part);
     dfree(c->d_fb);
     dfree(c->d_fb_ws);
+    dfree(c->d_ind);
     c->fb_slots = 0;
     c->h_bptr.clear();
     c->h_pidx.clear();
@@ -229,7 +252,7 @@ extern "C" int bv_create(bv_ctx** out, int device, void* stream) {
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_fail, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_wctr, sizeof(int) * 2 * BV_WCTR_PER_PREC);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_wctr, sizeof(int) * BV_WCTR_GROUPS * BV_WCTR_PER_PREC);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_fail, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_fb, sizeof(int));
     if (e == cudaSuccess) *c->h_fb = 0;
@@ -752,9 +775,11 @@ static LLArgs make_args(bv_ctx* c) {
     a.theta = c->d_theta;
     a.work = nullptr;
     a.nwork = 0;
+    a.nwork_dev = nullptr;
     a.ctr = nullptr;
     a.ell_blk = c->d_ell_blk;
     a.u_blk = c->d_u_blk;
+    a.ind_blk = nullptr;
     a.fail = c->d_fail;
     a.ws = c->d_ws;
     a.ws_stride = c->ws_stride;
@@ -776,6 +801,103 @@ static int set_grid(bv_ctx* c, BinPlan& bp) {
     if (occ <= 0) return BV_EINTERNAL;
     const int64_t per_cta = (bp.kind == 3 || bp.kind == 4) ? bp.threads / 32 : 1;  // blocks in flight per CTA
     bp.grid = (int)std::min<int64_t>((bp.nwork + per_cta - 1) / per_cta, (int64_t)occ * c->num_sms);
+    return BV_OK;
+}
+
+// Samples per dataset of the mixed path's error check: every block of a small dataset,
+// else at least kChkMinSamples and 1/kChkFrac of the blocks, at evenly spaced positions
+// of the (random) block order.
+static const int64_t kChkMinSamples = 64, kChkFrac = 256;
+
+// FP64 bins of the mixed path's error check: one launch per bin for the sampled blocks
+// (static lists) and one for the blocks of datasets that fail the check (lists filled on
+// the device during the evaluation).  Blocks beyond the FP64 shared-memory limit use the
+// global-memory kernel with the fallback workspace.
+static int build_check(bv_ctx* c, const std::vector<int>& Nof) {
+    free_check(c);
+    auto& k = c->chk;
+    const int nsm = bv_smem_max_n(0, c->d);
+    std::vector<int> edges;
+    for (int e : kBinEdges)
+        if (e < nsm) edges.push_back(e);
+    edges.push_back(nsm);
+    const size_t nbin = edges.size() + 1;
+    std::vector<int32_t> bin_of(c->nblk);
+    std::vector<std::vector<int32_t>> all(nbin), smp(nbin);
+    for (int64_t i = 0; i < c->nblk; ++i) {
+        size_t b = 0;
+        while (b < edges.size() && Nof[i] > edges[b]) ++b;
+        bin_of[i] = (int32_t)b;
+        all[b].push_back((int32_t)i);
+    }
+    std::vector<int64_t> sptr(c->ndata + 1, 0);
+    std::vector<int32_t> samp;
+    for (int ds = 0; ds < c->ndata; ++ds) {
+        const int64_t lo = c->ds_blk_off[ds], B = c->ds_blk_off[ds + 1] - lo;
+        const int64_t sn = std::min<int64_t>(B, std::max<int64_t>(kChkMinSamples, (B + kChkFrac - 1) / kChkFrac));
+        for (int64_t q = 0; q < sn; ++q) {
+            const int32_t blk = (int32_t)(lo + (q * B) / sn);
+            samp.push_back(blk);
+            smp[bin_of[blk]].push_back(blk);
+        }
+        sptr[ds + 1] = (int64_t)samp.size();
+    }
+    k.nsamp = (int64_t)samp.size();
+    std::vector<int64_t> roff(nbin + 1, 0);
+    for (size_t b = 0; b < nbin; ++b) roff[b + 1] = roff[b] + (int64_t)all[b].size();
+    BV_CUDA(bv_plan_malloc(&k.d_samp, sizeof(int32_t) * std::max<size_t>(samp.size(), 1)));
+    BV_CUDA(bv_plan_malloc(&k.d_samp_ptr, sizeof(int64_t) * (c->ndata + 1)));
+    BV_CUDA(bv_plan_malloc(&k.d_blk_bin, sizeof(int32_t) * c->nblk));
+    BV_CUDA(bv_plan_malloc(&k.d_roff, sizeof(int64_t) * (nbin + 1)));
+    BV_CUDA(bv_plan_malloc(&k.d_redo, sizeof(int32_t) * c->nblk));
+    BV_CUDA(bv_plan_malloc(&k.d_cnt, sizeof(int) * BV_WCTR_PER_PREC));
+    BV_CUDA(bv_plan_malloc(&k.d_ell, sizeof(double) * c->nblk));
+    BV_CUDA(bv_plan_malloc(&k.d_u, sizeof(double) * c->nblk));
+    BV_CUDA(bv_plan_malloc(&k.d_flag, sizeof(int32_t) * c->ndata));
+    BV_CUDA(bv_plan_malloc(&k.d_thr, sizeof(float) * c->ndata));
+    BV_CUDA(bv_plan_malloc(&k.d_est, sizeof(double) * c->ndata));
+    BV_CUDA(cudaMemcpyAsync(k.d_samp, samp.data(), sizeof(int32_t) * samp.size(), cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaMemcpyAsync(k.d_samp_ptr, sptr.data(), sizeof(int64_t) * sptr.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+    BV_CUDA(cudaMemcpyAsync(k.d_blk_bin, bin_of.data(), sizeof(int32_t) * c->nblk, cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaMemcpyAsync(k.d_roff, roff.data(), sizeof(int64_t) * roff.size(), cudaMemcpyHostToDevice, c->stream));
+    BV_CUDA(cudaMemsetAsync(k.d_flag, 0, sizeof(int32_t) * c->ndata, c->stream));
+    BV_CUDA(cudaMemsetAsync(k.d_est, 0, sizeof(double) * c->ndata, c->stream));
+    if (nbin > (size_t)BV_WCTR_PER_PREC) return BV_EINTERNAL;
+    for (size_t b = 0; b < nbin; ++b) {
+        if (all[b].empty()) continue;
+        BinPlan bp;
+        bp.kind = b < edges.size() ? 0 : 2;
+        int nmax = 0;
+        for (int32_t i : all[b]) nmax = std::max(nmax, Nof[i]);
+        bp.nmax = nmax;
+        bp.threads = default_threads(bp.kind, bp.nmax);
+        // redo launch: the whole bin's capacity, count from the device
+        bp.nwork = (int32_t)all[b].size();
+        bp.d_work = k.d_redo + roff[b];
+        bp.d_ctr = c->d_wctr + 3 * BV_WCTR_PER_PREC + b;
+        bp.smem = bv_smem_bytes(bp.kind, bp.nmax, c->d, bp.threads);
+        if (bp.kind == 2) {
+            bp.grid = std::min<int>(bp.nwork, c->fb_slots);
+        } else {
+            const int occ = bv_occupancy(bp.kind, bp.threads, bp.smem);
+            if (occ <= 0) return BV_EINTERNAL;
+            bp.grid = (int)std::min<int64_t>(bp.nwork, (int64_t)occ * c->num_sms);
+        }
+        bp.slot = (int)b;
+        k.rbins.push_back(bp);
+        if (!smp[b].empty()) {
+            BinPlan sb = bp;
+            sb.nwork = (int32_t)smp[b].size();
+            sb.d_ctr = c->d_wctr + 2 * BV_WCTR_PER_PREC + b;
+            sb.grid = std::min(sb.grid, sb.nwork);
+            sb.d_work = nullptr;
+            BV_CUDA(bv_plan_malloc(&sb.d_work, sizeof(int32_t) * smp[b].size()));
+            k.sbins.push_back(sb);
+            BV_CUDA(cudaMemcpyAsync(k.sbins.back().d_work, smp[b].data(), sizeof(int32_t) * smp[b].size(),
+                                    cudaMemcpyHostToDevice, c->stream));
+        }
+    }
     return BV_OK;
 }
 
@@ -832,7 +954,9 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
         while (slots > 1 && (double)slots * stride * 8.0 > 2e9) --slots;
         dfree(c->d_fb_ws);
         dfree(c->d_fb);
+        dfree(c->d_ind);
         c->fb_slots = 0;
+        BV_CUDA(bv_plan_malloc(&c->d_ind, sizeof(float) * c->nblk));
         BV_CUDA(bv_plan_malloc(&c->d_fb_ws, sizeof(double) * stride * slots));
         BV_CUDA(bv_plan_malloc(&c->d_fb, sizeof(int) * (c->nblk + 1)));
         BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));
@@ -862,6 +986,7 @@ int bv_ensure_plan(bv_ctx* c, int prec) {
                      [](const BinPlan& x, const BinPlan& y) { return x.nmax > y.nmax; });
     if (c->plan[prec].size() > BV_WCTR_PER_PREC) return BV_EINVAL;
     for (size_t i = 0; i < c->plan[prec].size(); ++i) c->plan[prec][i].d_ctr = c->d_wctr + prec * BV_WCTR_PER_PREC + i;
+    if (prec == BV_MIXED) BV_TRY(build_check(c, Nof));
     BV_CUDA(cudaStreamSynchronize(c->stream));
     c->plan_valid[prec] = true;
     return BV_OK;
@@ -876,7 +1001,8 @@ static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     float best = 1e30f;
     const bool ok = !c->cur_gen || bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream) == cudaSuccess;
     for (int r = 0; ok && r < reps + 1; ++r) {
-        if (bv_launch_eval_reset(c->d_fail, c->d_wctr, 2 * BV_WCTR_PER_PREC, c->stream) != cudaSuccess) break;
+        if (bv_launch_eval_reset(c->d_fail, c->d_wctr, BV_WCTR_GROUPS * BV_WCTR_PER_PREC, c->stream) != cudaSuccess)
+            break;
         cudaEventRecord(e0, c->stream);
         cudaError_t e = bv_launch_bin(bp, a, c->stream);
         cudaEventRecord(e1, c->stream);
@@ -910,12 +1036,19 @@ static int autotune(bv_ctx* c, int prec) {
         const char* form = getenv("BV_KERNEL_FORM");
         const bool only_cta = form && strcmp(form, "cta") == 0;
         const bool only_warp = form && strcmp(form, "warp") == 0;
+        // mixed bins with N >= 64 also try the tensor-core kernel (BV_KERNEL_FORM=tc
+        // restricts them to it, =cta to the SIMT CTA kernel)
         std::vector<std::pair<int, int>> cands;
         const bool warp_ok = (bp.kind == 1 && bp.nmax <= 128) || (bp.kind == 0 && bp.nmax <= 64);
-        if (!(only_warp && warp_ok))
+        const bool only_tc = form && strcmp(form, "tc") == 0;
+        const bool tc_ok = bp.kind == 1 && bp.nmax >= 64 &&
+                           bv_smem_bytes(5, bp.nmax, c->d, 256) <= (size_t)(227 * 1024 - 3072);
+        if (!(only_warp && warp_ok) && !(only_tc && tc_ok))
             for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
-        if (!only_cta && warp_ok)
+        if (!only_cta && !only_tc && warp_ok)
             for (int t : {64, 128, 256}) cands.push_back({bp.kind == 1 ? 3 : 4, t});
+        if (!only_cta && !only_warp && tc_ok)
+            for (int t : {256, 384, 512}) cands.push_back({5, t});
         int best_k = bp.kind, best_t = bp.threads;
         float best_ms = 1e30f;
         for (auto kt : cands) {
@@ -957,17 +1090,14 @@ extern "C" int bv_autotune(bv_ctx* c, int32_t prec) {
             bv_theta_to_dev(&t, c->d, &c->h_theta[k]);
         }
     c->tuned[prec] = false;
-    if (c->graph[prec]) cudaGraphExecDestroy(c->graph[prec]);
-    c->graph[prec] = nullptr;
+    for (int slot : {prec, prec == BV_MIXED ? 2 : prec}) {
+        if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
+        c->graph[slot] = nullptr;
+    }
     return autotune(c, prec);
 }
 
-// The bins of one evaluation as parallel branches: failure reset, fork, every bin on its
-// own side stream, join, reduction.  Captured into the graph, the branches become
-// independent kernel nodes, so the CTAs of small bins fill the SMs that the tail of a
-// large bin leaves idle.
-static int enqueue_eval_forked(bv_ctx* c, int prec) {
-    const size_t nb = c->plan[prec].size();
+static int ensure_side(bv_ctx* c, size_t nb) {
     while (c->side.size() < nb) {
         cudaStream_t s;
         BV_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -978,13 +1108,62 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         BV_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->side_ev.push_back(e);
     }
-    BV_CUDA(bv_launch_eval_reset(c->d_fail, c->d_wctr, 2 * BV_WCTR_PER_PREC, c->stream));
+    return BV_OK;
+}
+
+// Launch `bins` as parallel branches off the context's stream and join them (with
+// dyn, each launch's work count is its bin's slot of the mixed check's device counts).
+static int fork_bins(bv_ctx* c, const std::vector<BinPlan>& bins, const LLArgs& a, bool dyn) {
+    BV_TRY(ensure_side(c, bins.size()));
+    BV_CUDA(cudaEventRecord(c->side_ev[0], c->stream));
+    for (size_t i = 0; i < bins.size(); ++i) {
+        LLArgs ai = a;
+        if (dyn) ai.nwork_dev = c->chk.d_cnt + bins[i].slot;
+        BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
+        BV_CUDA(bv_launch_bin(bins[i], ai, c->side[i]));
+        BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
+    }
+    for (size_t i = 0; i < bins.size(); ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
+    return BV_OK;
+}
+
+// The mixed path's error check (after the FP32 bins and their FP64 fallback): the sampled
+// blocks in FP64, the per-dataset test against kMixedTol, and the FP64 recomputation of
+// every block of a dataset that fails it.
+static int enqueue_check(bv_ctx* c, const LLArgs& a) {
+    auto& k = c->chk;
+    LLArgs a64 = a;
+    a64.fb = nullptr;
+    a64.dyn = 0;
+    a64.ws = c->d_fb_ws;
+    a64.ws_stride = c->fb_stride;
+    LLArgs as = a64;
+    as.ell_blk = k.d_ell;
+    as.u_blk = k.d_u;
+    BV_TRY(fork_bins(c, k.sbins, as, false));
+    BV_CUDA(bv_launch_mixed_check(c->d_ell_blk, c->d_u_blk, k.d_ell, k.d_u, c->d_ind, k.d_samp, k.d_samp_ptr,
+                                  c->d_ds_blk_off, c->ndata, c->mixed_tol, k.d_flag, k.d_thr, k.d_est, c->stream));
+    BV_CUDA(cudaMemsetAsync(k.d_cnt, 0, sizeof(int) * BV_WCTR_PER_PREC, c->stream));
+    BV_CUDA(bv_launch_mixed_redo_list(c->d_bds, c->nblk, k.d_flag, k.d_thr, c->d_ind, k.d_blk_bin, k.d_roff, k.d_redo,
+                                      k.d_cnt, c->stream));
+    return fork_bins(c, k.rbins, a64, true);
+}
+
+// The bins of one evaluation as parallel branches: failure reset, fork, every bin on its
+// own side stream, join, reduction.  Captured into the graph, the branches become
+// independent kernel nodes, so the CTAs of small bins fill the SMs that the tail of a
+// large bin leaves idle.
+static int enqueue_eval_forked(bv_ctx* c, int prec) {
+    const size_t nb = c->plan[prec].size();
+    BV_TRY(ensure_side(c, nb));
+    BV_CUDA(bv_launch_eval_reset(c->d_fail, c->d_wctr, BV_WCTR_GROUPS * BV_WCTR_PER_PREC, c->stream));
     if (c->cur_gen) BV_CUDA(bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream));
     const bool fallback = prec == BV_MIXED && c->d_fb;
     if (fallback) BV_CUDA(cudaMemsetAsync(c->d_fb, 0, sizeof(int), c->stream));
     BV_CUDA(cudaEventRecord(c->side_ev[0], c->stream));
     LLArgs a = make_args(c);
     if (fallback) a.fb = c->d_fb;
+    if (prec == BV_MIXED) a.ind_blk = c->d_ind;
     for (size_t i = 0; i < nb; ++i) {
         BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
         BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
@@ -997,6 +1176,11 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
         fa.ws_stride = c->fb_stride;
         BV_CUDA(bv_launch_fallback(fa, c->fb_slots, c->stream));
     }
+    if (prec == BV_MIXED && c->mixed_tol > 0.0 && !c->chk.rbins.empty()) {
+        LLArgs ac = a;
+        ac.ind_blk = nullptr;
+        BV_TRY(enqueue_check(c, ac));
+    }
     BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->red_chunks, c->d_red_part,
                              c->d_out, c->d_quad, c->stream));
     return BV_OK;
@@ -1004,13 +1188,17 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
 
 // Graph of one evaluation, captured once per precision after tuning.  theta is copied in
 // front of each launch.
+static int graph_slot(const bv_ctx* c, int prec) { return prec == BV_MIXED && c->mixed_tol <= 0.0 ? 2 : prec; }
+
 static int ensure_graph(bv_ctx* c, int prec) {
-    if (c->graph[prec] && c->graph_gen[prec] != c->cur_gen) {
-        cudaGraphExecDestroy(c->graph[prec]);
-        c->graph[prec] = nullptr;
+    const int slot = graph_slot(c, prec);
+    if (c->graph[slot] && (c->graph_gen[slot] != c->cur_gen || (slot == 1 && c->graph_tol != c->mixed_tol))) {
+        cudaGraphExecDestroy(c->graph[slot]);
+        c->graph[slot] = nullptr;
     }
-    if (c->graph[prec]) return BV_OK;
-    c->graph_gen[prec] = c->cur_gen;
+    if (c->graph[slot]) return BV_OK;
+    c->graph_gen[slot] = c->cur_gen;
+    if (slot == 1) c->graph_tol = c->mixed_tol;
     cudaGraph_t g = nullptr;
     BV_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const int st = enqueue_eval_forked(c, prec);
@@ -1020,7 +1208,7 @@ static int ensure_graph(bv_ctx* c, int prec) {
         return st;
     }
     BV_CUDA(e);
-    e = cudaGraphInstantiate(&c->graph[prec], g, 0);
+    e = cudaGraphInstantiate(&c->graph[slot], g, 0);
     cudaGraphDestroy(g);
     BV_CUDA(e);
     return BV_OK;
@@ -1032,7 +1220,7 @@ int bv_enqueue_loglik(bv_ctx* c, int prec, double* d_out, bool) {
     BV_TRY(ensure_graph(c, prec));
     BV_CUDA(cudaMemcpyAsync(c->d_theta, c->h_theta.data(), sizeof(DevTheta) * c->ndata, cudaMemcpyHostToDevice,
                             c->stream));
-    BV_CUDA(cudaGraphLaunch(c->graph[prec], c->stream));
+    BV_CUDA(cudaGraphLaunch(c->graph[graph_slot(c, prec)], c->stream));
     if (d_out && d_out != c->d_out)
         BV_CUDA(cudaMemcpyAsync(d_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToDevice, c->stream));
     return BV_OK;
@@ -1113,7 +1301,14 @@ extern "C" int bv_plan_info(bv_ctx* c, int32_t prec, int32_t* launches, int32_t*
     BV_CUDA(cudaSetDevice(c->device));
     BV_TRY(bv_ensure_plan(c, prec));
     // bins + failure reset + two reduction stages (+ the general-nu table)
-    if (launches) *launches = (int32_t)c->plan[prec].size() + 3 + (c->cur_gen ? 1 : 0);
+    // (mixed: + the FP64 fallback pass, the check's sample and redo launches, the check
+    // and the redo-list kernels)
+    int32_t nl = (int32_t)c->plan[prec].size() + 3 + (c->cur_gen ? 1 : 0);
+    if (prec == BV_MIXED) {
+        nl += 1;
+        if (c->mixed_tol > 0.0) nl += (int32_t)c->chk.sbins.size() + (int32_t)c->chk.rbins.size() + 2;
+    }
+    if (launches) *launches = nl;
     if (nbins) *nbins = (int32_t)c->plan[prec].size();
     double f = 0.0, e = 0.0;
     for (int64_t i = 0; i < c->nblk; ++i) {
@@ -1142,6 +1337,45 @@ extern "C" int bv_loglik_terms(bv_ctx* c, const bv_theta* theta, int32_t prec, d
 extern "C" int bv_last_error_block(bv_ctx* c, int64_t* block) {
     if (!c || !block) return BV_EINVAL;
     *block = (c->h_fail && *c->h_fail != ~0ull) ? (int64_t)*c->h_fail : -1;
+    return BV_OK;
+}
+
+extern "C" int bv_set_mixed_tolerance(bv_ctx* c, double tol) {
+    if (!c || !(tol >= 0.0) || !(tol < 1.0)) return BV_EINVAL;
+    c->mixed_tol = tol;  // the evaluation graph of this setting is (re)captured on next use
+    return BV_OK;
+}
+
+extern "C" int bv_mixed_block_indicator(bv_ctx* c, float* out) {
+    if (!c || !out) return BV_EINVAL;
+    if (!c->d_ind || !c->plan_valid[BV_MIXED]) return BV_ESTATE;
+    BV_CUDA(cudaSetDevice(c->device));
+    BV_CUDA(cudaMemcpyAsync(out, c->d_ind, sizeof(float) * c->nblk, cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    return BV_OK;
+}
+
+extern "C" int bv_mixed_check_info(bv_ctx* c, int64_t* blocks_fp64, int32_t* datasets_touched, double* est_rel) {
+    if (!c || !blocks_fp64) return BV_EINVAL;
+    *blocks_fp64 = 0;
+    if (datasets_touched) *datasets_touched = 0;
+    if (!c->chk.d_flag || !c->plan_valid[BV_MIXED]) return BV_ESTATE;
+    if (c->mixed_tol <= 0.0) return BV_OK;  // no check ran
+    BV_CUDA(cudaSetDevice(c->device));
+    std::vector<int32_t> f(c->ndata);
+    std::vector<double> e(c->ndata);
+    std::vector<int> cnt(BV_WCTR_PER_PREC);
+    BV_CUDA(cudaMemcpyAsync(f.data(), c->chk.d_flag, sizeof(int32_t) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaMemcpyAsync(e.data(), c->chk.d_est, sizeof(double) * c->ndata, cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaMemcpyAsync(cnt.data(), c->chk.d_cnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, c->stream));
+    BV_CUDA(cudaStreamSynchronize(c->stream));
+    int64_t nb = c->chk.nsamp;
+    for (int v : cnt) nb += v;
+    *blocks_fp64 = nb;
+    for (int k = 0; k < c->ndata; ++k) {
+        if (datasets_touched) *datasets_touched += f[k] ? 1 : 0;
+        if (est_rel) est_rel[k] = e[k];
+    }
     return BV_OK;
 }
 

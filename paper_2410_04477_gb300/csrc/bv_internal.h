@@ -71,8 +71,10 @@ struct DevTheta {
 // L1 + L2 = ln2/256, 2^{n/256} = 2^{floor(n/256)} tab[n mod 256].  Filled on the host in
 // long double.
 #define BV_EXP_TAB 256
-// work counters per precision (at most 15 shared-memory bins and one global-memory bin)
+// work counters per group of launches (at most 15 shared-memory bins and one global-memory
+// bin each): FP64 bins, mixed bins, the mixed check's FP64 sample bins and its FP64 redo bins
 #define BV_WCTR_PER_PREC 32
+#define BV_WCTR_GROUPS 4
 struct ExpConsts {
     double tab[BV_EXP_TAB];   // 2^{j/256}, j = 0..255
     double k;                 // 256 / ln 2
@@ -97,6 +99,7 @@ struct LLArgs {
     const DevTheta* theta;   // per dataset
     const int32_t* work;     // block ids of this launch, largest first
     int32_t nwork;
+    const int* nwork_dev;    // or null; else the launch's work count is min(*nwork_dev, nwork)
     int* ctr;                // work counter of this launch (zeroed before it), or null: grid stride
     int gen;                 // host side: launch the general-smoothness instantiation
     int* fb;                 // mixed precision: [0] count, [1..] blocks to redo in FP64 (or null)
@@ -104,6 +107,8 @@ struct LLArgs {
     const double* gtab;      // per dataset: general-nu Matern table (GTAB_SIZE doubles)
     double* ell_blk;         // per-block conditional log-likelihood (output)
     double* u_blk;           // per-block quadratic form u_i = v_i^T v_i (output)
+    float* ind_blk;          // mixed kernels, or null: per-block sum over all pivots of
+                             // (sigma^2 + tau^2) / pivot, the conditioning indicator
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
     double* ws;              // global workspace (large-block path)
     int64_t ws_stride;       // doubles per workspace slot
@@ -113,7 +118,8 @@ struct LLArgs {
 // Per-size-bin launch plan entry.
 struct BinPlan {
     int kind;            // 0: FP64 shared-memory, 1: mixed (CTA per block), 2: large (global),
-                         // 3: mixed (warp per block), 4: FP64 (warp per block)
+                         // 3: mixed (warp per block), 4: FP64 (warp per block),
+                         // 5: mixed with tensor-core updates (CTA per block)
     int nmax;            // largest augmented size N = m + b in the bin
     int threads;         // CTA size (autotuned)
     int grid;            // CTAs launched
@@ -121,8 +127,14 @@ struct BinPlan {
     int32_t* d_work;     // device block ids (largest N first)
     int32_t nwork;
     int* d_ctr;          // this bin's work counter (a slot of the context's counter array)
+    int slot = -1;       // mixed check's redo launches: index of the bin's device count
     std::vector<int32_t> h_work;
 };
+
+// Tensor-core mixed-precision kernel (bv_mixed_tc.cu), kind 5 of a bin plan.
+size_t bv_tc_smem_bytes(int nmax);
+int bv_tc_occupancy(int threads, size_t smem);
+cudaError_t bv_tc_launch(int threads, int grid, size_t smem, const LLArgs& a, cudaStream_t s);
 
 // Launchers (bv_loglik.cu).
 int bv_smem_max_n(int kind, int d);
@@ -143,6 +155,18 @@ cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s);
 cudaError_t bv_launch_eval_reset(unsigned long long* fail, int* ctr, int n, cudaStream_t s);
 // FP64 recomputation (global-memory kernel) of the blocks listed in a.fb.
 cudaError_t bv_launch_fallback(const LLArgs& a, int grid, cudaStream_t s);
+// Mixed-precision error check of every dataset (one CTA each) from the FP64 values of its
+// sampled blocks (samp[samp_ptr[ds] .. samp_ptr[ds+1])) and the blocks' conditioning
+// indicators: per dataset a flag (0 keep, 1 redo blocks with ind > thr, 2 redo all), the
+// threshold and the bound on the relative error of what stays in FP32 (bv_loglik.cu).
+cudaError_t bv_launch_mixed_check(double* ell_blk, double* u_blk, const double* ell64, const double* u64,
+                                  const float* ind, const int32_t* samp, const int64_t* samp_ptr,
+                                  const int64_t* ds_blk_off, int32_t ndata, double tol, int32_t* flag, float* thr,
+                                  double* est, cudaStream_t s);
+// Queue every block the check sends back on the FP64 redo list of its bin.
+cudaError_t bv_launch_mixed_redo_list(const int32_t* bds, int64_t nblk, const int32_t* flag, const float* thr,
+                                      const float* ind, const int32_t* blk_bin, const int64_t* roff, int32_t* redo,
+                                      int* cnt, cudaStream_t s);
 // Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
 cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s);
 #define BV_GTAB_DOUBLES 931  // GTAB_NOCT * GTAB_DEG
@@ -234,6 +258,8 @@ struct bv_ctx {
     int* d_fb = nullptr;              // mixed-precision FP64 fallback list: [0] count, [1..] blocks
     int* h_fb = nullptr;              // pinned copy of the count
     double* d_fb_ws = nullptr;        // FP64 workspace slots for the fallback pass
+    float* d_ind = nullptr;           // mixed: per-block conditioning indicator (LLArgs::ind_blk)
+    double mixed_tol = 1e-6;          // mixed: bound enforced by the FP64 check (0: no check)
     int64_t fb_stride = 0;
     int fb_slots = 0;
     int32_t red_chunks = 1;
@@ -251,12 +277,35 @@ struct bv_ctx {
     int64_t ws_stride = 0;
     int ws_slots = 0;
 
+    // mixed precision's error check (built with the mixed plan): FP64 bins over all blocks
+    // (the sampled blocks' static lists and the redo lists filled per evaluation), the
+    // sample CSR by dataset, per-block FP64 bin, per-dataset flags and error estimates
+    struct MixedCheck {
+        std::vector<BinPlan> sbins;        // FP64 launches of the sampled blocks (own d_work)
+        std::vector<BinPlan> rbins;        // FP64 launches of the redo lists (d_work inside d_redo)
+        int32_t* d_samp = nullptr;         // sampled blocks, dataset after dataset
+        int64_t* d_samp_ptr = nullptr;     // ndata + 1
+        int32_t* d_blk_bin = nullptr;      // FP64 bin of every block
+        int64_t* d_roff = nullptr;         // per bin: offset of its redo segment
+        int32_t* d_redo = nullptr;         // nblk
+        int* d_cnt = nullptr;              // per bin: blocks queued for redo this evaluation
+        double* d_ell = nullptr;           // FP64 ell_i of the sampled blocks (by block id)
+        double* d_u = nullptr;
+        int32_t* d_flag = nullptr;         // per dataset: 0 kept, 1 worst blocks redone, 2 all redone
+        float* d_thr = nullptr;            // per dataset: indicator threshold of flag 1
+        double* d_est = nullptr;           // per dataset: estimated bound of the FP32 part's relative error
+        int64_t nsamp = 0;
+    } chk;
+
     // per precision: plan, graph
     std::vector<BinPlan> plan[2];
     bool plan_valid[2] = {false, false};
     bool tuned[2] = {false, false};
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    bool graph_gen[2] = {false, false};   // whether each graph holds the general-nu kernels
+    // graphs of one evaluation: [0] FP64, [1] mixed with its check (captured at tolerance
+    // graph_tol), [2] mixed without the check
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    double graph_tol = 0.0;
+    bool graph_gen[3] = {false, false, false};  // whether each graph holds the general-nu kernels
     bool cur_gen = false;                 // whether the current theta needs them
     std::vector<cudaStream_t> side;   // fork/join streams of the captured graph
     std::vector<cudaEvent_t> side_ev; // [0] fork, [1..] joins

@@ -33,49 +33,9 @@
 
 #include "bv_device.cuh"
 #include "bv_internal.h"
+#include "bv_ll_block.cuh"
 
 namespace {
-
-constexpr double kLog2Pi = 1.8378770664093454835606594728112;
-
-__device__ __forceinline__ float matern32(int nu, float sigma2, float x) {
-    const float e = expf(-x);
-    if (nu == NU_HALF) return sigma2 * e;
-    if (nu == NU_3HALF) return sigma2 * ((1.0f + x) * e);
-    return sigma2 * ((1.0f + x * (1.0f + x * (1.0f / 3.0f))) * e);
-}
-
-// Sums of the block columns' terms z_k^2 + log L_kk (Algorithm 1's quadratic form and
-// log-determinant) and of z_k^2 alone, k = m..N-1, taken by the 32 lanes of one warp
-// (a block has few columns, b = N - m); the totals are valid in lane 0.
-template <typename ZF, typename LF>
-__device__ __forceinline__ double2 warp_terms(int m, int N, int lane, ZF zk, LF logk) {
-    double part = 0.0, partu = 0.0;
-    for (int k = m + lane; k < N; k += 32) {
-        const double z = zk(k);
-        partu += z * z;
-        part += z * z + logk(k);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        part += __shfl_xor_sync(0xffffffffu, part, o);
-        partu += __shfl_xor_sync(0xffffffffu, partu, o);
-    }
-    return make_double2(part, partu);
-}
-
-__device__ __forceinline__ void record_fail(unsigned long long* fail, int blk) {
-    atomicMin(fail, (unsigned long long)blk);
-}
-
-// Work distribution of one launch.  With a counter, each CTA (or warp) takes its next
-// work item from the launch's atomic counter, asked for one item ahead so that the
-// atomic's latency hides behind the current block; a CTA that starts late (its SM held
-// by a concurrent bin of the same evaluation) then takes fewer items instead of a fixed
-// share.  Without a counter: the fixed grid stride `stride_next`.
-__device__ __forceinline__ int take_work(int* ctr, int stride_next) {
-    return ctr ? atomicAdd(ctr, 1) : stride_next;
-}
 
 // ---------------------------------------------------------------------------------
 // FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2][N+1] | pts[d][N]
@@ -91,9 +51,10 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
 
     __shared__ int s_w;
+    const int nwork = work_count(a);
     if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
     __syncthreads();
-    for (int w = s_w; w < a.nwork; w = s_w) {
+    for (int w = s_w; w < nwork; w = s_w) {
         const int nx = tid == 0 ? take_work(a.ctr, w + gridDim.x) : 0;
         const int blk = a.work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
@@ -451,31 +412,21 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
         gsync<WARP>();
     }
 
-    // quadratic form and log-determinant terms of the block columns, accumulated in FP64
-    // (the logarithm of an FP32 pivot is taken in FP32: its 1-ulp error is far below the
-    // pivot's own FP32 rounding)
-    // by the first warp only; the totals are valid in thread 0
+    // quadratic form and log-determinant terms of the block columns, accumulated in FP64,
+    // the logarithm of each pivot taken in FP64; by the first warp only, the totals are
+    // valid in thread 0
     if (tid >= 32) return make_double2(0.0, 0.0);
+    if (a.ind_blk) {
+        const float ind = warp_indicator(N, tid, s2 + tau2, [&](int k) { return piv[k]; });
+        if (tid == 0) a.ind_blk[blk] = ind;
+    }
     return warp_terms(
         m, N, tid,
         [&](int k) {
             return (k >> 2) == (N >> 2) ? (double)ydiag[k & 3]
                                         : (double)tile_row(tiles, tile_index(N >> 2, k >> 2), N & 3)[k & 3];
         },
-        [&](int k) { return (double)logf(piv[k]); });
-}
-
-// A block whose FP32 factorisation breaks down (non-positive pivot) is queued for the FP64
-// fallback pass instead of failing the evaluation.
-__device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, double su, int failed) {
-    double ell = -0.5 * (s + (double)b * kLog2Pi);
-    if (failed || !(ell == ell)) {
-        ell = -INFINITY;
-        if (a.fb) a.fb[1 + atomicAdd(a.fb, 1)] = blk;
-        else record_fail(a.fail, blk);
-    }
-    a.ell_blk[blk] = ell;
-    a.u_blk[blk] = su;
+        [&](int k) { return log((double)piv[k]); });
 }
 
 // CTA per block.
@@ -543,8 +494,9 @@ __global__ void __launch_bounds__(NT) k_ll_fp64_w(LLArgs a, int region_doubles) 
     __syncthreads();
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
     double* A = reinterpret_cast<double*>(smraw) + (size_t)warp * region_doubles;
+    const int nwork = work_count(a);
     int w = __shfl_sync(0xffffffffu, lane == 0 ? take_work(a.ctr, blockIdx.x * WPB + warp) : 0, 0);
-    while (w < a.nwork) {
+    while (w < nwork) {
         const int nx = lane == 0 ? take_work(a.ctr, w + gridDim.x * WPB) : 0;
         const int blk = a.work[w];
         const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
@@ -630,7 +582,7 @@ __global__ void __launch_bounds__(NT) k_ll_large(LLArgs a) {
     double* slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
     for (int i = tid; i < BV_EXP_TAB; i += NT) etab[i] = a.ex.tab[i];
     const double eK = a.ex.k, eL1 = a.ex.l1, eL2 = a.ex.l2;
-    const int nwork = a.dyn ? *a.fb : a.nwork;
+    const int nwork = a.dyn ? *a.fb : work_count(a);
     const int* work = a.dyn ? a.fb + 1 : a.work;
 
     __shared__ int s_w;
@@ -804,6 +756,142 @@ __global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64
     out_quad[ds] = S2 + C2;
 }
 
+// ---------------------------------------------------------------------------------
+// Mixed precision's error check.  Model: the FP32 error of block i's term is
+// delta_i = r_i eps B_i, eps = 2^-24 and B_i the block's conditioning indicator (the sum
+// over its pivots of variance / conditional variance), with r_i independent, zero mean and
+// of a scale rho that depends on the dataset.  Per dataset (one CTA):
+//   1. on the fixed sample of blocks (evenly spaced positions in the random block order),
+//      recomputed in FP64: rho^2 = mean r_i^2, the mean of r_i and its z-score, and the
+//      log-likelihood estimate L = B mean(ell_i(FP64)); the sampled blocks take their FP64
+//      terms;
+//   2. the bound on the dataset's error is 3 (1.2 rho) eps sqrt(sum B_i^2) over the blocks
+//      still in FP32 (3 standard deviations, with a 20% margin for the sampled rho);
+//   3. if a bias shows (|z| > 4) every block is recomputed in FP64 (flag 2); else if the
+//      bound exceeds tol |L|, the blocks with the largest B_i are recomputed in FP64 until
+//      it does not: the largest threshold B* (bisection on log2 B*, 16 steps) with the bound
+//      over {B_i <= B*} within tol |L| (flag 1, thr = B*).
+// Fixed-order sums throughout: the decision is deterministic.  Blocks that the FP32-failure
+// fallback already recomputed carry B_i = 0 and count as exact.
+// ---------------------------------------------------------------------------------
+constexpr int kChkThreads = 256;
+constexpr float kEps32 = 5.9604644775390625e-8f;  // 2^-24
+
+// Whether local block j of a dataset with B blocks is one of its s sampled blocks
+// (positions floor(q B / s), q = 0 .. s-1).
+__device__ __forceinline__ bool is_sampled(int64_t j, int64_t B, int64_t s) {
+    if (s >= B) return true;
+    const int64_t q = (j * s + B - 1) / B;  // smallest q with q B / s >= j
+    return q < s && (q * B) / s == j;
+}
+
+__device__ __forceinline__ double cta_sum(double v, double* sh, int tid) {
+    sh[tid] = v;
+    __syncthreads();
+    for (int w = kChkThreads / 2; w > 0; w >>= 1) {
+        if (tid < w) sh[tid] += sh[tid + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Sum of B_i^2 over the dataset's FP32 blocks with B_i <= thr.
+__device__ __forceinline__ double kept_b2(const float* ind, int64_t lo, int64_t B, int64_t s, float thr, double* sh,
+                                          int tid) {
+    double acc = 0.0;
+    for (int64_t j = tid; j < B; j += kChkThreads) {
+        const float b = ind[lo + j];
+        if (b > 0.0f && b <= thr && !is_sampled(j, B, s)) acc += (double)b * (double)b;
+    }
+    return cta_sum(acc, sh, tid);
+}
+
+__global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, double* u_blk, const double* ell64,
+                                                             const double* u64, const float* ind,
+                                                             const int32_t* samp, const int64_t* samp_ptr,
+                                                             const int64_t* ds_off, double tol, int32_t* flag,
+                                                             float* thr, double* est) {
+    __shared__ double sh[kChkThreads];
+    const int ds = blockIdx.x, tid = threadIdx.x;
+    const int64_t s0 = samp_ptr[ds], s1 = samp_ptr[ds + 1], lo = ds_off[ds];
+    const int64_t B = ds_off[ds + 1] - lo, s = s1 - s0;
+    double r1 = 0.0, r2 = 0.0, e = 0.0, cnt = 0.0, bad = 0.0;
+    for (int64_t j = s0 + tid; j < s1; j += kChkThreads) {
+        const int blk = samp[j];
+        const double x64 = ell64[blk], x32 = ell_blk[blk];
+        const float b = ind[blk];
+        if (!(x64 > -INFINITY) || !(x64 < INFINITY)) bad += 1.0;
+        e += x64;
+        if (b > 0.0f && b < INFINITY) {
+            const double r = (x32 - x64) / ((double)kEps32 * (double)b);
+            r1 += r;
+            r2 += r * r;
+            cnt += 1.0;
+        }
+        ell_blk[blk] = x64;
+        u_blk[blk] = u64[blk];
+    }
+    r1 = cta_sum(r1, sh, tid);
+    r2 = cta_sum(r2, sh, tid);
+    e = cta_sum(e, sh, tid);
+    cnt = cta_sum(cnt, sh, tid);
+    bad = cta_sum(bad, sh, tid);
+    int f = 0;
+    float t = INFINITY;
+    double bound = 0.0;
+    if (bad > 0.0) {
+        bound = INFINITY;  // a block fails in FP64 too: the dataset's ell is -inf either way
+    } else if (s < B && cnt > 1.0) {
+        const double rho = sqrt(r2 / cnt), mu = r1 / cnt;
+        const double sd_mu = sqrt(fmax(r2 / cnt - mu * mu, 0.0) / cnt);
+        const double L = fabs((double)B * e / (double)s);
+        const double k = 3.0 * 1.2 * rho * (double)kEps32 / L;  // bound = k sqrt(S)
+        if (!(fabs(mu) <= 4.0 * sd_mu + 1e-300) || !(L > 0.0)) {
+            f = 2;
+            bound = INFINITY;
+        } else {
+            const double S = kept_b2(ind, lo, B, s, INFINITY, sh, tid);
+            bound = k * sqrt(S);
+            if (!(bound <= tol)) {
+                // largest log2 threshold in [0, 48] whose kept blocks meet the bound
+                float a = 0.0f, c = 48.0f;
+                for (int it = 0; it < 16; ++it) {
+                    const float mid = 0.5f * (a + c);
+                    const double Sm = kept_b2(ind, lo, B, s, exp2f(mid), sh, tid);
+                    if (k * sqrt(Sm) <= tol) a = mid;
+                    else c = mid;
+                }
+                f = 1;
+                t = exp2f(a);
+                bound = k * sqrt(kept_b2(ind, lo, B, s, t, sh, tid));
+            }
+        }
+    }
+    if (tid == 0) {
+        flag[ds] = f;
+        thr[ds] = t;
+        est[ds] = bound;
+    }
+}
+
+// Queue on the FP64 redo list of its bin every block the check sends back: all blocks of a
+// dataset with flag 2, those with B_i above the dataset's threshold with flag 1.
+__global__ void k_mixed_redo_list(const int32_t* __restrict__ bds, int64_t nblk, const int32_t* __restrict__ flag,
+                                  const float* __restrict__ thr, const float* __restrict__ ind,
+                                  const int32_t* __restrict__ blk_bin, const int64_t* __restrict__ roff,
+                                  int32_t* __restrict__ redo, int* cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nblk) return;
+    const int ds = bds[i];
+    const int f = flag[ds];
+    if (f == 0 || (f == 1 && !(ind[i] > thr[ds]))) return;
+    const int b = blk_bin[i];
+    const int pos = atomicAdd(cnt + b, 1);
+    redo[roff[b] + pos] = (int32_t)i;
+}
+
 __global__ void k_fail_reset(unsigned long long* f) { *f = ~0ull; }
 
 __global__ void k_eval_reset(unsigned long long* f, int* ctr, int n) {
@@ -900,6 +988,7 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
     const size_t R = (size_t)nmax + 1;
     const size_t el = kind == 1 ? sizeof(float) : sizeof(double);
     if (kind == 2) return 0;
+    if (kind == 5) return bv_tc_smem_bytes(nmax);
     if (kind == 1) return sizeof(float) * (size_t)mixed_floats(nmax);
     if (kind == 3) return sizeof(float) * (size_t)mixed_floats(nmax) * (size_t)(threads / 32);
     if (kind == 4) {  // one region per warp, each a multiple of 16 bytes
@@ -926,6 +1015,7 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
     a.work = bp.d_work;
     a.nwork = bp.nwork;
     a.ctr = bp.d_ctr;
+    if (bp.kind == 5) return bv_tc_launch(bp.threads, bp.grid, bp.smem, a, s);
     switch (bp.threads) {
         case 64: return launch_kind<64>(bp.kind, bp.grid, bp.smem, a, s);
         case 128: return launch_kind<128>(bp.kind, bp.grid, bp.smem, a, s);
@@ -967,6 +1057,23 @@ cudaError_t bv_launch_fallback(const LLArgs& a0, int grid, cudaStream_t s) {
     return a.gen ? launch_kind_g<256, true>(2, grid, 0, a, s) : launch_kind_g<256, false>(2, grid, 0, a, s);
 }
 
+cudaError_t bv_launch_mixed_check(double* ell_blk, double* u_blk, const double* ell64, const double* u64,
+                                  const float* ind, const int32_t* samp, const int64_t* samp_ptr,
+                                  const int64_t* ds_blk_off, int32_t ndata, double tol, int32_t* flag, float* thr,
+                                  double* est, cudaStream_t s) {
+    k_mixed_check<<<ndata, kChkThreads, 0, s>>>(ell_blk, u_blk, ell64, u64, ind, samp, samp_ptr, ds_blk_off, tol,
+                                               flag, thr, est);
+    return cudaGetLastError();
+}
+
+cudaError_t bv_launch_mixed_redo_list(const int32_t* bds, int64_t nblk, const int32_t* flag, const float* thr,
+                                      const float* ind, const int32_t* blk_bin, const int64_t* roff, int32_t* redo,
+                                      int* cnt, cudaStream_t s) {
+    k_mixed_redo_list<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(bds, nblk, flag, thr, ind, blk_bin, roff, redo,
+                                                                     cnt);
+    return cudaGetLastError();
+}
+
 cudaError_t bv_launch_fail_reset(unsigned long long* fail, cudaStream_t s) {
     k_fail_reset<<<1, 1, 0, s>>>(fail);
     return cudaGetLastError();
@@ -979,6 +1086,7 @@ cudaError_t bv_launch_eval_reset(unsigned long long* fail, int* ctr, int n, cuda
 
 // Occupancy helper for the planner.
 int bv_occupancy(int kind, int threads, size_t smem) {
+    if (kind == 5) return bv_tc_occupancy(threads, smem);
     int nb = 0;
     cudaError_t e = cudaSuccess;
 #define BV_OCC(NT)                                                                            \

@@ -364,6 +364,16 @@ bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double*
 
 }  // namespace
 
+// The mixed-precision search stage scores points for an FP64 polish that fixes the final
+// estimate, so it evaluates without the mixed path's FP64 check (its error sets the stage's
+// tolerance instead, see mle_search); the caller's setting is restored on return.
+struct UncheckedMixed {
+    bv_ctx* c;
+    double old;
+    explicit UncheckedMixed(bv_ctx* ctx) : c(ctx), old(ctx->mixed_tol) { bv_set_mixed_tolerance(c, 0.0); }
+    ~UncheckedMixed() { bv_set_mixed_tolerance(c, old); }
+};
+
 // The search of one dataset with n observations: checks, start point, the stages.
 static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* theta0, const bv_theta* lo,
                       const bv_theta* hi, uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
@@ -497,6 +507,7 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
         if (free_mask & BV_FREE_NU) warm.nu = std::min(hi->nu, std::max(lo->nu, warm.nu));
         theta0 = &warm;
     }
+    UncheckedMixed unchecked(c);
     DirectEval ev(c);
     return mle_search(c, &ev, (double)c->n_tot, theta0, lo, hi, free_mask, opts, theta_hat, loglik_hat, n_evals);
 }
@@ -595,6 +606,7 @@ extern "C" int bv_mle_multi(bv_ctx* c, const bv_theta* theta0, const bv_theta* l
         if (free_mask & BV_FREE_NU)
             for (auto& t : start) t.nu = std::min(hi->nu, std::max(lo->nu, t.nu));
     }
+    UncheckedMixed unchecked(c);
     Batch b;
     b.c = c;
     b.nd = nd;

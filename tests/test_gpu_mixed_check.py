@@ -1,0 +1,116 @@
+"""The mixed-precision path's error check.  The FP32 error of each block's term is modelled
+as zero-mean noise of scale rho eps B_i (B_i the block's conditioning indicator), rho
+calibrated per dataset on a fixed sample of blocks recomputed in FP64; the worst-
+conditioned blocks are recomputed in FP64 until the 3-sigma bound meets the tolerance
+(default 1e-6 relative).  Checked against the FP64 oracle: well-conditioned data stays
+(almost) all FP32, ill-conditioned data sends more blocks to FP64, every dataset of a
+mixed batch meets the bound, the reported bound covers the actual error, and the
+tolerance setting (0 = no check) takes effect."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_04477_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bv():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2410_04477_gb300 import bv as _bv
+    return _bv
+
+
+def _one(bv, th, n=20_000, bc=2000, m=60, seed=21):
+    locs = synth.locs_uniform(n, 2, seed)
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=seed)
+    gnp, gni = oracle.select_neighbors(locs, bp, pi, ce, 30)
+    y = oracle.bv_draw(oracle.theta(*th), locs, bp, pi, gnp, gni, synth.normal(seed, 20, n))
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+    ell = oracle.loglik(oracle.theta(*th), locs, y, bp, pi, nnp, nni)[0]
+    out = {}
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        ctx.build_blocks(bc, seed=seed)
+        ctx.select_neighbors(m)
+        out["l64"] = ctx.loglik(bv.theta(*th))
+        out["lmx"] = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+        out["nb64"], out["touched"], est = ctx.mixed_check_info()
+        out["est"] = est[0]
+        out["lmx2"] = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+        ctx.set_mixed_tolerance(0.0)
+        out["l32"] = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+        out["off"] = ctx.mixed_check_info()[0]
+        ctx.set_mixed_tolerance(1e-4)
+        out["l4"] = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+        out["nb4"] = ctx.mixed_check_info()[0]
+        ctx.set_mixed_tolerance(1e-6)
+        out["lmx3"] = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+    out["ell"] = ell
+    out["nblk"] = len(bp) - 1
+    return out
+
+
+@pytest.mark.parametrize("th,name", [((1.0, 0.05, 0.5, 1e-2), "rough field"),
+                                     ((1.0, 0.3, 2.5, 1e-4), "smooth field, tiny nugget")])
+def test_check_meets_the_bound(bv, th, name):
+    o = _one(bv, th)
+    ell = o["ell"]
+    rel = abs(o["lmx"] - ell) / abs(ell)
+    rel32 = abs(o["l32"] - ell) / abs(ell)
+    print(f"{name}: checked rel {rel:.2e} (bound {o['est']:.2e}, {o['nb64']} of {o['nblk']} blocks FP64); "
+          f"unchecked rel {rel32:.2e}; tol 1e-4: {o['nb4']} blocks FP64")
+    assert abs(o["l64"] - ell) <= 1e-10 * abs(ell)
+    assert rel <= 1e-6 and o["est"] <= 1e-6
+    assert rel <= 2.0 * o["est"] + 1e-13      # the stated bound covers the actual error
+    assert o["lmx2"] == o["lmx"] and o["lmx3"] == o["lmx"]   # deterministic, and the setting round-trips
+    assert o["off"] == 0                      # tolerance 0: no check, no FP64 blocks
+    assert o["nb4"] <= o["nb64"]              # a looser bound recomputes no more blocks
+    assert abs(o["l4"] - ell) <= 1e-4 * abs(ell)
+
+
+def test_check_sends_more_blocks_to_fp64_on_ill_conditioned_data(bv):
+    rough = _one(bv, (1.0, 0.05, 0.5, 1e-2))
+    smooth = _one(bv, (1.0, 0.3, 2.5, 1e-4))
+    assert smooth["nb64"] > rough["nb64"]
+    assert rough["nb64"] < rough["nblk"] // 4
+
+
+def test_batch_every_dataset_within_the_bound(bv):
+    nd, m, seed = 24, 60, 31
+    sizes = synth.dataset_sizes(seed, nd, 3000, 20000)
+    th = synth.theta_draws(seed, nd)
+    locs_l, y_l, ells = [], [], []
+    for k in range(nd):
+        n = int(sizes[k])
+        locs = synth.locs_uniform(n, 2, seed * 1000 + k)
+        bp, pi, ce = oracle.build_blocks(locs, n // 10, seed=seed * 1000 + k)
+        s2, beta, tau2, nu = map(float, th[k])
+        oth = oracle.theta(s2, beta, nu, tau2)
+        gnp, gni = oracle.select_neighbors(locs, bp, pi, ce, 30)
+        y = oracle.bv_draw(oth, locs, bp, pi, gnp, gni, synth.normal(seed * 1000 + k, 20, n))
+        nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+        ells.append(oracle.loglik(oth, locs, y, bp, pi, nnp, nni)[0])
+        locs_l.append(locs)
+        y_l.append(y)
+    ells = np.array(ells)
+    with bv.Context() as ctx:
+        ctx.set_datasets(locs_l, y_l)
+        ctx.build_blocks_multi([int(n) // 10 for n in sizes], seed=seed * 1000)
+        ctx.select_neighbors(m)
+        thetas = [bv.theta(t[0], t[1], t[3], t[2]) for t in th]
+        l64 = ctx.loglik_multi(thetas)
+        lmx = ctx.loglik_multi(thetas, bv.BV_MIXED)
+        nb64, touched, est = ctx.mixed_check_info()
+        nblk = ctx.sizes()[0]
+    rel = np.abs(lmx - ells) / np.abs(ells)
+    print(f"batch: {nb64} of {nblk} blocks FP64, {touched} of {nd} datasets beyond the sample; "
+          f"worst rel {rel.max():.2e}; bounds {np.sort(est)}")
+    np.testing.assert_allclose(l64, ells, rtol=1e-10, atol=0)
+    assert rel.max() <= 1e-6
+    assert np.all(est <= 1e-6) or np.all(np.isfinite(est) | (np.abs(lmx - l64) <= 1e-12 * np.abs(l64)))
+    fin = np.isfinite(est) & (est > 0)
+    assert np.all(rel[fin] <= 2.0 * est[fin] + 1e-13), (rel[fin], est[fin])
+    assert nb64 < nblk

@@ -151,7 +151,7 @@ def test_loglik_mixed_precision_bound(bv):
     assert abs(ll64 - llo) <= REL64 * abs(llo)
     rel = abs(llm - llo) / abs(llo)
     # mixed precision: FP32 covariance/updates; stated bound for this configuration
-    assert rel < 1e-4, rel
+    assert rel <= 1e-6, (rel, abs(llm - llo))
 
 
 def test_singletons_and_no_neighbours(bv):
@@ -277,8 +277,9 @@ def test_mixed_precision_per_block(bv, d, m, bc, ranges):
     llo, per_o, _ = oracle.loglik(th, locs, y, *os_)
     Ns = np.diff(os_[0]) + np.diff(os_[2])
     assert set(Ns % 4) == {0, 1, 2, 3}
-    np.testing.assert_allclose(per, per_o, rtol=0, atol=2e-2)
-    assert abs(llm - llo) <= 1e-4 * abs(llo), (llm, llo)
+    # sampled blocks carry their FP64 terms, the others FP32-level errors
+    np.testing.assert_allclose(per, per_o, rtol=1e-5, atol=5e-3)
+    assert abs(llm - llo) <= 1e-6 * abs(llo), (llm, llo, abs(llm - llo))
 
 
 @pytest.mark.parametrize("n,d,m,seed", [(3000, 2, 30, 0), (1500, 3, 60, 1)])
@@ -355,4 +356,4 @@ def test_mixed_precision_fp64_fallback(bv):
     assert abs(l64 - lo) <= 1e-7 * abs(lo)
     assert nfb > 0 and nfb_easy == 0
     assert np.all(np.isfinite(per_mx)) and st == 0
-    assert abs(lmx - l64) <= 1e-2 * abs(l64), (lmx, l64, nfb)
+    assert abs(lmx - l64) <= 1e-6 * abs(l64), (lmx, l64, nfb)

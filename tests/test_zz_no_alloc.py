@@ -143,7 +143,13 @@ def test_noalloc_not_positive_definite():
     per = torch.zeros(len(bp) - 1, dtype=torch.float64, device="cuda")
     assert _call(bv, bv.theta(*th), dev, n, 2, len(bp) - 1, out, per) == bv.BV_ENOTPD
     assert out.item() == -np.inf and per[0].item() == -np.inf
-    assert np.isfinite(per[1:].cpu().numpy()).all()
+    # the same blocks fail as in the oracle (later blocks that condition on both copies of
+    # the site fail too); the others agree to 1e-9
+    got = per.cpu().numpy()
+    np.testing.assert_array_equal(np.isinf(got), np.isinf(per_o))
+    ok = np.isfinite(per_o)
+    assert ok.sum() > len(per_o) // 2
+    np.testing.assert_allclose(got[ok], per_o[ok], rtol=1e-9, atol=1e-9)
     # the next call with a nugget is fine: the failure word was reset
     th2 = (1.0, 0.1, 1.5, 1e-3)
     assert _call(bv, bv.theta(*th2), dev, n, 2, len(bp) - 1, out) == bv.BV_OK
