@@ -375,6 +375,8 @@ def config_of(w, args):
     else:
         c.update(n=w["n"], bc=w["bc"], nu=w["nu"], sigma2=w["sigma2"], nugget=w["nugget"],
                  range=w.get("ranges") or w["beta"])
+        if "n_scale" in w:
+            c.update(n_scale=w["n_scale"])
     return c
 
 
@@ -407,7 +409,8 @@ def run_mle(bv, ctx, w, log):
         res["warm_start_nu_class"] = ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu  # truth: w["nu"]
     # initial simplex scale: 0.5 in log-parameters from the fixed cold start; from the
     # learned warm start its validation RMSE (0.2 for log sigma^2 and log beta, 0.75 for
-    # log tau^2, weights/warmstart.json)
+    # log tau^2, weights/warmstart.json), which starts with Newton steps (the simplex search
+    # only if they fail)
     for pname, prec in (("fp64", bv.BV_FP64), ("mixed", bv.BV_MIXED)):
         for sname, th0, step, stepn in (("cold", cold0, 0.5, 0.5), ("warm", warm0, 0.2, 0.75)):
             if th0 is None:
@@ -415,7 +418,7 @@ def run_mle(bv, ctx, w, log):
             ctx.loglik(th0, prec)   # plan, tune and capture outside the timed MLE
             t0 = time.perf_counter()
             th, ll, ne = ctx.mle(th0, lo, hi, precision=prec, ftol_rel=1e-10, xtol=1e-5, max_evals=2000,
-                                 init_step=step, init_step_nugget=stepn)
+                                 init_step=step, init_step_nugget=stepn, newton_first=(sname == "warm"))
             el = time.perf_counter() - t0
             if sname == "warm":
                 el += res.get("warm_predict_s", 0.0)
@@ -746,12 +749,24 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-extras", action="store_true", help="skip the other-precision line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--n-scale", type=float, default=1.0,
+                    help="scale n and bc (3D: the number of sites) by this factor, keeping the block and "
+                         "conditioning sizes; for profiling a smaller case of the same kernel shapes")
     ap.add_argument("--no-mle", action="store_true",
                     help="skip the MLE wall-time extras (n=5e5 MLE, cold/warm x FP64/mixed) of the default run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     w = dict(WORKLOADS[args.workload])
+    if args.n_scale != 1.0 and "n" in w and "bc" in w:
+        f = args.n_scale
+        if "sites" in w:
+            w["sites"] = max(1, int(round(w["sites"] * f)))
+            w["n"] = w["sites"] * w["levels"]
+        else:
+            w["n"] = max(1, int(round(w["n"] * f)))
+        w["bc"] = max(1, int(round(w["bc"] * f)))
+        w["n_scale"] = f
     if w.get("kind") == "kl":
         log = (lambda s: print(s, file=sys.stderr, flush=True)) if _dist()[1] == 0 else (lambda s: None)
         return run_kl(args, w, log)

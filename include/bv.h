@@ -232,16 +232,17 @@ int bv_loglik_async(bv_ctx* ctx, const bv_theta* thetas, int32_t precision,
 int bv_mixed_fallbacks(bv_ctx* ctx, int64_t* count);
 
 /* The error check of the last mixed-precision evaluation.  The FP32 error of a block's
- * term is modelled as r_i eps B_i: eps = 2^-24, B_i the block's conditioning indicator
+ * term is modelled as r_i eps B_i: eps = 2^-24, B_i the block's error weight
  * (bv_mixed_block_indicator) and r_i independent, zero-mean, of a scale rho that depends
  * on the dataset.  Every dataset recomputes a fixed sample of its blocks in FP64 (all
  * blocks of a dataset with fewer than 64; else max(64, ceil(B/256)) of its B blocks at
  * evenly spaced positions of the random block order); the sample gives rho (the RMS of
  * delta_i / (eps B_i), delta_i the FP32 minus FP64 term), a test for a systematic bias
- * (|mean| over 4 standard errors: the whole dataset is recomputed in FP64) and the
- * log-likelihood estimate L (B times the mean FP64 term).  The bound on the dataset's
- * relative error is 3 x 1.2 rho eps sqrt(sum B_i^2) / |L| over the blocks still in FP32
- * (three standard deviations, a 20% margin for the sampled rho); while it exceeds the
+ * (|mean| over 4 standard errors: the whole dataset is recomputed in FP64); L is the sum
+ * of the dataset's terms (FP32 and sampled FP64).  The bound on the dataset's relative
+ * error is eps (|mean r| sum B_i + 3 x 1.25 rho sqrt(sum B_i^2)) / |L| over the blocks
+ * still in FP32 (the bias the sample shows plus three standard deviations of the noise,
+ * a 25% margin on the sampled rho); while it exceeds the
  * tolerance (bv_set_mixed_tolerance, default 1e-6) the blocks with the largest B_i are
  * recomputed in FP64 in the same evaluation.  The sampled blocks always keep their FP64
  * terms.  Outputs: *blocks_fp64 = blocks whose terms came from FP64 (sampled and
@@ -257,11 +258,13 @@ int bv_mixed_check_info(bv_ctx* ctx, int64_t* blocks_fp64, int32_t* datasets_tou
  * FP64).  Takes effect at the next evaluation.  BV_EINVAL unless 0 <= tol < 1. */
 int bv_set_mixed_tolerance(bv_ctx* ctx, double tol);
 
-/* Per-block conditioning indicator of the last mixed-precision evaluation (nblocks
- * floats): the sum over the block's N = m_i + b_i pivots of its FP32 factorisation of
- * (sigma^2 + tau^2) / pivot, i.e. of each point's variance over its conditional variance
- * given the points before it.  The FP32 rounding error of the block's term grows with
- * it.  Synchronous.  BV_ESTATE before the first mixed evaluation. */
+/* Per-block error weight of the last mixed-precision evaluation (nblocks floats): the
+ * block's conditioning indicator -- the sum over the N = m_i + b_i pivots of its FP32
+ * factorisation of (sigma^2 + tau^2) / pivot, i.e. of each point's variance over its
+ * conditional variance given the points before it -- times 1 + u_i / b_i (u_i the
+ * block's quadratic form).  The FP32 rounding error of the block's term grows with it;
+ * 0 for a block recomputed in FP64 after an FP32 breakdown.  Synchronous.  BV_ESTATE
+ * before the first mixed evaluation. */
 int bv_mixed_block_indicator(bv_ctx* ctx, float* out);
 
 /* First failing block (not positive definite) of the last synchronous evaluation, or -1. */
@@ -365,6 +368,13 @@ typedef struct bv_mle_opts {
                                 with sigma^2 profiled, log(tau^2 / sigma^2) (0: same as
                                 init_step); the nugget is the least identified parameter,
                                 so a start point can be much surer of sigma^2 and beta */
+    int32_t newton_first;  /* 1: start with Newton steps on a central-difference quadratic
+                              model (steps up to 0.5 in log units, up to 12 iterations, in
+                              FP64) and run the Nelder-Mead search only if they fail
+                              (the model not convex, a step not improving); for a start
+                              already near the optimum, such as the learned warm start.
+                              0: Nelder-Mead first                                      */
+    int32_t reserved;
 } bv_mle_opts;
 
 /* Maximise ell over log(sigma^2), log(beta), log(nu), log(tau^2) (free_mask selects) inside the

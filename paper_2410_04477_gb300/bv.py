@@ -53,7 +53,8 @@ class bv_theta(ctypes.Structure):
 class bv_mle_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_evals", ctypes.c_int32),
                 ("ftol_rel", ctypes.c_double), ("xtol", ctypes.c_double),
-                ("init_step", ctypes.c_double), ("init_step_nugget", ctypes.c_double)]
+                ("init_step", ctypes.c_double), ("init_step_nugget", ctypes.c_double),
+                ("newton_first", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def theta(sigma2=1.0, beta=0.1, nu=0.5, nugget=0.0, ranges=None) -> bv_theta:
@@ -528,8 +529,8 @@ class Context:
 
     def mle(self, th0: bv_theta, lo: bv_theta, hi: bv_theta,
             free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
-            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0):
-        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget)
+            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0, newton_first=False):
+        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget, int(newton_first), 0)
         out = bv_theta()
         ll = ctypes.c_double(0.0)
         ne = ctypes.c_int32(0)
@@ -540,11 +541,12 @@ class Context:
 
     def mle_multi(self, th0, lo: bv_theta, hi: bv_theta,
                   free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
-                  max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0):
+                  max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0,
+                  newton_first=False):
         """Every dataset's MLE with batched evaluations: (thetas, logliks, evals, statuses, batches).
         th0: a list of starts (one per dataset) or None for the learned warm start."""
         nd = self.ndata
-        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget)
+        o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget, int(newton_first), 0)
         starts = (bv_theta * nd)(*th0) if th0 is not None else None
         out = (bv_theta * nd)()
         ll = np.empty(nd)

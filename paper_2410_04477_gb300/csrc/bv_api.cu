@@ -842,6 +842,8 @@ static int build_check(bv_ctx* c, const std::vector<int>& Nof) {
         }
         sptr[ds + 1] = (int64_t)samp.size();
     }
+    // (the positions are fixed by (B, s) alone: the check kernel and the redo list
+    // recognise a sampled block from its position, bv_loglik.cu)
     k.nsamp = (int64_t)samp.size();
     std::vector<int64_t> roff(nbin + 1, 0);
     for (size_t b = 0; b < nbin; ++b) roff[b + 1] = roff[b] + (int64_t)all[b].size();
@@ -1048,7 +1050,7 @@ static int autotune(bv_ctx* c, int prec) {
         if (!only_cta && !only_tc && warp_ok)
             for (int t : {64, 128, 256}) cands.push_back({bp.kind == 1 ? 3 : 4, t});
         if (!only_cta && !only_warp && tc_ok)
-            for (int t : {256, 384, 512}) cands.push_back({5, t});
+            for (int t : {128, 256, 384, 512}) cands.push_back({5, t});
         int best_k = bp.kind, best_t = bp.threads;
         float best_ms = 1e30f;
         for (auto kt : cands) {
@@ -1144,8 +1146,8 @@ static int enqueue_check(bv_ctx* c, const LLArgs& a) {
     BV_CUDA(bv_launch_mixed_check(c->d_ell_blk, c->d_u_blk, k.d_ell, k.d_u, c->d_ind, k.d_samp, k.d_samp_ptr,
                                   c->d_ds_blk_off, c->ndata, c->mixed_tol, k.d_flag, k.d_thr, k.d_est, c->stream));
     BV_CUDA(cudaMemsetAsync(k.d_cnt, 0, sizeof(int) * BV_WCTR_PER_PREC, c->stream));
-    BV_CUDA(bv_launch_mixed_redo_list(c->d_bds, c->nblk, k.d_flag, k.d_thr, c->d_ind, k.d_blk_bin, k.d_roff, k.d_redo,
-                                      k.d_cnt, c->stream));
+    BV_CUDA(bv_launch_mixed_redo_list(c->d_bds, c->nblk, k.d_flag, k.d_thr, c->d_ind, k.d_samp_ptr, c->d_ds_blk_off,
+                                      k.d_blk_bin, k.d_roff, k.d_redo, k.d_cnt, c->stream));
     return fork_bins(c, k.rbins, a64, true);
 }
 

@@ -165,8 +165,9 @@ cudaError_t bv_launch_mixed_check(double* ell_blk, double* u_blk, const double* 
                                   double* est, cudaStream_t s);
 // Queue every block the check sends back on the FP64 redo list of its bin.
 cudaError_t bv_launch_mixed_redo_list(const int32_t* bds, int64_t nblk, const int32_t* flag, const float* thr,
-                                      const float* ind, const int32_t* blk_bin, const int64_t* roff, int32_t* redo,
-                                      int* cnt, cudaStream_t s);
+                                      const float* ind, const int64_t* samp_ptr, const int64_t* ds_blk_off,
+                                      const int32_t* blk_bin, const int64_t* roff, int32_t* redo, int* cnt,
+                                      cudaStream_t s);
 // Builds every general-nu dataset's Matern table (bv_device.cuh) from the device thetas.
 cudaError_t bv_launch_gtab(const DevTheta* theta, int32_t ndata, double* gtab, cudaStream_t s);
 #define BV_GTAB_DOUBLES 931  // GTAB_NOCT * GTAB_DEG

@@ -74,6 +74,9 @@ __device__ __forceinline__ int work_count(const LLArgs& a) {
 
 // A block whose FP32 factorisation breaks down (non-positive pivot) is queued for the FP64
 // fallback pass instead of failing the evaluation.
+// With the mixed path's check, the block's error weight: its conditioning indicator
+// (written by the same thread before) times 1 + u_i / b_i, since the quadratic form's
+// rounding error grows with the form itself; 0 for a block recomputed in FP64.
 __device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, double s, double su, int failed) {
     double ell = -0.5 * (s + (double)b * kLog2Pi);
     if (failed || !(ell == ell)) {
@@ -81,6 +84,8 @@ __device__ __forceinline__ void finish_block(const LLArgs& a, int blk, int b, do
         if (a.fb) a.fb[1 + atomicAdd(a.fb, 1)] = blk;
         else record_fail(a.fail, blk);
         if (a.ind_blk) a.ind_blk[blk] = 0.0f;  // recomputed in FP64: exact for the check
+    } else if (a.ind_blk) {
+        a.ind_blk[blk] = (float)((double)a.ind_blk[blk] * (1.0 + su / (double)(b > 0 ? b : 1)));
     }
     a.ell_blk[blk] = ell;
     a.u_blk[blk] = su;

@@ -758,21 +758,24 @@ __global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64
 
 // ---------------------------------------------------------------------------------
 // Mixed precision's error check.  Model: the FP32 error of block i's term is
-// delta_i = r_i eps B_i, eps = 2^-24 and B_i the block's conditioning indicator (the sum
-// over its pivots of variance / conditional variance), with r_i independent, zero mean and
-// of a scale rho that depends on the dataset.  Per dataset (one CTA):
+// delta_i = r_i eps w_i, eps = 2^-24 and w_i the block's error weight (its conditioning
+// indicator, the sum over its pivots of variance / conditional variance, times
+// 1 + u_i / b_i), with r_i independent, zero mean and of a scale rho that depends on the
+// dataset.  Per dataset (one CTA):
 //   1. on the fixed sample of blocks (evenly spaced positions in the random block order),
-//      recomputed in FP64: rho^2 = mean r_i^2, the mean of r_i and its z-score, and the
-//      log-likelihood estimate L = B mean(ell_i(FP64)); the sampled blocks take their FP64
-//      terms;
-//   2. the bound on the dataset's error is 3 (1.2 rho) eps sqrt(sum B_i^2) over the blocks
-//      still in FP32 (3 standard deviations, with a 20% margin for the sampled rho);
-//   3. if a bias shows (|z| > 4) every block is recomputed in FP64 (flag 2); else if the
-//      bound exceeds tol |L|, the blocks with the largest B_i are recomputed in FP64 until
-//      it does not: the largest threshold B* (bisection on log2 B*, 16 steps) with the bound
-//      over {B_i <= B*} within tol |L| (flag 1, thr = B*).
+//      recomputed in FP64: rho^2 = mean r_i^2, the mean of r_i and its z-score; the
+//      sampled blocks take their FP64 terms;
+//   2. the dataset's log-likelihood L is the sum of all its terms (FP32 and sampled FP64;
+//      its own error is the quantity bounded, far below |L|);
+//   3. the bound on the dataset's error is eps (|mean r| sum w_i + 3 (1.25 rho)
+//      sqrt(sum w_i^2)) over the blocks still in FP32: the bias the sample shows plus
+//      3 standard deviations of the noise, with a 25% margin on the sampled rho;
+//   4. if a bias shows (|z| > 4) every block is recomputed in FP64 (flag 2); else if the
+//      bound exceeds tol |L|, the blocks with the largest w_i are recomputed in FP64 until
+//      it does not: the largest threshold w* (bisection on log2 w*, 16 steps) with the bound
+//      over {w_i <= w*} within tol |L| (flag 1, thr = w*).
 // Fixed-order sums throughout: the decision is deterministic.  Blocks that the FP32-failure
-// fallback already recomputed carry B_i = 0 and count as exact.
+// fallback already recomputed carry w_i = 0 and count as exact.
 // ---------------------------------------------------------------------------------
 constexpr int kChkThreads = 256;
 constexpr float kEps32 = 5.9604644775390625e-8f;  // 2^-24
@@ -797,15 +800,21 @@ __device__ __forceinline__ double cta_sum(double v, double* sh, int tid) {
     return r;
 }
 
-// Sum of B_i^2 over the dataset's FP32 blocks with B_i <= thr.
-__device__ __forceinline__ double kept_b2(const float* ind, int64_t lo, int64_t B, int64_t s, float thr, double* sh,
-                                          int tid) {
-    double acc = 0.0;
+// The bound on the error of the dataset's FP32 blocks with w_i <= thr, in units of eps:
+// |mean r| sum w_i (the bias the sample shows) + 3 rho' sqrt(sum w_i^2) (the noise).
+__device__ __forceinline__ double kept_bound(const float* ind, int64_t lo, int64_t B, int64_t s, float thr,
+                                             double mu, double rho, double* sh, int tid) {
+    double a1 = 0.0, a2 = 0.0;
     for (int64_t j = tid; j < B; j += kChkThreads) {
         const float b = ind[lo + j];
-        if (b > 0.0f && b <= thr && !is_sampled(j, B, s)) acc += (double)b * (double)b;
+        if (b > 0.0f && b <= thr && !is_sampled(j, B, s)) {
+            a1 += (double)b;
+            a2 += (double)b * (double)b;
+        }
     }
-    return cta_sum(acc, sh, tid);
+    a1 = cta_sum(a1, sh, tid);
+    a2 = cta_sum(a2, sh, tid);
+    return fabs(mu) * a1 + 3.0 * rho * sqrt(a2);
 }
 
 __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, double* u_blk, const double* ell64,
@@ -817,13 +826,12 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
     const int ds = blockIdx.x, tid = threadIdx.x;
     const int64_t s0 = samp_ptr[ds], s1 = samp_ptr[ds + 1], lo = ds_off[ds];
     const int64_t B = ds_off[ds + 1] - lo, s = s1 - s0;
-    double r1 = 0.0, r2 = 0.0, e = 0.0, cnt = 0.0, bad = 0.0;
+    double r1 = 0.0, r2 = 0.0, cnt = 0.0, bad = 0.0;
     for (int64_t j = s0 + tid; j < s1; j += kChkThreads) {
         const int blk = samp[j];
         const double x64 = ell64[blk], x32 = ell_blk[blk];
         const float b = ind[blk];
         if (!(x64 > -INFINITY) || !(x64 < INFINITY)) bad += 1.0;
-        e += x64;
         if (b > 0.0f && b < INFINITY) {
             const double r = (x32 - x64) / ((double)kEps32 * (double)b);
             r1 += r;
@@ -835,37 +843,40 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
     }
     r1 = cta_sum(r1, sh, tid);
     r2 = cta_sum(r2, sh, tid);
-    e = cta_sum(e, sh, tid);
     cnt = cta_sum(cnt, sh, tid);
     bad = cta_sum(bad, sh, tid);
+    double e = 0.0;  // the dataset's ell (after the sampled blocks took their FP64 terms)
+    for (int64_t j = tid; j < B; j += kChkThreads) e += ell_blk[lo + j];
+    e = cta_sum(e, sh, tid);
     int f = 0;
     float t = INFINITY;
     double bound = 0.0;
     if (bad > 0.0) {
         bound = INFINITY;  // a block fails in FP64 too: the dataset's ell is -inf either way
-    } else if (s < B && cnt > 1.0) {
-        const double rho = sqrt(r2 / cnt), mu = r1 / cnt;
+    } else if (s < B && cnt < 2.0) {
+        f = 2;  // too few FP32 blocks in the sample to calibrate rho: all to FP64
+        bound = INFINITY;
+    } else if (s < B) {
+        const double rho = 1.25 * sqrt(r2 / cnt), mu = r1 / cnt;  // 25% margin on the sampled scale
         const double sd_mu = sqrt(fmax(r2 / cnt - mu * mu, 0.0) / cnt);
-        const double L = fabs((double)B * e / (double)s);
-        const double k = 3.0 * 1.2 * rho * (double)kEps32 / L;  // bound = k sqrt(S)
+        const double L = fabs(e);
+        const double k = (double)kEps32 / L;  // bound = k kept_bound
         if (!(fabs(mu) <= 4.0 * sd_mu + 1e-300) || !(L > 0.0)) {
             f = 2;
             bound = INFINITY;
         } else {
-            const double S = kept_b2(ind, lo, B, s, INFINITY, sh, tid);
-            bound = k * sqrt(S);
+            bound = k * kept_bound(ind, lo, B, s, INFINITY, mu, rho, sh, tid);
             if (!(bound <= tol)) {
                 // largest log2 threshold in [0, 48] whose kept blocks meet the bound
                 float a = 0.0f, c = 48.0f;
                 for (int it = 0; it < 16; ++it) {
                     const float mid = 0.5f * (a + c);
-                    const double Sm = kept_b2(ind, lo, B, s, exp2f(mid), sh, tid);
-                    if (k * sqrt(Sm) <= tol) a = mid;
+                    if (k * kept_bound(ind, lo, B, s, exp2f(mid), mu, rho, sh, tid) <= tol) a = mid;
                     else c = mid;
                 }
                 f = 1;
                 t = exp2f(a);
-                bound = k * sqrt(kept_b2(ind, lo, B, s, t, sh, tid));
+                bound = k * kept_bound(ind, lo, B, s, t, mu, rho, sh, tid);
             }
         }
     }
@@ -880,6 +891,7 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
 // dataset with flag 2, those with B_i above the dataset's threshold with flag 1.
 __global__ void k_mixed_redo_list(const int32_t* __restrict__ bds, int64_t nblk, const int32_t* __restrict__ flag,
                                   const float* __restrict__ thr, const float* __restrict__ ind,
+                                  const int64_t* __restrict__ samp_ptr, const int64_t* __restrict__ ds_off,
                                   const int32_t* __restrict__ blk_bin, const int64_t* __restrict__ roff,
                                   int32_t* __restrict__ redo, int* cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -887,6 +899,8 @@ __global__ void k_mixed_redo_list(const int32_t* __restrict__ bds, int64_t nblk,
     const int ds = bds[i];
     const int f = flag[ds];
     if (f == 0 || (f == 1 && !(ind[i] > thr[ds]))) return;
+    const int64_t lo = ds_off[ds];
+    if (is_sampled(i - lo, ds_off[ds + 1] - lo, samp_ptr[ds + 1] - samp_ptr[ds])) return;  // FP64 already
     const int b = blk_bin[i];
     const int pos = atomicAdd(cnt + b, 1);
     redo[roff[b] + pos] = (int32_t)i;
@@ -1067,10 +1081,11 @@ cudaError_t bv_launch_mixed_check(double* ell_blk, double* u_blk, const double* 
 }
 
 cudaError_t bv_launch_mixed_redo_list(const int32_t* bds, int64_t nblk, const int32_t* flag, const float* thr,
-                                      const float* ind, const int32_t* blk_bin, const int64_t* roff, int32_t* redo,
-                                      int* cnt, cudaStream_t s) {
-    k_mixed_redo_list<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(bds, nblk, flag, thr, ind, blk_bin, roff, redo,
-                                                                     cnt);
+                                      const float* ind, const int64_t* samp_ptr, const int64_t* ds_blk_off,
+                                      const int32_t* blk_bin, const int64_t* roff, int32_t* redo, int* cnt,
+                                      cudaStream_t s) {
+    k_mixed_redo_list<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(bds, nblk, flag, thr, ind, samp_ptr, ds_blk_off,
+                                                                     blk_bin, roff, redo, cnt);
     return cudaGetLastError();
 }
 

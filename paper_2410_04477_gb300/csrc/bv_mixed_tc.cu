@@ -150,10 +150,20 @@ __device__ __forceinline__ void diag_factor(float* tile, float* Lp, float* rs, f
     float a[kE];
 #pragma unroll
     for (int c = 0; c < kE; ++c) a[c] = tile[toff(r, c)];
+    // Column c's update uses the unscaled column: a_ri -= (a_rc / p_c) a_ic, so the
+    // broadcasts of a_ic do not wait for the pivot's reciprocal square root; the column is
+    // scaled by 1/sqrt(p_c) afterwards, off the chain from one pivot to the next.
 #pragma unroll
     for (int c = 0; c < kE; ++c) {
         if (c < nc) {  // warp-uniform
+            float col[kE];
+#pragma unroll
+            for (int i = c + 1; i < kE; ++i) col[i] = __shfl_sync(0xffffffffu, a[c], i);
             const float pc = __shfl_sync(0xffffffffu, a[c], c);
+            const float t = a[c] * __frcp_rn(pc);
+#pragma unroll
+            for (int i = c + 1; i < kE; ++i)
+                if (r >= i) a[i] = fmaf(-t, col[i], a[i]);
             const float rc = rsqrtf(pc);
             if (lane == c) {
                 piv[k0 + c] = pc;
@@ -161,11 +171,6 @@ __device__ __forceinline__ void diag_factor(float* tile, float* Lp, float* rs, f
                 if (!(pc > 0.0f) || !(pc < INFINITY)) *fail = 1;
             }
             if (r > c) a[c] *= rc;
-#pragma unroll
-            for (int i = c + 1; i < kE; ++i) {
-                const float lic = __shfl_sync(0xffffffffu, a[c], i);
-                if (r >= i) a[i] = fmaf(-a[c], lic, a[i]);
-            }
         }
     }
     if (lane < kE) {

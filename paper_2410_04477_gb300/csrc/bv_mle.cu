@@ -310,16 +310,16 @@ bool newton_step(std::vector<double> H, const std::vector<double>& g, int n, std
 
 // Newton polish of f from x (f(x) = fx) on a central-difference quadratic model with
 // step h: gradient and Hessian from 1 + 2n + n(n-1)/2 evaluations, a Newton step (at
-// most 0.1 in the sup norm), repeated while it improves f.  True when the last step was
+// most `cap` in the sup norm), repeated while it improves f (at most `iters` times).  True when the last step was
 // within xtol or the model's predicted decrease g^T H^-1 g / 2 was within ftol |f| (the
 // rounding floor of f bounds how well a weakly identified direction can be resolved);
 // false when the model was not convex, a point left the box, a step did not improve f,
 // or the iterations ran out (the caller then falls back to Nelder-Mead).
 bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double* fx, double h, double xtol,
-                   double ftol, int max_evals) {
+                   double ftol, int max_evals, double cap = 0.1, int iters = 4) {
     const int n = S.dim;
     std::vector<double> H(n * n), g(n), fp(n), fm(n), p, y;
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < iters; ++it) {
         if (f.evals + 2 + n * (n + 3) / 2 > max_evals) return false;
         for (int i = 0; i < n; ++i) {
             y = *x;
@@ -346,7 +346,7 @@ bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double*
             len = std::max(len, fabs(p[i]));
             pred -= 0.5 * g[i] * p[i];
         }
-        const double sc = len > 0.1 ? 0.1 / len : 1.0;
+        const double sc = len > cap ? cap / len : 1.0;
         y = *x;
         for (int i = 0; i < n; ++i) y[i] += sc * p[i];
         const double fy = f(y);
@@ -446,9 +446,32 @@ static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* th
             ftol_c = std::max(ftol_c, 10.0 * err);
         }
         obj.reset(prec);
-        BV_TRY(nelder_mead(obj, S, x, s0, sn, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
-        const double s1 = std::max(s0 * 0.1, 20.0 * xtol_c);
-        BV_TRY(nelder_mead(obj, S, xb, s1, s1, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
+        // a start near the optimum: Newton steps first (in FP64, whose finite differences
+        // the model needs), the simplex search only if they fail
+        bool near = false;
+        if (opts->newton_first) {
+            obj.reset(BV_FP64);
+            double fx = obj(x);
+            BV_TRY(obj.hard_error);
+            std::vector<double> xn = x;
+            near = std::isfinite(fx) && newton_polish(obj, S, &xn, &fx, 1e-3, xtol_c, ftol_c, opts->max_evals, 0.5, 12);
+            BV_TRY(obj.hard_error);
+            if (near) {
+                xb = xn;
+                fb = fx;
+            } else {
+                x = obj.xbest;  // continue from the best point the steps reached
+                obj.reset(prec);
+            }
+            if (getenv("BV_LOG_MLE"))
+                fprintf(stderr, "bv_mle: Newton-first start %s after %d evals\n", near ? "converged" : "failed",
+                        obj.evals);
+        }
+        if (!near) {
+            BV_TRY(nelder_mead(obj, S, x, s0, sn, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
+            const double s1 = std::max(s0 * 0.1, 20.0 * xtol_c);
+            BV_TRY(nelder_mead(obj, S, xb, s1, s1, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
+        }
         if (std::isfinite(fb)) {
             obj.reset(BV_FP64);
             fb = obj(xb);

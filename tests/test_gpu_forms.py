@@ -104,6 +104,7 @@ def test_tensor_core_form_matches_oracle(bv, case, monkeypatch):
         ctx.set_mixed_tolerance(0.0)          # FP32 throughout: the kernel's own arithmetic
         ll32, per32, _ = ctx.loglik(gth, bv.BV_MIXED, per_block=True)
         nfb = ctx.mixed_fallbacks()
+        w = ctx.mixed_block_indicator().astype(np.float64)
         ctx.set_mixed_tolerance(1e-6)
         llm = ctx.loglik(gth, bv.BV_MIXED)
         info = ctx.plan_info(bv.BV_MIXED)
@@ -114,6 +115,9 @@ def test_tensor_core_form_matches_oracle(bv, case, monkeypatch):
     assert Ns.max() >= 64
     ok = np.isfinite(per32)
     assert ok.all() or nfb > 0
-    np.testing.assert_allclose(per32, per_ref, rtol=1e-3, atol=1e-3)
+    # every block within the FP32 error its weight predicts (measured |delta_i| / (eps w_i)
+    # stays below about 5 on the benchmark workloads)
+    err = np.abs(per32 - per_ref)
+    assert np.all(err <= 8.0 * 2.0 ** -24 * w + 1e-9), (err / (2.0 ** -24 * np.maximum(w, 1e-30))).max()
     assert abs(ll32 - ref) <= 1e-4 * abs(ref)
     assert abs(llm - ref) <= 1e-6 * abs(ref)
