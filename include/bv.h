@@ -240,9 +240,9 @@ int bv_mixed_fallbacks(bv_ctx* ctx, int64_t* count);
  * delta_i / (eps B_i), delta_i the FP32 minus FP64 term), a test for a systematic bias
  * (|mean| over 4 standard errors: the whole dataset is recomputed in FP64); L is the sum
  * of the dataset's terms (FP32 and sampled FP64).  The bound on the dataset's relative
- * error is eps (|mean r| sum B_i + 3 x 1.25 rho sqrt(sum B_i^2)) / |L| over the blocks
- * still in FP32 (the bias the sample shows plus three standard deviations of the noise,
- * a 25% margin on the sampled rho); while it exceeds the
+ * error is 3 x 1.5 rho eps sqrt(sum B_i^2) / |L| over the blocks still in FP32 (three
+ * standard deviations of their summed noise, a 50% margin on the sampled rho); while it
+ * exceeds the
  * tolerance (bv_set_mixed_tolerance, default 1e-6) the blocks with the largest B_i are
  * recomputed in FP64 in the same evaluation.  The sampled blocks always keep their FP64
  * terms.  Outputs: *blocks_fp64 = blocks whose terms came from FP64 (sampled and

@@ -1132,23 +1132,28 @@ static int fork_bins(bv_ctx* c, const std::vector<BinPlan>& bins, const LLArgs& 
 // The mixed path's error check (after the FP32 bins and their FP64 fallback): the sampled
 // blocks in FP64, the per-dataset test against kMixedTol, and the FP64 recomputation of
 // every block of a dataset that fails it.
-static int enqueue_check(bv_ctx* c, const LLArgs& a) {
-    auto& k = c->chk;
+static LLArgs check_args(bv_ctx* c, const LLArgs& a, bool sample) {
     LLArgs a64 = a;
     a64.fb = nullptr;
     a64.dyn = 0;
+    a64.ind_blk = nullptr;
     a64.ws = c->d_fb_ws;
     a64.ws_stride = c->fb_stride;
-    LLArgs as = a64;
-    as.ell_blk = k.d_ell;
-    as.u_blk = k.d_u;
-    BV_TRY(fork_bins(c, k.sbins, as, false));
+    if (sample) {
+        a64.ell_blk = c->chk.d_ell;
+        a64.u_blk = c->chk.d_u;
+    }
+    return a64;
+}
+
+static int enqueue_check(bv_ctx* c, const LLArgs& a) {
+    auto& k = c->chk;
     BV_CUDA(bv_launch_mixed_check(c->d_ell_blk, c->d_u_blk, k.d_ell, k.d_u, c->d_ind, k.d_samp, k.d_samp_ptr,
                                   c->d_ds_blk_off, c->ndata, c->mixed_tol, k.d_flag, k.d_thr, k.d_est, c->stream));
     BV_CUDA(cudaMemsetAsync(k.d_cnt, 0, sizeof(int) * BV_WCTR_PER_PREC, c->stream));
     BV_CUDA(bv_launch_mixed_redo_list(c->d_bds, c->nblk, k.d_flag, k.d_thr, c->d_ind, k.d_samp_ptr, c->d_ds_blk_off,
                                       k.d_blk_bin, k.d_roff, k.d_redo, k.d_cnt, c->stream));
-    return fork_bins(c, k.rbins, a64, true);
+    return fork_bins(c, k.rbins, check_args(c, a, false), true);
 }
 
 // The bins of one evaluation as parallel branches: failure reset, fork, every bin on its
@@ -1157,7 +1162,11 @@ static int enqueue_check(bv_ctx* c, const LLArgs& a) {
 // large bin leaves idle.
 static int enqueue_eval_forked(bv_ctx* c, int prec) {
     const size_t nb = c->plan[prec].size();
-    BV_TRY(ensure_side(c, nb));
+    // with the mixed check, its FP64 sample runs as further branches beside the bins: it
+    // needs only the inputs, and its latency hides behind theirs
+    const bool check = prec == BV_MIXED && c->mixed_tol > 0.0 && !c->chk.rbins.empty();
+    const size_t ns = check ? c->chk.sbins.size() : 0;
+    BV_TRY(ensure_side(c, nb + ns));
     BV_CUDA(bv_launch_eval_reset(c->d_fail, c->d_wctr, BV_WCTR_GROUPS * BV_WCTR_PER_PREC, c->stream));
     if (c->cur_gen) BV_CUDA(bv_launch_gtab(c->d_theta, c->ndata, c->d_gtab, c->stream));
     const bool fallback = prec == BV_MIXED && c->d_fb;
@@ -1166,23 +1175,20 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
     LLArgs a = make_args(c);
     if (fallback) a.fb = c->d_fb;
     if (prec == BV_MIXED) a.ind_blk = c->d_ind;
-    for (size_t i = 0; i < nb; ++i) {
+    for (size_t i = 0; i < nb + ns; ++i) {
         BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
-        BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
+        if (i < nb) BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
+        else BV_CUDA(bv_launch_bin(c->chk.sbins[i - nb], check_args(c, a, true), c->side[i]));
         BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
     }
-    for (size_t i = 0; i < nb; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
+    for (size_t i = 0; i < nb + ns; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
     if (fallback) {
         LLArgs fa = a;
         fa.ws = c->d_fb_ws;
         fa.ws_stride = c->fb_stride;
         BV_CUDA(bv_launch_fallback(fa, c->fb_slots, c->stream));
     }
-    if (prec == BV_MIXED && c->mixed_tol > 0.0 && !c->chk.rbins.empty()) {
-        LLArgs ac = a;
-        ac.ind_blk = nullptr;
-        BV_TRY(enqueue_check(c, ac));
-    }
+    if (check) BV_TRY(enqueue_check(c, a));
     BV_CUDA(bv_launch_reduce(c->d_ell_blk, c->d_u_blk, c->d_ds_blk_off, c->ndata, c->red_chunks, c->d_red_part,
                              c->d_out, c->d_quad, c->stream));
     return BV_OK;

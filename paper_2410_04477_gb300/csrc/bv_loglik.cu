@@ -767,9 +767,9 @@ __global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64
 //      sampled blocks take their FP64 terms;
 //   2. the dataset's log-likelihood L is the sum of all its terms (FP32 and sampled FP64;
 //      its own error is the quantity bounded, far below |L|);
-//   3. the bound on the dataset's error is eps (|mean r| sum w_i + 3 (1.25 rho)
-//      sqrt(sum w_i^2)) over the blocks still in FP32: the bias the sample shows plus
-//      3 standard deviations of the noise, with a 25% margin on the sampled rho;
+//   3. the bound on the dataset's error is 3 (1.5 rho) eps sqrt(sum w_i^2) over the blocks
+//      still in FP32: 3 standard deviations of their summed noise, with a 50% margin on
+//      the sampled rho (64 or more samples of a heavy-tailed r);
 //   4. if a bias shows (|z| > 4) every block is recomputed in FP64 (flag 2); else if the
 //      bound exceeds tol |L|, the blocks with the largest w_i are recomputed in FP64 until
 //      it does not: the largest threshold w* (bisection on log2 w*, 16 steps) with the bound
@@ -801,20 +801,16 @@ __device__ __forceinline__ double cta_sum(double v, double* sh, int tid) {
 }
 
 // The bound on the error of the dataset's FP32 blocks with w_i <= thr, in units of eps:
-// |mean r| sum w_i (the bias the sample shows) + 3 rho' sqrt(sum w_i^2) (the noise).
+// 3 rho' sqrt(sum w_i^2), three standard deviations of their summed noise.
 __device__ __forceinline__ double kept_bound(const float* ind, int64_t lo, int64_t B, int64_t s, float thr,
-                                             double mu, double rho, double* sh, int tid) {
-    double a1 = 0.0, a2 = 0.0;
+                                             double rho, double* sh, int tid) {
+    double a2 = 0.0;
     for (int64_t j = tid; j < B; j += kChkThreads) {
         const float b = ind[lo + j];
-        if (b > 0.0f && b <= thr && !is_sampled(j, B, s)) {
-            a1 += (double)b;
-            a2 += (double)b * (double)b;
-        }
+        if (b > 0.0f && b <= thr && !is_sampled(j, B, s)) a2 += (double)b * (double)b;
     }
-    a1 = cta_sum(a1, sh, tid);
     a2 = cta_sum(a2, sh, tid);
-    return fabs(mu) * a1 + 3.0 * rho * sqrt(a2);
+    return 3.0 * rho * sqrt(a2);
 }
 
 __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, double* u_blk, const double* ell64,
@@ -857,7 +853,7 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
         f = 2;  // too few FP32 blocks in the sample to calibrate rho: all to FP64
         bound = INFINITY;
     } else if (s < B) {
-        const double rho = 1.25 * sqrt(r2 / cnt), mu = r1 / cnt;  // 25% margin on the sampled scale
+        const double rho = 1.5 * sqrt(r2 / cnt), mu = r1 / cnt;  // 50% margin on the sampled scale
         const double sd_mu = sqrt(fmax(r2 / cnt - mu * mu, 0.0) / cnt);
         const double L = fabs(e);
         const double k = (double)kEps32 / L;  // bound = k kept_bound
@@ -865,18 +861,18 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
             f = 2;
             bound = INFINITY;
         } else {
-            bound = k * kept_bound(ind, lo, B, s, INFINITY, mu, rho, sh, tid);
+            bound = k * kept_bound(ind, lo, B, s, INFINITY, rho, sh, tid);
             if (!(bound <= tol)) {
                 // largest log2 threshold in [0, 48] whose kept blocks meet the bound
                 float a = 0.0f, c = 48.0f;
                 for (int it = 0; it < 16; ++it) {
                     const float mid = 0.5f * (a + c);
-                    if (k * kept_bound(ind, lo, B, s, exp2f(mid), mu, rho, sh, tid) <= tol) a = mid;
+                    if (k * kept_bound(ind, lo, B, s, exp2f(mid), rho, sh, tid) <= tol) a = mid;
                     else c = mid;
                 }
                 f = 1;
                 t = exp2f(a);
-                bound = k * kept_bound(ind, lo, B, s, t, mu, rho, sh, tid);
+                bound = k * kept_bound(ind, lo, B, s, t, rho, sh, tid);
             }
         }
     }

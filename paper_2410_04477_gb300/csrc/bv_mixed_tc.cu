@@ -77,32 +77,39 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// C -= X_I X_J^T for one 16 x 16 tile C (tile pointers into the tile array), by one warp.
-// A fragments (rows g, g+8; columns 2t, 2t+1 and 2t+8, 2t+9 of X_I) and B fragments
-// (rows h*8 + g of X_J, the same columns) are split into BF16 parts; the negated A parts
-// make the MMAs subtract.
-__device__ __forceinline__ void tile_update(float* C, const float* XI, const float* XJ, int lane) {
+// The A operand of C -= X_I X_J^T, split once for every tile of row I a warp updates: the
+// rows g, g+8 and columns 2t, 2t+1, 2t+8, 2t+9 of X_I, negated (so that the MMAs
+// subtract) and split into three BF16 parts, packed in pairs.
+struct AFrag {
+    uint32_t q[3][4];
+};
+
+__device__ __forceinline__ void load_a(const float* XI, int lane, AFrag& A) {
     const int g = lane >> 2, t = lane & 3;
-    uint32_t A[3][4];
-    {
-        float v[8];
-        const float2 p0 = *reinterpret_cast<const float2*>(XI + toff(g, 2 * t));
-        const float2 p1 = *reinterpret_cast<const float2*>(XI + toff(g + 8, 2 * t));
-        const float2 p2 = *reinterpret_cast<const float2*>(XI + toff(g, 2 * t + 8));
-        const float2 p3 = *reinterpret_cast<const float2*>(XI + toff(g + 8, 2 * t + 8));
-        v[0] = -p0.x; v[1] = -p0.y; v[2] = -p1.x; v[3] = -p1.y;
-        v[4] = -p2.x; v[5] = -p2.y; v[6] = -p3.x; v[7] = -p3.y;
-        float s[3][8];
+    float v[8];
+    const float2 p0 = *reinterpret_cast<const float2*>(XI + toff(g, 2 * t));
+    const float2 p1 = *reinterpret_cast<const float2*>(XI + toff(g + 8, 2 * t));
+    const float2 p2 = *reinterpret_cast<const float2*>(XI + toff(g, 2 * t + 8));
+    const float2 p3 = *reinterpret_cast<const float2*>(XI + toff(g + 8, 2 * t + 8));
+    v[0] = -p0.x; v[1] = -p0.y; v[2] = -p1.x; v[3] = -p1.y;
+    v[4] = -p2.x; v[5] = -p2.y; v[6] = -p3.x; v[7] = -p3.y;
+    float s[3][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) split3(v[e], s[0][e], s[1][e], s[2][e]);
+    for (int e = 0; e < 8; ++e) split3(v[e], s[0][e], s[1][e], s[2][e]);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            A[q][0] = pack_bf16(s[q][0], s[q][1]);
-            A[q][1] = pack_bf16(s[q][2], s[q][3]);
-            A[q][2] = pack_bf16(s[q][4], s[q][5]);
-            A[q][3] = pack_bf16(s[q][6], s[q][7]);
-        }
+    for (int q = 0; q < 3; ++q) {
+        A.q[q][0] = pack_bf16(s[q][0], s[q][1]);
+        A.q[q][1] = pack_bf16(s[q][2], s[q][3]);
+        A.q[q][2] = pack_bf16(s[q][4], s[q][5]);
+        A.q[q][3] = pack_bf16(s[q][6], s[q][7]);
     }
+}
+
+// C -= X_I X_J^T for one 16 x 16 tile C (tile pointers into the tile array), by one warp,
+// with X_I's fragments in A.  B fragments: rows h*8 + g of X_J, columns 2t, 2t+1 and
+// 2t+8, 2t+9, split the same way.
+__device__ __forceinline__ void tile_update_a(float* C, const AFrag& A, const float* XJ, int lane) {
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t B[3][2];
@@ -127,16 +134,22 @@ __device__ __forceinline__ void tile_update(float* C, const float* XI, const flo
         // FP32 afterwards: the tensor core's accumulation does not round C to nearest, so C
         // itself never enters it
         float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        mma_bf16(d, A[2], B[0][0], B[0][1]);
-        mma_bf16(d, A[1], B[1][0], B[1][1]);
-        mma_bf16(d, A[0], B[2][0], B[2][1]);
-        mma_bf16(d, A[1], B[0][0], B[0][1]);
-        mma_bf16(d, A[0], B[1][0], B[1][1]);
-        mma_bf16(d, A[0], B[0][0], B[0][1]);
+        mma_bf16(d, A.q[2], B[0][0], B[0][1]);
+        mma_bf16(d, A.q[1], B[1][0], B[1][1]);
+        mma_bf16(d, A.q[0], B[2][0], B[2][1]);
+        mma_bf16(d, A.q[1], B[0][0], B[0][1]);
+        mma_bf16(d, A.q[0], B[1][0], B[1][1]);
+        mma_bf16(d, A.q[0], B[0][0], B[0][1]);
         const float2 u = *c01, w = *c23;
         *c01 = make_float2(u.x + d[0], u.y + d[1]);
         *c23 = make_float2(w.x + d[2], w.y + d[3]);
     }
+}
+
+__device__ __forceinline__ void tile_update(float* C, const float* XI, const float* XJ, int lane) {
+    AFrag A;
+    load_a(XI, lane, A);
+    tile_update_a(C, A, XJ, lane);
 }
 
 // Factor the diagonal tile of panel p (warp 0, FP32, lane r < 16 holds row r): pivot
@@ -300,14 +313,13 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_tc(LLArgs a) {
             if (warp == 0) {
                 if (nc1 > 0) diag_factor(tiles + tc_tile(p1, p1) * kTF, Lp, rs, piv, k1, nc1, lane, &s_fail);
             } else {
-                const int S = T - p - 2;  // trailing tile rows/columns p+2 .. T-1
-                const int cnt = (S * (S + 1)) >> 1;
-                for (int f = warp - 1; f < cnt; f += NW - 1) {
-                    int ii, jj;
-                    tri_rc(f, ii, jj);
-                    const int I = p + 2 + ii, J = p + 2 + jj;
-                    tile_update(tiles + tc_tile(I, J) * kTF, tiles + tc_tile(I, p) * kTF,
-                                tiles + tc_tile(J, p) * kTF, lane);
+                // trailing tile rows p+2 .. T-1, each (with all its tiles J = p+2 .. I) owned
+                // by one warp, longest rows first, so that X_I is split once per row
+                for (int I = T - 1 - (warp - 1); I >= p + 2; I -= NW - 1) {
+                    AFrag A;
+                    load_a(tiles + tc_tile(I, p) * kTF, lane, A);
+                    for (int J = p + 2; J <= I; ++J)
+                        tile_update_a(tiles + tc_tile(I, J) * kTF, A, tiles + tc_tile(J, p) * kTF, lane);
                 }
             }
             __syncthreads();
