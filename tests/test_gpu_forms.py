@@ -51,7 +51,15 @@ def test_kernel_form_matches_oracle(bv, form, case, monkeypatch):
     oth = oracle.theta(*th)
     y = oracle.exact_draw(oth, locs, synth.normal(seed, 20, n))
     ll64, per64, llm, gs = _run(bv, locs, y, th, singletons, bc, m, seed)
-    ref, per_ref, _ = oracle.loglik(oth, locs, y, *gs)
+    # the oracle builds its own structure; the GPU's must equal it bit for bit
+    if singletons:
+        obp, opi, oce = oracle.build_singletons(locs, seed=seed)
+    else:
+        obp, opi, oce = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    onnp, onni = oracle.select_neighbors(locs, obp, opi, oce, m)
+    for a, b in zip(gs, (obp, opi, onnp, onni)):
+        np.testing.assert_array_equal(a, b)
+    ref, per_ref, _ = oracle.loglik(oth, locs, y, obp, opi, onnp, onni)
     assert abs(ll64 - ref) <= REL64 * abs(ref), (form, ll64, ref)
     np.testing.assert_allclose(per64, per_ref, rtol=1e-9, atol=1e-9)
     assert abs(llm - ref) <= 1e-6 * abs(ref), (form, llm, ref, abs(llm - ref))
@@ -108,7 +116,14 @@ def test_tensor_core_form_matches_oracle(bv, case, monkeypatch):
         ctx.set_mixed_tolerance(1e-6)
         llm = ctx.loglik(gth, bv.BV_MIXED)
         info = ctx.plan_info(bv.BV_MIXED)
-    ref, per_ref, _ = oracle.loglik(oth, locs, y, bp, pi, nnp, nni)
+    if singletons:
+        obp, opi, oce = oracle.build_singletons(locs, seed=seed)
+    else:
+        obp, opi, oce = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    onnp, onni = oracle.select_neighbors(locs, obp, opi, oce, m)
+    for a, b in zip((bp, pi, nnp, nni), (obp, opi, onnp, onni)):
+        np.testing.assert_array_equal(a, b)
+    ref, per_ref, _ = oracle.loglik(oth, locs, y, obp, opi, onnp, onni)
     Ns = np.diff(bp) + np.diff(nnp)
     print(f"tc form N {Ns.min()}..{Ns.max()}: unchecked rel {abs(ll32 - ref) / abs(ref):.2e}, "
           f"checked rel {abs(llm - ref) / abs(ref):.2e}, fallbacks {nfb}")

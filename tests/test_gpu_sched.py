@@ -36,7 +36,12 @@ def _setup(bv, n=3000, seed=11, bc=150, m=40):
     ctx.set_data(locs, y)
     bp, pi = ctx.build_blocks(bc, seed=seed, iters=20)
     nnp, nni = ctx.select_neighbors(m)
-    ref = [oracle.loglik(oracle.theta(*t), locs, y, bp, pi, nnp, nni)[0] for t in THETAS]
+    # the oracle's own structure, equal to the GPU's bit for bit
+    obp, opi, oce = oracle.build_blocks(locs, bc, seed=seed, iters=20)
+    onnp, onni = oracle.select_neighbors(locs, obp, opi, oce, m)
+    for a, b in zip((bp, pi, nnp, nni), (obp, opi, onnp, onni)):
+        np.testing.assert_array_equal(a, b)
+    ref = [oracle.loglik(oracle.theta(*t), locs, y, obp, opi, onnp, onni)[0] for t in THETAS]
     return ctx, ref
 
 
