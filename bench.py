@@ -407,10 +407,10 @@ def run_mle(bv, ctx, w, log):
         res["warm_predict_s"] = time.perf_counter() - t0
         res["warm_start_theta"] = [warm0.sigma2, warm0.range[0], warm0.nugget]
         res["warm_start_nu_class"] = ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu  # truth: w["nu"]
-    # initial simplex scale: 0.5 in log-parameters from the fixed cold start; from the
-    # learned warm start its validation RMSE (0.2 for log sigma^2 and log beta, 0.75 for
-    # log tau^2, weights/warmstart.json), which starts with Newton steps (the simplex search
-    # only if they fail)
+    # both starts run the same search (trust-region Newton steps first, the simplex search
+    # only if they fail); the simplex scale is 0.5 in log-parameters from the fixed cold
+    # start, and from the learned warm start its validation RMSE (0.2 for log sigma^2 and
+    # log beta, 0.75 for log tau^2, weights/warmstart.json)
     for pname, prec in (("fp64", bv.BV_FP64), ("mixed", bv.BV_MIXED)):
         for sname, th0, step, stepn in (("cold", cold0, 0.5, 0.5), ("warm", warm0, 0.2, 0.75)):
             if th0 is None:
@@ -418,7 +418,7 @@ def run_mle(bv, ctx, w, log):
             ctx.loglik(th0, prec)   # plan, tune and capture outside the timed MLE
             t0 = time.perf_counter()
             th, ll, ne = ctx.mle(th0, lo, hi, precision=prec, ftol_rel=1e-10, xtol=1e-5, max_evals=2000,
-                                 init_step=step, init_step_nugget=stepn, newton_first=(sname == "warm"))
+                                 init_step=step, init_step_nugget=stepn, newton_first=True)
             el = time.perf_counter() - t0
             if sname == "warm":
                 el += res.get("warm_predict_s", 0.0)
@@ -844,6 +844,13 @@ def main():
         ctx.autotune(other)
         n2 = min(args.steps, 30) if other == bv.BV_MIXED or nd > 1 else min(args.steps, 5)
         ms2 = time_device(torch, bv, ctx, stream, thetas, other, 3, n2, flush)
+        steps64, steps_ell = [], []
+        if other == bv.BV_MIXED:
+            # the check's FP64 share at each timed theta (untimed re-evaluations): the bound
+            # is relative to |ell|, so a theta where ell is small needs more FP64 blocks
+            for k in range(n2):
+                steps_ell.append(float(np.sum(ctx.loglik_multi(thetas[(3 + k) % len(thetas)], bv.BV_MIXED))))
+                steps64.append(int(ctx.mixed_check_info()[0]))
         llm = ctx.loglik_multi(base, bv.BV_MIXED)
         nb64, ntouched, est = ctx.mixed_check_info()
         rel = np.abs(llm - ll64) / np.abs(ll64)
@@ -858,6 +865,10 @@ def main():
             "check": {"bound": 1e-6, "blocks_fp64": int(nb64), "blocks": int(ctx.sizes()[0]),
                       "datasets_with_blocks_recomputed": int(ntouched), "datasets": int(nd),
                       "est_rel_err_max": float(est.max())}}
+        if steps64:
+            extras["other_precision"]["check"]["timed_steps"] = {
+                "blocks_fp64": steps64, "ell": steps_ell,
+                "mean_fraction_fp64": float(np.mean(steps64)) / int(ctx.sizes()[0])}
         if other == bv.BV_MIXED:
             # the same without the check: FP32 throughout (bv_set_mixed_tolerance(0))
             ctx.set_mixed_tolerance(0.0)

@@ -368,12 +368,15 @@ typedef struct bv_mle_opts {
                                 with sigma^2 profiled, log(tau^2 / sigma^2) (0: same as
                                 init_step); the nugget is the least identified parameter,
                                 so a start point can be much surer of sigma^2 and beta */
-    int32_t newton_first;  /* 1: start with Newton steps on a central-difference quadratic
-                              model (steps up to 0.5 in log units, up to 12 iterations, in
-                              FP64) and run the Nelder-Mead search only if they fail
-                              (the model not convex, a step not improving); for a start
-                              already near the optimum, such as the learned warm start.
-                              0: Nelder-Mead first                                      */
+    int32_t newton_first;  /* 1 (recommended): trust-region Newton iterations on a
+                              central-difference quadratic model from theta0 (radius 0.5
+                              in log units to start, up to 40 iterations; in FP64 to
+                              ftol_rel / xtol, in mixed precision to the coarse stage's
+                              tolerances and then an FP64 polish), the Nelder-Mead search
+                              only if they fail (no step lowers ell's negative, the
+                              iterations run out).  A start near the optimum, such as the
+                              learned warm start, converges in a few iterations.
+                              0: Nelder-Mead first, then the FP64 Newton polish          */
     int32_t reserved;
 } bv_mle_opts;
 
@@ -463,8 +466,9 @@ int bv_mle_multi(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const 
  *            (y_i - y_j)^2 / 2 (0 if the bin is empty), over a seeded subsample of
  *            min(n, max_points) points (point j kept when floor(r_j n / 2^64) < max_points,
  *            r_j = SplitMix64 draw j of stream seed);
- *   [32] log var(y); [33..36] block size mean, std, min, max; [37] mean conditioning
- *   size m_i; [38] nearest-neighbour semivariance: mean over subsample points i of
+ *   [32] log var(y); [33..37] block-size histogram: the fractions of the blocks with
+ *   b_i in 1-4, 5-8, 9-12, 13-16 and >= 17 points (the same at any n for a given n / bc);
+ *   [38] nearest-neighbour semivariance: mean over subsample points i of
  *   (y_i - y_nn(i))^2 / 2, divided by var(y), nn(i) the nearest other subsample point
  *   (squared distance without fused multiply-add, lowest index on ties); [39] 64 x the
  *   mean nearest-neighbour distance (in semivariogram-bin units).

@@ -22,8 +22,10 @@ BLOB = NPARAM + 2 * NFEAT + 6
 
 def features(locs, y, block_ptr, nn_ptr, max_points=10000, seed=0):
     """Semivariogram gamma_k / var(y) in 32 bins of width 1/64 on (0, 0.5] over a seeded
-    subsample, then log var(y), block-size mean/std/min/max, mean conditioning size, the
-    nearest-neighbour semivariance / var(y) and 64 x the mean nearest-neighbour distance."""
+    subsample, then log var(y), the fractions of blocks with 1-4, 5-8, 9-12, 13-16 and 17 or
+    more points, the nearest-neighbour semivariance / var(y) and 64 x the mean
+    nearest-neighbour distance.  (nn_ptr is accepted for the interface; no feature uses the
+    conditioning sizes.)"""
     locs = np.asarray(locs, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     n, d = locs.shape
@@ -51,11 +53,12 @@ def features(locs, y, block_ptr, nn_ptr, max_points=10000, seed=0):
     f = np.zeros(NFEAT)
     nz = cnts > 0
     f[:32][nz] = sums[nz] / cnts[nz] / var
-    bs = np.diff(np.asarray(block_ptr)).astype(np.float64)
-    ms = np.diff(np.asarray(nn_ptr)).astype(np.float64)
+    # block-size histogram: the fraction of blocks of each size class
+    bs = np.diff(np.asarray(block_ptr))
     f[32] = np.log(var)
-    f[33], f[34], f[35], f[36] = bs.mean(), bs.std(), bs.min(), bs.max()
-    f[37] = ms.mean()
+    for k, (lo, hi) in enumerate(((1, 4), (5, 8), (9, 12), (13, 16), (17, None))):
+        inside = (bs >= lo) if hi is None else ((bs >= lo) & (bs <= hi))
+        f[33 + k] = np.count_nonzero(inside) / len(bs)
     # nearest other subsample point (squared distance summed left to right, lowest index
     # on ties): semivariance and distance at the smallest lag
     g_nn, d_nn = 0.0, 0.0

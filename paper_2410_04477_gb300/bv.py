@@ -529,7 +529,7 @@ class Context:
 
     def mle(self, th0: bv_theta, lo: bv_theta, hi: bv_theta,
             free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
-            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0, newton_first=False):
+            max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0, newton_first=True):
         o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget, int(newton_first), 0)
         out = bv_theta()
         ll = ctypes.c_double(0.0)
@@ -542,7 +542,7 @@ class Context:
     def mle_multi(self, th0, lo: bv_theta, hi: bv_theta,
                   free_mask=BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET, precision=BV_FP64,
                   max_evals=2000, ftol_rel=1e-10, xtol=1e-7, init_step=0.5, init_step_nugget=0.0,
-                  newton_first=False):
+                  newton_first=True):
         """Every dataset's MLE with batched evaluations: (thetas, logliks, evals, statuses, batches).
         th0: a list of starts (one per dataset) or None for the learned warm start."""
         nd = self.ndata

@@ -869,10 +869,11 @@ static int build_check(bv_ctx* c, const std::vector<int>& Nof) {
     for (size_t b = 0; b < nbin; ++b) {
         if (all[b].empty()) continue;
         BinPlan bp;
-        bp.kind = b < edges.size() ? 0 : 2;
         int nmax = 0;
         for (int32_t i : all[b]) nmax = std::max(nmax, Nof[i]);
         bp.nmax = nmax;
+        // (not timed by the autotuner: two-column steps from N = 112, where they win)
+        bp.kind = b < edges.size() ? (nmax >= 112 && bv_smem_bytes(6, nmax, c->d, 0) <= (size_t)(227 * 1024 - 3072) ? 6 : 0) : 2;
         bp.threads = default_threads(bp.kind, bp.nmax);
         // redo launch: the whole bin's capacity, count from the device
         bp.nwork = (int32_t)all[b].size();
@@ -1034,9 +1035,11 @@ static int autotune(bv_ctx* c, int prec) {
         // blocks also a warp per block with 2/4/8 warps per CTA (mixed up to N = 128,
         // FP64 up to N = 64)
         // BV_KERNEL_FORM=cta or =warp restricts the choice to one form where both exist
-        // (tests use it to check each kernel against the oracle)
+        // (tests use it to check each kernel against the oracle); FP64 CTA bins try the
+        // one-column and the two-column step (=cta keeps the first, =cta2 the second)
         const char* form = getenv("BV_KERNEL_FORM");
-        const bool only_cta = form && strcmp(form, "cta") == 0;
+        const bool only_cta2 = form && strcmp(form, "cta2") == 0;
+        const bool only_cta = (form && strcmp(form, "cta") == 0) || only_cta2;
         const bool only_warp = form && strcmp(form, "warp") == 0;
         // mixed bins with N >= 64 also try the tensor-core kernel (BV_KERNEL_FORM=tc
         // restricts them to it, =cta to the SIMT CTA kernel)
@@ -1045,8 +1048,11 @@ static int autotune(bv_ctx* c, int prec) {
         const bool only_tc = form && strcmp(form, "tc") == 0;
         const bool tc_ok = bp.kind == 1 && bp.nmax >= 64 &&
                            bv_smem_bytes(5, bp.nmax, c->d, 256) <= (size_t)(227 * 1024 - 3072);
-        if (!(only_warp && warp_ok) && !(only_tc && tc_ok))
+        const bool w2_ok = bp.kind == 0 && bv_smem_bytes(6, bp.nmax, c->d, 0) <= (size_t)(227 * 1024 - 3072);
+        if (!(only_warp && warp_ok) && !(only_tc && tc_ok) && !(only_cta2 && w2_ok))
             for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
+        if (w2_ok && !only_warp && !(only_cta && !only_cta2))
+            for (int t : {96, 160, 288, 544}) cands.push_back({6, t});
         if (!only_cta && !only_tc && warp_ok)
             for (int t : {64, 128, 256}) cands.push_back({bp.kind == 1 ? 3 : 4, t});
         if (!only_cta && !only_warp && tc_ok)

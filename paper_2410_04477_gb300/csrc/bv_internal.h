@@ -119,7 +119,8 @@ struct LLArgs {
 struct BinPlan {
     int kind;            // 0: FP64 shared-memory, 1: mixed (CTA per block), 2: large (global),
                          // 3: mixed (warp per block), 4: FP64 (warp per block),
-                         // 5: mixed with tensor-core updates (CTA per block)
+                         // 5: mixed with tensor-core updates (CTA per block),
+                         // 6: FP64 shared-memory with two-column steps
     int nmax;            // largest augmented size N = m + b in the bin
     int threads;         // CTA size (autotuned)
     int grid;            // CTAs launched

@@ -20,7 +20,7 @@
 // locations, y and the index lists is read from HBM and one double per block is written.
 //
 // Paths:
-//   k_ll_fp64<NT>   FP64 packed lower triangle in shared memory (N up to ~234 for d=3)
+//   k_ll_fp64<NT>   FP64 packed lower triangle in shared memory (N up to 233 for d=3; 231 with two-column steps)
 //   k_ll_mixed<NT>  FP32 covariance (block-local coordinates), FP32 updates; pivots,
 //                   log-determinant and quadratic form accumulated in FP64
 //   k_ll_large<NT>  FP64, packed triangle in a global-memory workspace slot (any N)
@@ -38,9 +38,40 @@
 namespace {
 
 // ---------------------------------------------------------------------------------
-// FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2][N+1] | pts[d][N]
+// FP64, shared memory.  Layout (doubles): A packed (N+1)(N+2)/2 | col[2 or 4][N+1] | pts[d][N]
 // ---------------------------------------------------------------------------------
-template <int NT, bool GEN>
+
+// Column c of the factor, by one warp: its entries in rows c..N have been updated with
+// every column before it except those in `prev` (np of them, each a finished column held
+// contiguously by row, applied here in order); then the pivot and the scaling, the scaled
+// column written to A and to out.  Raises *fail on a bad pivot.
+template <int NP>
+__device__ __forceinline__ void fp64_column(double* A, int c, int N, int lane, const double* const (&prev)[NP], int np,
+                                            double* out, int* fail) {
+    for (int j = c + lane; j <= N; j += 32) {
+        double v = A[pk(j, c)];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            if (q < np) v = fma(-prev[q][j], prev[q][c], v);
+        A[pk(j, c)] = v;
+    }
+    __syncwarp();
+    const double p = A[pk(c, c)];
+    if (bad_pivot(p) && lane == 0) *fail = 1;
+    const double rs = rsqrt(p);
+    for (int j = c + 1 + lane; j <= N; j += 32) {
+        const double v = A[pk(j, c)] * rs;
+        A[pk(j, c)] = v;
+        out[j] = v;
+    }
+    __syncwarp();
+}
+
+// W2 selects the step width of the factorisation: one column per barrier (two column
+// buffers) or two (four buffers); both give the same results bit for bit, and the planner
+// times both per size bin (one column wins on small blocks, where the panel warp's pivot
+// chain is the critical path, two on large ones, where the trailing update is).
+template <int NT, bool GEN, bool W2>
 __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double* sm = reinterpret_cast<double*>(smraw);
@@ -62,9 +93,8 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         const int N = m + b, R = N + 1;
         const DevTheta th = a.theta[a.bds[blk]];
         double* A = sm;
-        double* col0 = A + ((R * (R + 1)) >> 1);
-        double* col1 = col0 + R;
-        double* px = col1 + R;
+        double* colbuf = A + ((R * (R + 1)) >> 1);  // column buffers of R doubles
+        double* px = colbuf + (W2 ? 4 : 2) * R;
         const int d = a.d;
 
         // gather: conditioning points first, then the block (Algorithm 1 order)
@@ -101,57 +131,91 @@ __global__ void __launch_bounds__(NT) k_ll_fp64(LLArgs a) {
         }
         __syncthreads();
 
-        // column 0
-        if (warp == 0) {
-            const double p = A[0];
-            if (bad_pivot(p) && lane == 0) s_fail = 1;
-            const double rs = rsqrt(p);
-            for (int j = 1 + lane; j <= N; j += 32) {
-                const double v = A[pk(j, 0)] * rs;
-                A[pk(j, 0)] = v;
-                col0[j] = v;
-            }
-        }
-        __syncthreads();
-
-        // right-looking steps: warp 0 finishes column k+1 (update, pivot, scale) while
-        // all warps apply column k to the rest of the trailing triangle; one barrier/step
-        for (int k = 0; k + 1 < N; ++k) {
-            const double* cur = (k & 1) ? col1 : col0;
-            double* nxt = (k & 1) ? col0 : col1;
-            const int kk = k + 1;
+        if constexpr (!W2) {
+            // column 0 (warp 0)
             if (warp == 0) {
-                const double ck = cur[kk];
-                for (int j = kk + lane; j <= N; j += 32) A[pk(j, kk)] = fma(-cur[j], ck, A[pk(j, kk)]);
-                __syncwarp();
-                const double p = A[pk(kk, kk)];
-                if (bad_pivot(p) && lane == 0) s_fail = 1;
-                const double rs = rsqrt(p);
-                for (int j = kk + 1 + lane; j <= N; j += 32) {
-                    const double v = A[pk(j, kk)] * rs;
-                    A[pk(j, kk)] = v;
-                    nxt[j] = v;
-                }
+                const double* none[1] = {nullptr};
+                fp64_column<1>(A, 0, N, lane, none, 0, colbuf, &s_fail);
             }
-            // warps 1.. update the rest of the trailing triangle (rows kk+1..N, columns
-            // kk+1..row), two independent elements per iteration
-            if (warp > 0) {
-                const int S = N - kk;
-                const int TS = (S * (S + 1)) >> 1;
-                constexpr int NU = NT - 32;
-                for (int f = tid - 32; f < TS; f += 2 * NU) {
-                    int r1, c1, r2, c2;
-                    tri_rc(f, r1, c1);
-                    const bool two = f + NU < TS;
-                    tri_rc(two ? f + NU : f, r2, c2);
-                    const int j1 = kk + 1 + r1, i1 = kk + 1 + c1, j2 = kk + 1 + r2, i2 = kk + 1 + c2;
-                    const double a1 = A[pk(j1, i1)], x1 = cur[j1], y1 = cur[i1];
-                    const double a2 = A[pk(j2, i2)], x2 = cur[j2], y2 = cur[i2];
-                    A[pk(j1, i1)] = fma(-x1, y1, a1);
-                    if (two) A[pk(j2, i2)] = fma(-x2, y2, a2);
+            __syncthreads();
+
+            // right-looking steps: warp 0 finishes column k+1 (update, pivot, scale) while
+            // the other warps apply column k to the rest of the trailing triangle; one
+            // barrier per step
+            for (int k = 0; k + 1 < N; ++k) {
+                const double* cur = colbuf + (k & 1) * R;
+                double* nxt = colbuf + ((k & 1) ^ 1) * R;
+                const int kk = k + 1;
+                if (warp == 0) {
+                    const double* p1[1] = {cur};
+                    fp64_column<1>(A, kk, N, lane, p1, 1, nxt, &s_fail);
+                } else {
+                    // rows kk+1..N, columns kk+1..row, two independent elements per iteration
+                    const int S = N - kk;
+                    const int TS = (S * (S + 1)) >> 1;
+                    constexpr int NU = NT - 32;
+                    for (int f = tid - 32; f < TS; f += 2 * NU) {
+                        int r1, c1, r2, c2;
+                        tri_rc(f, r1, c1);
+                        const bool two = f + NU < TS;
+                        tri_rc(two ? f + NU : f, r2, c2);
+                        const int j1 = kk + 1 + r1, i1 = kk + 1 + c1, j2 = kk + 1 + r2, i2 = kk + 1 + c2;
+                        const double a1 = A[pk(j1, i1)], x1 = cur[j1], y1 = cur[i1];
+                        const double a2 = A[pk(j2, i2)], x2 = cur[j2], y2 = cur[i2];
+                        A[pk(j1, i1)] = fma(-x1, y1, a1);
+                        if (two) A[pk(j2, i2)] = fma(-x2, y2, a2);
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            // columns 0 and 1 (warp 0)
+            if (warp == 0) {
+                const double* none[1] = {nullptr};
+                fp64_column<1>(A, 0, N, lane, none, 0, colbuf, &s_fail);
+                if (N > 1) {
+                    const double* p0[1] = {colbuf};
+                    fp64_column<1>(A, 1, N, lane, p0, 1, colbuf + R, &s_fail);
                 }
             }
             __syncthreads();
+
+            // right-looking steps of two columns: with columns k and k+1 finished (buffers
+            // c0, c1), warp 0 finishes columns k+2 and k+3 (their updates by k and k+1, then
+            // k+3's by k+2; pivots; scaling) while the other warps apply columns k and k+1 to
+            // the trailing triangle from row and column k+4; one barrier per two columns.
+            // Every entry receives its updates in column order, as in a one-column-per-step
+            // factorisation, so the results are the same bit for bit.
+            for (int k = 0; k + 2 < N; k += 2) {
+                const int sel = (k >> 1) & 1;
+                const double* c0 = colbuf + (2 * sel) * R;
+                const double* c1 = c0 + R;
+                double* n0b = colbuf + (2 * (sel ^ 1)) * R;
+                double* n1b = n0b + R;
+                if (warp == 0) {
+                    const double* p2[2] = {c0, c1};
+                    fp64_column<2>(A, k + 2, N, lane, p2, 2, n0b, &s_fail);
+                    if (k + 3 < N) {
+                        const double* p3[3] = {c0, c1, n0b};
+                        fp64_column<3>(A, k + 3, N, lane, p3, 3, n1b, &s_fail);
+                    }
+                } else {
+                    const int kk = k + 4;  // trailing triangle: rows kk..N, columns kk..row
+                    const int S = N - kk + 1;
+                    if (S > 0) {
+                        const int TS = (S * (S + 1)) >> 1;
+                        constexpr int NU = NT - 32;
+                        for (int f = tid - 32; f < TS; f += NU) {
+                            int r, c;
+                            tri_rc(f, r, c);
+                            const int j = kk + r, i = kk + c;
+                            const double v = fma(-c0[j], c0[i], A[pk(j, i)]);
+                            A[pk(j, i)] = fma(-c1[j], c1[i], v);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
 
         // u + d over the block columns (warp 0)
@@ -953,7 +1017,9 @@ constexpr int kSmemCap = 227 * 1024 - 3072;
 
 template <int NT, bool GEN>
 cudaError_t set_smem_cap_g() {
-    cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ll_mixed<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
@@ -973,7 +1039,8 @@ cudaError_t set_smem_cap() {
 // any dataset's nu is not 1/2, 3/2 or 5/2); the others carry no call in their inner loops.
 template <int NT, bool GEN>
 cudaError_t launch_kind_g(int kind, int grid, size_t smem, const LLArgs& a, cudaStream_t s) {
-    if (kind == 0) k_ll_fp64<NT, GEN><<<grid, NT, smem, s>>>(a);
+    if (kind == 0) k_ll_fp64<NT, GEN, false><<<grid, NT, smem, s>>>(a);
+    else if (kind == 6) k_ll_fp64<NT, GEN, true><<<grid, NT, smem, s>>>(a);
     else if (kind == 1) k_ll_mixed<NT, GEN><<<grid, NT, smem, s>>>(a);
     else if (kind == 3) k_ll_mixed_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
     else if (kind == 4) k_ll_fp64_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(double) / (NT / 32)));
@@ -1005,7 +1072,7 @@ size_t bv_smem_bytes(int kind, int nmax, int d, int threads) {
         const size_t region = (R * (R + 1) / 2 + R + (size_t)d * nmax + 1) & ~(size_t)1;
         return sizeof(double) * region * (size_t)(threads / 32);
     }
-    size_t bytes = el * (R * (R + 1) / 2 + 2 * R + (size_t)d * nmax);
+    size_t bytes = el * (R * (R + 1) / 2 + (kind == 6 ? 4 : 2) * R + (size_t)d * nmax);
     return (bytes + 15) & ~(size_t)15;
 }
 
@@ -1105,7 +1172,9 @@ int bv_occupancy(int kind, int threads, size_t smem) {
         if (kind != 2) e = set_smem_cap<NT>();                                                \
         if (e == cudaSuccess) {                                                               \
             if (kind == 0)                                                                    \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT, false>, NT, smem);  \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT, false, false>, NT, smem); \
+            else if (kind == 6)                                                               \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<NT, false, true>, NT, smem); \
             else if (kind == 1)                                                               \
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_mixed<NT, false>, NT, smem); \
             else if (kind == 3)                                                               \

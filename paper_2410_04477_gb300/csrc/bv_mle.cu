@@ -1,8 +1,11 @@
 // bv_mle.cu -- maximum-likelihood driver over the block-Vecchia log-likelihood.
 //
-// The paper estimates theta with the derivative-free BOBYQA optimiser (Sec. 3.2); this
-// library uses the derivative-free Nelder-Mead simplex method (Nelder and Mead 1965) with
-// the standard coefficients (reflection 1, expansion 2, contraction 1/2, shrink 1/2).
+// The paper estimates theta with the derivative-free BOBYQA optimiser (Sec. 3.2), a
+// trust-region method on interpolated quadratic models; this library runs trust-region
+// Newton iterations on central-difference quadratic models (with newton_first, the
+// default of the Python binding) and falls back to the derivative-free Nelder-Mead
+// simplex method (Nelder and Mead 1965, the standard coefficients: reflection 1,
+// expansion 2, contraction 1/2, shrink 1/2).
 //
 // Profile likelihood.  Write the covariance as sigma^2 (R_beta + eta I) with eta =
 // tau^2 / sigma^2.  Every block's kriging weights depend on (beta, eta) only and its
@@ -18,15 +21,19 @@
 // Matern model sigma^2 and beta are poorly identified separately but that combination is
 // well identified, so the change of variables straightens the ridge of the surface.
 //
-// Points outside the box score -inf, and so does a non-positive-definite point.  The
-// search runs in two stages.  A coarse Nelder-Mead search (in the requested precision)
-// stops at a simplex of diameter 1e-3 in log-parameters; the simplex is then rebuilt once
-// around the best point and the search resumed (a standard guard against premature
-// collapse).  An FP64 Newton polish on a central-difference quadratic model then takes
-// the estimate to the caller's xtol in a few evaluations; where the model is not convex
-// or a step fails to improve (e.g. an optimum on the box boundary), an FP64 Nelder-Mead
-// search with the caller's tolerances finishes instead.  The returned estimate is the
-// best FP64-scored point, and ell is its FP64 value.
+// Points outside the box score -inf, and so does a non-positive-definite point.  With
+// newton_first, trust-region Newton iterations run from the start point: in FP64 to the
+// caller's tolerances; in mixed precision to coarse ones (step 1e-3 in log-parameters,
+// relative ell change ten times the measured mixed error) with wide difference steps,
+// then an FP64 polish.  Where they fail, or without newton_first, the search runs in two
+// stages.  A coarse Nelder-Mead search (in the requested precision) stops at a simplex of
+// diameter 1e-3 in log-parameters; the simplex is then rebuilt once around the best point
+// and the search resumed (a standard guard against premature collapse).  An FP64 Newton
+// polish on a central-difference quadratic model then takes the estimate to the caller's
+// xtol in a few evaluations; where the model is not convex or a step fails to improve
+// (e.g. an optimum on the box boundary), an FP64 Nelder-Mead search with the caller's
+// tolerances finishes instead.  The returned estimate is the best FP64-scored point, and
+// ell is its FP64 value.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -362,6 +369,105 @@ bool newton_polish(Objective& f, const Space& S, std::vector<double>* x, double*
     return false;
 }
 
+// Central-difference gradient and Hessian of f at x (f(x) = fx) with step h: 2n + n(n-1)/2
+// evaluations.  False when a point is not finite (outside the box, not positive definite).
+bool fd_model(Objective& f, const std::vector<double>& x, double fx, double h, std::vector<double>* g,
+              std::vector<double>* H) {
+    const int n = (int)x.size();
+    std::vector<double> fp(n), y;
+    g->assign(n, 0.0);
+    H->assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        y = x;
+        y[i] += h;
+        fp[i] = f(y);
+        y[i] = x[i] - h;
+        const double fm = f(y);
+        if (f.hard_error || !std::isfinite(fp[i]) || !std::isfinite(fm)) return false;
+        (*g)[i] = (fp[i] - fm) / (2.0 * h);
+        (*H)[i * n + i] = (fp[i] - 2.0 * fx + fm) / (h * h);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            y = x;
+            y[i] += h;
+            y[j] += h;
+            const double fij = f(y);
+            if (f.hard_error || !std::isfinite(fij)) return false;
+            (*H)[i * n + j] = (*H)[j * n + i] = (fij - fp[i] - fp[j] + fx) / (h * h);
+        }
+    return true;
+}
+
+// Trust-region Newton iteration (the basic trust-region algorithm of Nocedal and Wright,
+// Numerical Optimization, Alg. 4.1, with a sup-norm radius) on the central-difference
+// model of fd_model.  Each iteration builds the model at x, solves H p = -g (H shifted by
+// a multiple of the identity where it is not positive definite, the Levenberg-Marquardt
+// remedy), truncates p to the radius and evaluates the step; the ratio of the actual to
+// the model's decrease grows the radius (ratio > 3/4 at a truncated step) or shrinks it
+// (ratio < 1/4: a quarter of the step taken).  A step that does not lower f is retried
+// at the smaller radius on the same model, at most three times.  Returns true when the
+// unshifted Newton step is within xtol or its predicted decrease g^T H^-1 g / 2 within
+// ftol |f|; false when the iterations or evaluations run out or no retry lowers f (the
+// caller then falls back to the simplex search).
+bool trust_newton(Objective& f, const Space& S, std::vector<double>* x, double* fx, double h, double xtol,
+                  double ftol, int max_evals, double rad, int iters, int* accepted = nullptr) {
+    const int n = S.dim;
+    const bool log = getenv("BV_LOG_MLE") && atoi(getenv("BV_LOG_MLE")) >= 2;
+    if (accepted) *accepted = 0;
+    std::vector<double> g, H, Hs, p, st(n), y;
+    double maxdiag = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        if (f.evals + 2 + n * (n + 3) / 2 + 3 > max_evals) return false;
+        if (!fd_model(f, *x, *fx, h, &g, &H)) return false;
+        maxdiag = 0.0;
+        for (int i = 0; i < n; ++i) maxdiag = std::max(maxdiag, fabs(H[i * n + i]));
+        double lam = 0.0;
+        Hs = H;
+        while (!newton_step(Hs, g, n, &p)) {
+            lam = lam > 0.0 ? 4.0 * lam : 1e-3 * maxdiag + 1e-300;
+            if (!(lam < 1e6 * maxdiag + 1.0)) return false;
+            Hs = H;
+            for (int i = 0; i < n; ++i) Hs[i * n + i] += lam;
+        }
+        double len = 0.0, pred_full = 0.0;
+        for (int i = 0; i < n; ++i) {
+            len = std::max(len, fabs(p[i]));
+            pred_full -= 0.5 * g[i] * p[i];
+        }
+        bool improved = false;
+        for (int tr = 0; tr < 4 && !improved; ++tr) {
+            const double sc = len > rad ? rad / len : 1.0;
+            double pred = 0.0;
+            for (int i = 0; i < n; ++i) st[i] = sc * p[i];
+            for (int i = 0; i < n; ++i) {
+                double hs = 0.0;
+                for (int j = 0; j < n; ++j) hs += H[i * n + j] * st[j];
+                pred -= g[i] * st[i] + 0.5 * st[i] * hs;
+            }
+            y = *x;
+            for (int i = 0; i < n; ++i) y[i] += st[i];
+            const double fy = f(y);
+            if (f.hard_error) return false;
+            const double ratio = pred > 0.0 && std::isfinite(fy) ? (*fx - fy) / pred : -1.0;
+            if (ratio > 0.75 && sc < 1.0) rad = std::min(2.0 * rad, 4.0);
+            else if (ratio < 0.25) rad = 0.25 * sc * len;
+            if (log)
+                fprintf(stderr, "bv_mle:   it %d try %d: f %.9g -> %.9g, predicted %.3g, full step %.3g (lambda %.3g), "
+                        "radius %.3g\n", it, tr, *fx, fy, pred, len, lam, rad);
+            if (fy < *fx) {
+                *x = y;
+                *fx = fy;
+                improved = true;
+                if (accepted) ++*accepted;
+            }
+        }
+        if (lam == 0.0 && (len <= xtol || pred_full <= ftol * fabs(*fx))) return true;
+        if (!improved) return false;
+    }
+    return false;
+}
+
 }  // namespace
 
 // The mixed-precision search stage scores points for an FP64 polish that fixes the final
@@ -446,25 +552,37 @@ static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* th
             ftol_c = std::max(ftol_c, 10.0 * err);
         }
         obj.reset(prec);
-        // a start near the optimum: Newton steps first (in FP64, whose finite differences
-        // the model needs), the simplex search only if they fail
-        bool near = false;
+        // Newton first: trust-region steps on a central-difference model from the start
+        // point; in FP64 straight to the caller's tolerances, in mixed precision to the
+        // coarse ones with difference steps of 0.02 (FP32 rounding of ell, about 1e-8 of
+        // it, would swamp difference quotients over 1e-3).  The simplex search runs only
+        // if the steps fail, from the best point they reached.
+        bool near = false, done = false;
         if (opts->newton_first) {
-            obj.reset(BV_FP64);
+            const bool fp64 = prec == BV_FP64;
             double fx = obj(x);
             BV_TRY(obj.hard_error);
             std::vector<double> xn = x;
-            near = std::isfinite(fx) && newton_polish(obj, S, &xn, &fx, 1e-3, xtol_c, ftol_c, opts->max_evals, 0.5, 12);
+            int acc = 0;
+            near = std::isfinite(fx) && trust_newton(obj, S, &xn, &fx, fp64 ? 1e-3 : 2e-2, fp64 ? opts->xtol : xtol_c,
+                                                     fp64 ? opts->ftol_rel : ftol_c, opts->max_evals, 0.5, 40, &acc);
             BV_TRY(obj.hard_error);
+            // in mixed precision, iterations that moved and then stalled have reached the
+            // FP32 rounding floor of ell near the optimum: the FP64 polish takes over there
+            if (!near && !fp64 && acc > 0 && std::isfinite(fx)) {
+                near = true;
+                if (getenv("BV_LOG_MLE")) fprintf(stderr, "bv_mle: Newton-first stalled after %d steps\n", acc);
+            }
             if (near) {
                 xb = xn;
                 fb = fx;
-            } else {
-                x = obj.xbest;  // continue from the best point the steps reached
+                done = fp64;
+            } else if (!obj.xbest.empty()) {
+                x = obj.xbest;
                 obj.reset(prec);
             }
             if (getenv("BV_LOG_MLE"))
-                fprintf(stderr, "bv_mle: Newton-first start %s after %d evals\n", near ? "converged" : "failed",
+                fprintf(stderr, "bv_mle: Newton-first %s after %d evals\n", near ? "converged" : "failed",
                         obj.evals);
         }
         if (!near) {
@@ -472,12 +590,16 @@ static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* th
             const double s1 = std::max(s0 * 0.1, 20.0 * xtol_c);
             BV_TRY(nelder_mead(obj, S, xb, s1, s1, ftol_c, xtol_c, opts->max_evals, &xb, &fb));
         }
-        if (std::isfinite(fb)) {
+        if (std::isfinite(fb) && !done) {
             obj.reset(BV_FP64);
             fb = obj(xb);
             BV_TRY(obj.hard_error);
             const int coarse = obj.evals;
-            bool done = std::isfinite(fb) && newton_polish(obj, S, &xb, &fb, 1e-3, opts->xtol, opts->ftol_rel, opts->max_evals);
+            done = std::isfinite(fb) && (opts->newton_first
+                                             ? trust_newton(obj, S, &xb, &fb, 1e-3, opts->xtol, opts->ftol_rel,
+                                                            opts->max_evals, 0.1, 8)
+                                             : newton_polish(obj, S, &xb, &fb, 1e-3, opts->xtol, opts->ftol_rel,
+                                                             opts->max_evals));
             BV_TRY(obj.hard_error);
             if (getenv("BV_LOG_MLE"))
                 fprintf(stderr, "bv_mle: coarse search %d evals, Newton polish %s after %d\n", coarse,

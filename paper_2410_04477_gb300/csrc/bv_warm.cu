@@ -461,24 +461,17 @@ extern "C" int bv_features(bv_ctx* c, int32_t max_points, uint64_t seed, float* 
             }
             f[k] = cnt ? (float)(s / (double)cnt / var) : 0.0f;
         }
-        // structure statistics
+        // block-size histogram: fractions of the dataset's blocks with b_i in 1-4, 5-8,
+        // 9-12, 13-16 and 17 or more points (unlike extremes or means of the structure,
+        // stable as n grows at a fixed points-per-block ratio)
         const int64_t b0 = c->ds_blk_off[ds], b1 = c->ds_blk_off[ds + 1], nbk = b1 - b0;
-        double sm = 0, sq = 0, mn = 1e300, mx = 0, mm = 0;
+        int64_t hist[5] = {0, 0, 0, 0, 0};
         for (int64_t i = b0; i < b1; ++i) {
-            const double bs = (double)(c->h_bptr[i + 1] - c->h_bptr[i]);
-            sm += bs;
-            sq += bs * bs;
-            mn = std::min(mn, bs);
-            mx = std::max(mx, bs);
-            mm += (double)(c->h_nptr[i + 1] - c->h_nptr[i]);
+            const int64_t bs = c->h_bptr[i + 1] - c->h_bptr[i];
+            ++hist[std::min<int64_t>(4, std::max<int64_t>(0, (bs - 1) / 4))];
         }
-        const double bmean = sm / nbk;
         f[32] = (float)log(var);
-        f[33] = (float)bmean;
-        f[34] = (float)sqrt(std::max(0.0, sq / nbk - bmean * bmean));
-        f[35] = (float)mn;
-        f[36] = (float)mx;
-        f[37] = (float)(mm / nbk);
+        for (int k = 0; k < 5; ++k) f[33 + k] = (float)((double)hist[k] / (double)nbk);
         f[38] = (float)(nn_gamma / var);
         f[39] = (float)(64.0 * nn_dist);
     }

@@ -1,5 +1,6 @@
-"""GPU: each kernel form the autotuner can choose for a size bin -- one CTA per block, or
-one warp per block (FP64 up to N = 64, mixed up to N = 128) -- forced in turn through
+"""GPU: each kernel form the autotuner can choose for a size bin -- one CTA per block (in
+FP64 with one- or two-column factorisation steps), or one warp per block (FP64 up to
+N = 64, mixed up to N = 128), or the tensor-core mixed kernel -- forced in turn through
 BV_KERNEL_FORM and checked against the FP64 oracle on the same structure, so that a form
 the timing never picks on these sizes is still tested: K-means blocks (N around 40) and
 classic-Vecchia singletons (N = m + 1), closed-form and general smoothness, 2D and 3D."""
@@ -35,7 +36,7 @@ def _run(bv, locs, y, th, singletons, bc, m, seed):
     return ll64, per64, llm, (bp, pi, nnp, nni)
 
 
-@pytest.mark.parametrize("form", ["cta", "warp"])
+@pytest.mark.parametrize("form", ["cta", "cta2", "warp"])
 @pytest.mark.parametrize("case", [
     # (n, d, singletons, bc, m, theta = (sigma^2, beta, nu, tau^2))
     (2000, 2, False, 200, 30, (1.0, 0.1, 1.5, 1e-3)),

@@ -54,15 +54,18 @@ def test_loglik_terms_match_oracle(bv):
     assert ll == pytest.approx(-0.5 * (Q + D + n * np.log(2 * np.pi)), rel=1e-13)
 
 
+@pytest.mark.parametrize("newton_first", [True, False])
 @pytest.mark.parametrize("prec_name", ["BV_FP64", "BV_MIXED"])
-def test_profile_mle_is_a_stationary_maximum(bv, prec_name):
+def test_profile_mle_is_a_stationary_maximum(bv, prec_name, newton_first):
+    # both search orders: trust-region Newton first (the default) and the simplex first
     locs, y, st, bc, m, seed = _problem()
     n = len(y)
     nu = 1.5
     lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
     with _ctx(bv, locs, y, bc, m, seed, st) as ctx:
         th, ll, ne = ctx.mle(bv.theta(1.0, 0.1, nu, 1e-2), lo, hi, precision=getattr(bv, prec_name),
-                             ftol_rel=1e-13, xtol=1e-7)
+                             ftol_rel=1e-13, xtol=1e-7, newton_first=newton_first)
+        print(f"{prec_name} newton_first={newton_first}: {ne} evaluations")
         assert 0 < ne < 2000
         # the returned ell is the FP64 ell at the returned theta
         assert ll == pytest.approx(ctx.loglik(th), rel=1e-11)

@@ -83,8 +83,9 @@ def test_training_reduces_loss(bv):
 
 @pytest.mark.parametrize("prec_name", ["BV_FP64", "BV_MIXED"])
 def test_warm_start_cuts_loglik_calls(bv, prec_name):
-    # the learned start lies near the optimum: Newton steps from it (the simplex search only
-    # if they fail) reach the cold start's optimum with at least 30% fewer evaluations
+    # the learned start lies near the optimum: the same search (trust-region Newton steps,
+    # the simplex search only if they fail) reaches the cold start's optimum with at least
+    # 30% fewer evaluations from it
     wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
     if not os.path.exists(wpath):
         pytest.skip("no trained warm-start weights committed")
@@ -100,7 +101,8 @@ def test_warm_start_cuts_loglik_calls(bv, prec_name):
             ctx.simulate(bv.theta(s2, beta, nu, tau2), synth.normal(900 + k, 20, n))
             cold0 = bv.theta(1.0, 0.1, nu, 1e-2)
             lo, hi = bv.theta(0.01, 0.001, nu, 1e-6), bv.theta(100.0, 3.0, nu, 10.0)
-            th_c, ll_c, ne_c = ctx.mle(cold0, lo, hi, precision=prec, ftol_rel=1e-12, xtol=1e-6)
+            th_c, ll_c, ne_c = ctx.mle(cold0, lo, hi, precision=prec, ftol_rel=1e-12, xtol=1e-6,
+                                       newton_first=True)
             ctx.warmstart_load(wpath)
             warm0 = ctx.warmstart_predict(cold0)
             # the simplex scale (used only if the Newton steps fail) is the network's
@@ -138,21 +140,27 @@ def test_mle_without_a_start_uses_the_warm_start(bv):
 
 def test_warm_start_smoothness_head(bv):
     # theta_in.nu = 0 asks the network for the smoothness class; on fields drawn at
-    # nu = 1/2 and 5/2 (clearly different roughness) it should tell them apart
+    # nu = 1/2 and 5/2 (clearly different roughness) it should tell them apart: never the
+    # other extreme, and the right class for at least 12 of 16 fields (its validation
+    # accuracy over the three classes is about 93%)
     wpath = os.path.join(ROOT, "paper_2410_04477_gb300", "weights", "warmstart.bvws")
     if not os.path.exists(wpath):
         pytest.skip("no trained warm-start weights committed")
     n = 10000
-    got = []
-    for k, nu in enumerate((0.5, 2.5)):
-        locs = synth.locs_uniform(n, 2, 960 + k)
-        with bv.Context() as ctx:
-            ctx.set_data(locs)
-            ctx.build_blocks(n // 10, seed=960 + k)
-            ctx.select_neighbors(100)
-            ctx.simulate(bv.theta(1.0, 0.1, nu, 1e-3), synth.normal(960 + k, 20, n))
-            ctx.warmstart_load(wpath)
-            got.append(ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu)
-            kept = ctx.warmstart_predict(bv.theta(1.0, 0.1, 1.5, 1e-2)).nu
+    right = 0
+    for k in range(8):
+        for nu in (0.5, 2.5):
+            seed = 960 + 2 * k + (nu > 1)
+            locs = synth.locs_uniform(n, 2, seed)
+            with bv.Context() as ctx:
+                ctx.set_data(locs)
+                ctx.build_blocks(n // 10, seed=seed)
+                ctx.select_neighbors(100)
+                ctx.simulate(bv.theta(1.0, 0.1, nu, 1e-3), synth.normal(seed, 20, n))
+                ctx.warmstart_load(wpath)
+                got = ctx.warmstart_predict(bv.theta(1.0, 0.1, 0.0, 1e-2)).nu
+                kept = ctx.warmstart_predict(bv.theta(1.0, 0.1, 1.5, 1e-2)).nu
             assert kept == 1.5
-    assert got == [0.5, 2.5], got
+            assert abs(got - nu) < 2.0, (nu, got)
+            right += got == nu
+    assert right >= 12, right

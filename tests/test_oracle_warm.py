@@ -77,7 +77,14 @@ def test_variogram_of_a_linear_field():
                 cnts[k] += 1
     want = np.where(cnts > 0, sums / np.maximum(cnts, 1) / var, 0.0)
     np.testing.assert_allclose(f[:32], want, rtol=1e-12)
-    assert f[33] == 150 and f[35] == 100 and f[36] == 200 and f[37] == 25
+    # two blocks of 100 and 200 points: both in the last size class
+    np.testing.assert_array_equal(f[33:38], [0, 0, 0, 0, 1])
+    # the size classes on a hand-made partition: sizes 1, 4, 5, 8, 9, 12, 13, 16, 17, 40
+    sizes = np.array([1, 4, 5, 8, 9, 12, 13, 16, 17, 40])
+    bp = np.concatenate([[0], np.cumsum(sizes)])
+    xx = rng.random((int(bp[-1]), 1))
+    g = warm.features(xx, xx[:, 0], bp, np.zeros(len(bp), np.int64), max_points=10000)
+    np.testing.assert_array_equal(g[33:38], [0.2, 0.2, 0.2, 0.2, 0.2])
     # nearest neighbour on a sorted line: the closer of the two adjacent points
     xs = x[:, 0]
     g_nn = d_nn = 0.0
