@@ -1031,7 +1031,8 @@ static int autotune(bv_ctx* c, int prec) {
     BV_CUDA(bv_launch_fail_reset(c->d_fail, c->stream));
     for (auto& bp : c->plan[prec]) {
         if (bp.kind == 2) continue;
-        // candidates: CTA per block with 1 panel warp + 2/4/8/16 update warps; for small
+        // candidates: CTA per block with 1 panel warp + 2/4/8/16 update warps (FP64 bins
+        // with N >= 128 also 31); for small
         // blocks also a warp per block with 2/4/8 warps per CTA (mixed up to N = 128,
         // FP64 up to N = 64)
         // BV_KERNEL_FORM=cta or =warp restricts the choice to one form where both exist
@@ -1050,9 +1051,11 @@ static int autotune(bv_ctx* c, int prec) {
                            bv_smem_bytes(5, bp.nmax, c->d, 256) <= (size_t)(227 * 1024 - 3072);
         const bool w2_ok = bp.kind == 0 && bv_smem_bytes(6, bp.nmax, c->d, 0) <= (size_t)(227 * 1024 - 3072);
         if (!(only_warp && warp_ok) && !(only_tc && tc_ok) && !(only_cta2 && w2_ok))
-            for (int t : {96, 160, 288, 544}) cands.push_back({bp.kind, t});
+            for (int t : {96, 160, 288, 544, 1024})
+                if (t < 1024 || (bp.kind == 0 && bp.nmax >= 128)) cands.push_back({bp.kind, t});
         if (w2_ok && !only_warp && !(only_cta && !only_cta2))
-            for (int t : {96, 160, 288, 544}) cands.push_back({6, t});
+            for (int t : {96, 160, 288, 544, 1024})
+                if (t < 1024 || bp.nmax >= 128) cands.push_back({6, t});
         if (!only_cta && !only_tc && warp_ok)
             for (int t : {64, 128, 256}) cands.push_back({bp.kind == 1 ? 3 : 4, t});
         if (!only_cta && !only_warp && tc_ok)

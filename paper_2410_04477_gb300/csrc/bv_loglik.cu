@@ -16,7 +16,8 @@
 // last row of the factor and p_k the pivots (squared diagonal of the factor), and
 //        ell_i = -(u + d + b log 2 pi) / 2.
 // The kernels generate the matrix (Matern, Eq. 5) straight into shared memory, factor it
-// in place (right-looking, one column per step) and reduce ell_i, so nothing but the
+// in place (right-looking, one or two columns per step in FP64, 4-column tile panels in
+// mixed precision) and reduce ell_i, so nothing but the
 // locations, y and the index lists is read from HBM and one double per block is written.
 //
 // Paths:
@@ -1015,11 +1016,14 @@ __global__ void k_matern_check(const double* x, double* out, int64_t n, const De
 // stay valid when a smaller bin is launched later).
 constexpr int kSmemCap = 227 * 1024 - 3072;
 
+// NT = 1024 (one panel warp and 31 update warps) exists for the FP64 CTA kernels only:
+// their large blocks run one CTA per SM, where more update warps hide more latency.
 template <int NT, bool GEN>
 cudaError_t set_smem_cap_g() {
     cudaError_t e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ll_fp64<NT, GEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    if constexpr (NT == 1024) return e;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ll_mixed<NT, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     if (e == cudaSuccess)
@@ -1041,6 +1045,7 @@ template <int NT, bool GEN>
 cudaError_t launch_kind_g(int kind, int grid, size_t smem, const LLArgs& a, cudaStream_t s) {
     if (kind == 0) k_ll_fp64<NT, GEN, false><<<grid, NT, smem, s>>>(a);
     else if (kind == 6) k_ll_fp64<NT, GEN, true><<<grid, NT, smem, s>>>(a);
+    else if constexpr (NT == 1024) return cudaErrorInvalidValue;
     else if (kind == 1) k_ll_mixed<NT, GEN><<<grid, NT, smem, s>>>(a);
     else if (kind == 3) k_ll_mixed_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(float) / (NT / 32)));
     else if (kind == 4) k_ll_fp64_w<NT, GEN><<<grid, NT, smem, s>>>(a, (int)(smem / sizeof(double) / (NT / 32)));
@@ -1101,6 +1106,7 @@ cudaError_t bv_launch_bin(const BinPlan& bp, const LLArgs& a0, cudaStream_t s) {
         case 288: return launch_kind<288>(bp.kind, bp.grid, bp.smem, a, s);
         case 544: return launch_kind<544>(bp.kind, bp.grid, bp.smem, a, s);
         case 256: return launch_kind<256>(bp.kind, bp.grid, bp.smem, a, s);
+        case 1024: return launch_kind<1024>(bp.kind, bp.grid, bp.smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1187,6 +1193,12 @@ int bv_occupancy(int kind, int threads, size_t smem) {
     }
     BV_OCC(64) BV_OCC(128) BV_OCC(96) BV_OCC(160) BV_OCC(288) BV_OCC(544) BV_OCC(256)
 #undef BV_OCC
+    if (threads == 1024 && (kind == 0 || kind == 6)) {
+        e = set_smem_cap<1024>();
+        if (e == cudaSuccess)
+            e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<1024, false, false>, 1024, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ll_fp64<1024, false, true>, 1024, smem);
+    }
     if (e != cudaSuccess) return 0;
     return nb;
 }

@@ -534,8 +534,8 @@ static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* th
         BV_TRY(obj.hard_error);
     } else {
         // Coarse search: Nelder-Mead to a simplex of diameter 1e-3 and relative ell spread
-        // 1e-7 (in mixed precision no tighter than ten times its measured error at the
-        // start point), restarted once around the optimum; then, in FP64, a Newton polish
+        // 1e-7 (in mixed precision no tighter than 1e-6 or ten times its measured error at
+        // the start point), restarted once around the optimum; then, in FP64, a Newton polish
         // to xtol, or, if that fails, the Nelder-Mead search and restart to the caller's
         // tolerances.
         const double s0 = opts->init_step, sn = opts->init_step_nugget > 0.0 ? opts->init_step_nugget : s0;
@@ -549,7 +549,10 @@ static int mle_search(bv_ctx* c, Evaluator* ev, double n_obs, const bv_theta* th
             const double f32 = obj(x);
             BV_TRY(obj.hard_error);
             const double err = (std::isfinite(f64) && std::isfinite(f32)) ? fabs(f32 - f64) / fabs(f64) : 1e-6;
-            ftol_c = std::max(ftol_c, 10.0 * err);
+            // no finer than the mixed path resolves ell: ten times its error at the start,
+            // and at least its stated relative accuracy (1e-6): between nearby points its
+            // FP32 rounding moves ell by about that much, more than at any single point
+            ftol_c = std::max(ftol_c, std::max(10.0 * err, 1e-6));
         }
         obj.reset(prec);
         // Newton first: trust-region steps on a central-difference model from the start
