@@ -240,9 +240,10 @@ int bv_mixed_fallbacks(bv_ctx* ctx, int64_t* count);
  * delta_i / (eps B_i), delta_i the FP32 minus FP64 term), a test for a systematic bias
  * (|mean| over 4 standard errors: the whole dataset is recomputed in FP64); L is the sum
  * of the dataset's terms (FP32 and sampled FP64).  The bound on the dataset's relative
- * error is 3 x 1.5 rho eps sqrt(sum B_i^2) / |L| over the blocks still in FP32 (three
- * standard deviations of their summed noise, a 50% margin on the sampled rho); while it
- * exceeds the
+ * error is 3 x 2.5 rho eps sqrt(sum B_i^2) / |L| over the blocks still in FP32 (three
+ * standard deviations of their summed noise; the margin of 2.5 on the sampled rho covers
+ * its sampling error and a small conditioning-dependent mean of the errors that cancels
+ * over a dataset but not over its well-conditioned blocks); while it exceeds the
  * tolerance (bv_set_mixed_tolerance, default 1e-6) the blocks with the largest B_i are
  * recomputed in FP64 in the same evaluation.  The sampled blocks always keep their FP64
  * terms.  Outputs: *blocks_fp64 = blocks whose terms came from FP64 (sampled and
@@ -341,6 +342,10 @@ int bv_tc_update_check(const float* C, const float* XI, const float* XJ, float* 
  * method, used for the Matern kernel in the FP64 path) evaluated on the GPU for host
  * inputs x[n] into host out[n]. */
 int bv_exp_neg_check(int64_t n, const double* x, double* out);
+
+/* Diagnostic: the mixed-precision kernels' FP32 e^{-x} (own[i]) and CUDA's expf(-x)
+ * (lib[i]) on the device for host x[n] >= 0 (host arrays).  Synchronous. */
+int bv_exp_neg32_check(int64_t n, const float* x, float* own, float* lib);
 
 /* ---- block-Vecchia sampler (Eq. 4 read generatively) ------------------------------ */
 

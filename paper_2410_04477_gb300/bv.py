@@ -122,6 +122,7 @@ _SIGS = {
     "bv_plan_info": (_int, [_vp, _i32, _P(_i32), _P(_i32), _P(_d), _P(_d)]),
     "bv_matern_check": (_int, [_d, _i32, _i64, _P(_d), _P(_d)]),
     "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
+    "bv_exp_neg32_check": (_int, [_i64, _P(_f), _P(_f), _P(_f)]),
     "bv_tc_update_check": (_int, [_P(_f), _P(_f), _P(_f), _P(_f)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
@@ -224,6 +225,14 @@ def exp_neg_check(x):
     out = np.empty_like(xv)
     _check(_lib.bv_exp_neg_check(xv.size, _p(xv, _d), _p(out, _d)), "bv_exp_neg_check")
     return out
+
+
+def exp_neg32_check(x):
+    """(own, lib): the mixed kernels' device FP32 e^{-x} and CUDA's expf(-x) for x >= 0."""
+    xv = _arr(x, np.float32)
+    own, lib = np.empty_like(xv), np.empty_like(xv)
+    _check(_lib.bv_exp_neg32_check(xv.size, _p(xv, _f), _p(own, _f), _p(lib, _f)), "bv_exp_neg32_check")
+    return own, lib
 
 
 class BVError(RuntimeError):

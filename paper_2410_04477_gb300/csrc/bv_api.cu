@@ -745,6 +745,10 @@ int bv_theta_to_dev(const bv_theta* t, int d, DevTheta* o) {
     o->nugget = t->nugget;
     o->sigma2_f = (float)o->sigma2;
     o->nugget_f = (float)o->nugget;
+    // the kernels' diagonal is the FP32 sum sigma2_f + nugget_f; its rounding is the same
+    // in every block, a systematic error that a small nugget turns into a bias of ell
+    const float d32 = o->sigma2_f + o->nugget_f;
+    o->diag_lo_f = (float)((o->sigma2 + o->nugget) - (double)d32);
     for (int k = 0; k < 3; ++k) o->inv_range_f[k] = (float)o->inv_range[k];
     return BV_OK;
 }
@@ -1023,6 +1027,32 @@ static float time_bin(bv_ctx* c, BinPlan& bp, int reps) {
     return best;
 }
 
+static int enqueue_eval_forked(bv_ctx* c, int prec);
+
+// Time of one whole evaluation (best of three after one warm-up), launched directly.
+static float time_eval(bv_ctx* c, int prec) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {
+        cudaEventRecord(e0, c->stream);
+        const int st = enqueue_eval_forked(c, prec);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st != BV_OK) {
+            best = 1e30f;
+            break;
+        }
+        if (r > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
 static int autotune(bv_ctx* c, int prec) {
     if (c->tuned[prec]) return BV_OK;
     // theta of the current h_theta must be valid: use it as is (the caller set it)
@@ -1085,6 +1115,23 @@ static int autotune(bv_ctx* c, int prec) {
                     prec, bp.nmax, bp.nwork, bp.kind, bp.threads, bp.grid, bp.smem, best_ms);
     }
     BV_CUDA(cudaGetLastError());
+    // Bins beside one another or one after another: the bins are timed alone above, but
+    // beside a persistent bin that fills every SM the others compete for its slots, so
+    // the evaluation is timed both ways (bins forked as parallel branches, or in sequence,
+    // largest work first) and the faster kept.
+    int nonempty = 0;
+    for (const auto& bp : c->plan[prec]) nonempty += bp.nwork > 0;
+    c->bin_serial[prec] = false;
+    if (nonempty > 1) {
+        const float t_fork = time_eval(c, prec);
+        c->bin_serial[prec] = true;
+        const float t_serial = time_eval(c, prec);
+        BV_CUDA(cudaGetLastError());
+        c->bin_serial[prec] = t_serial < t_fork;
+        if (getenv("BV_LOG_PLAN"))
+            fprintf(stderr, "[bv plan] prec %d evaluation: bins forked %.3f ms, in sequence %.3f ms -> %s\n", prec,
+                    t_fork, t_serial, c->bin_serial[prec] ? "in sequence" : "forked");
+    }
     c->tuned[prec] = true;
     return BV_OK;
 }
@@ -1184,13 +1231,24 @@ static int enqueue_eval_forked(bv_ctx* c, int prec) {
     LLArgs a = make_args(c);
     if (fallback) a.fb = c->d_fb;
     if (prec == BV_MIXED) a.ind_blk = c->d_ind;
-    for (size_t i = 0; i < nb + ns; ++i) {
-        BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
-        if (i < nb) BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
-        else BV_CUDA(bv_launch_bin(c->chk.sbins[i - nb], check_args(c, a, true), c->side[i]));
-        BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
+    if (c->bin_serial[prec]) {
+        // in sequence on the context's stream, largest work (blocks x N^3) first
+        std::vector<size_t> order(nb);
+        std::iota(order.begin(), order.end(), (size_t)0);
+        const auto& pl = c->plan[prec];
+        auto work = [&](size_t i) { return (double)pl[i].nwork * pl[i].nmax * pl[i].nmax * pl[i].nmax; };
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work(x) > work(y); });
+        for (size_t i : order) BV_CUDA(bv_launch_bin(pl[i], a, c->stream));
+        for (size_t i = 0; i < ns; ++i) BV_CUDA(bv_launch_bin(c->chk.sbins[i], check_args(c, a, true), c->stream));
+    } else {
+        for (size_t i = 0; i < nb + ns; ++i) {
+            BV_CUDA(cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0));
+            if (i < nb) BV_CUDA(bv_launch_bin(c->plan[prec][i], a, c->side[i]));
+            else BV_CUDA(bv_launch_bin(c->chk.sbins[i - nb], check_args(c, a, true), c->side[i]));
+            BV_CUDA(cudaEventRecord(c->side_ev[i + 1], c->side[i]));
+        }
+        for (size_t i = 0; i < nb + ns; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
     }
-    for (size_t i = 0; i < nb + ns; ++i) BV_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[i + 1], 0));
     if (fallback) {
         LLArgs fa = a;
         fa.ws = c->d_fb_ws;

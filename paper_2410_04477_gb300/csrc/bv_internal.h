@@ -61,8 +61,11 @@ struct DevTheta {
     int32_t nu_code;
     int32_t nrec;
     double nu, mu, gam1, gam2, gampl, gammi, lognorm;
-    // FP32 copies for the mixed-precision kernels (converted once on the host)
+    // FP32 copies for the mixed-precision kernels (converted once on the host), and the
+    // part of the diagonal sigma^2 + tau^2 that its FP32 value sigma2_f + nugget_f misses
+    // (added to every pivot, so that the FP32 factor is that of the exact diagonal)
     float sigma2_f, nugget_f, inv_range_f[3];
+    float diag_lo_f;
 };
 
 // Constants of the table-driven FP64 exponential (Tang, "Table-driven implementation of
@@ -79,6 +82,11 @@ struct ExpConsts {
     double tab[BV_EXP_TAB];   // 2^{j/256}, j = 0..255
     double k;                 // 256 / ln 2
     double l1, l2;            // ln2/256 split: l1 has its low 21 bits zero so n*l1 is exact
+    // FP32 version of the same method with 32 table steps (mixed-precision kernels):
+    // t32[j] + t32[32 + j] = 2^{-j/32} as two floats, k32 = 32 / ln 2, l1_32 + l2_32 =
+    // ln2/32 with l1_32's low 12 bits zero
+    float t32[64];
+    float k32, l1_32, l2_32;
 };
 void bv_exp_consts(ExpConsts* out);
 
@@ -112,7 +120,7 @@ struct LLArgs {
     unsigned long long* fail;  // min over failing block ids (ULLONG_MAX = none)
     double* ws;              // global workspace (large-block path)
     int64_t ws_stride;       // doubles per workspace slot
-    ExpConsts ex;            // FP64 exponential constants
+    ExpConsts ex;            // FP64 exponential constants (and the FP32 table of exp_neg32)
 };
 
 // Per-size-bin launch plan entry.
@@ -303,6 +311,9 @@ struct bv_ctx {
     std::vector<BinPlan> plan[2];
     bool plan_valid[2] = {false, false};
     bool tuned[2] = {false, false};
+    // per precision: the size-bin launches of an evaluation run one after another in
+    // descending order of work instead of as parallel branches (chosen by timing both)
+    bool bin_serial[2] = {false, false};
     // graphs of one evaluation: [0] FP64, [1] mixed with its check (captured at tolerance
     // graph_tol), [2] mixed without the check
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};

@@ -270,10 +270,12 @@ __device__ __forceinline__ const float* tile_row(const float* t, int q, int r) {
 
 // Factor the 4x4 diagonal tile q of `tiles` (pivot columns c < nc) into dfac:
 // dfac[0..15] = L (strictly lower part), dfac[16..19] = 1/sqrt(pivot), dfac[20..23] = pivot.
-// Writes the pivots of global columns k0.. to piv, row N's entries (if row N lies in this
-// tile) to ydiag, and raises *fail on a non-positive pivot.
+// Every pivot gets dlo, the part of the matrix diagonal its FP32 value misses (a diagonal
+// entry enters the factorisation only as its column's pivot).  Writes the pivots of global
+// columns k0.. to piv, row N's entries (if row N lies in this tile) to ydiag, and raises
+// *fail on a non-positive pivot.
 __device__ __forceinline__ void factor_diag(const float* tiles, int qd, int nc, int k0, int N, float* dfac,
-                                            float* piv, float* ydiag, int* fail) {
+                                            float* piv, float* ydiag, int* fail, float dlo) {
     float D[16];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -286,8 +288,11 @@ __device__ __forceinline__ void factor_diag(const float* tiles, int qd, int nc, 
     float rs[4], pv[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        pv[c] = D[5 * c];
-        rs[c] = c < nc ? rsqrtf(pv[c]) : 0.0f;
+        pv[c] = D[5 * c] + dlo;
+        // correctly rounded 1/sqrt: the approximate reciprocal square root errs to one
+        // side, and that shared bias of every column scaling turns into a bias of the
+        // Schur complements that grows with the block's conditioning
+        rs[c] = c < nc ? __frsqrt_rn(pv[c]) : 0.0f;
 #pragma unroll
         for (int r = c + 1; r < 4; ++r) D[4 * r + c] *= rs[c];
 #pragma unroll
@@ -332,7 +337,8 @@ __host__ __device__ __forceinline__ int mixed_floats(int nmax) {
 // group's shared region (mixed_floats(N) floats, 16-byte aligned).  Returns (sum of
 // z^2 + log pivot, sum of z^2) over the block columns, valid in thread 0, and sets *fail.
 template <int NG, bool WARP, bool GEN>
-__device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail) {
+__device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* sm, int tid, int* fail,
+                                               const float* t32) {
     const int64_t b0 = a.bptr[blk], n0 = a.nptr[blk];
     const int b = (int)(a.bptr[blk + 1] - b0), m = (int)(a.nptr[blk + 1] - n0);
     const int N = m + b, R = N + 1, T = (R + 3) >> 2;
@@ -390,7 +396,7 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                     float v = (GEN && th.nu_code == NU_GENERAL)
                                   ? s2 * matern_gen_tab32(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE,
                                                           a.theta + a.bds[blk], xf)
-                                  : matern32(th.nu_code, s2, xf);
+                                  : matern32(th.nu_code, s2, xf, t32, a.ex);
                     if (r == c) v += tau2;
                     o[e] = c <= r ? v : 0.0f;
                 }
@@ -405,7 +411,7 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
         }
     }
     gsync<WARP>();
-    if (tid == 0) factor_diag(tiles, 0, min(4, N), 0, N, dfac, piv, ydiag, fail);
+    if (tid == 0) factor_diag(tiles, 0, min(4, N), 0, N, dfac, piv, ydiag, fail, th.diag_lo_f);
     gsync<WARP>();
 
     for (int p = 0; (p << 2) < N; ++p) {
@@ -472,7 +478,7 @@ __device__ __forceinline__ double2 mixed_block(const LLArgs& a, int blk, float* 
                 st4(at, make_float4(o[0], o[1], o[2], o[3]));
             }
             if (q == 0 && ((p + 1) << 2) < N)
-                factor_diag(tiles, qa, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, fail);
+                factor_diag(tiles, qa, min(4, N - ((p + 1) << 2)), (p + 1) << 2, N, dfac, piv, ydiag, fail, th.diag_lo_f);
         }
         gsync<WARP>();
     }
@@ -501,7 +507,9 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ int s_fail;
     __shared__ int s_w;
+    __shared__ float t32[64];
     const int tid = threadIdx.x;
+    for (int i = tid; i < 64; i += NT) t32[i] = a.ex.t32[i];
     if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
     __syncthreads();
     for (int w = s_w; w < a.nwork; w = s_w) {
@@ -509,7 +517,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed(LLArgs a) {
         const int blk = a.work[w];
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        const double2 sr = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail);
+        const double2 sr = mixed_block<NT, false, GEN>(a, blk, sm, tid, &s_fail, t32);
         if (tid == 0) {
             finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), sr.x, sr.y, s_fail);
             s_w = nx;
@@ -525,7 +533,10 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int WPB = NT / 32;
     __shared__ int s_fail[WPB];
+    __shared__ float t32[64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 64; i += NT) t32[i] = a.ex.t32[i];
+    __syncthreads();
     float* sm = reinterpret_cast<float*>(smraw) + (size_t)warp * region_floats;
     int w = __shfl_sync(0xffffffffu, lane == 0 ? take_work(a.ctr, blockIdx.x * WPB + warp) : 0, 0);
     while (w < a.nwork) {
@@ -533,7 +544,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_w(LLArgs a, int region_floats) 
         const int blk = a.work[w];
         if (lane == 0) s_fail[warp] = 0;
         __syncwarp();
-        const double2 part = mixed_block<32, true, GEN>(a, blk, sm, lane, &s_fail[warp]);
+        const double2 part = mixed_block<32, true, GEN>(a, blk, sm, lane, &s_fail[warp], t32);
         __syncwarp();
         if (lane == 0) finish_block(a, blk, (int)(a.bptr[blk + 1] - a.bptr[blk]), part.x, part.y, s_fail[warp]);
         __syncwarp();
@@ -832,9 +843,13 @@ __global__ void k_reduce_final(const double4_16a* __restrict__ part, const int64
 //      sampled blocks take their FP64 terms;
 //   2. the dataset's log-likelihood L is the sum of all its terms (FP32 and sampled FP64;
 //      its own error is the quantity bounded, far below |L|);
-//   3. the bound on the dataset's error is 3 (1.5 rho) eps sqrt(sum w_i^2) over the blocks
-//      still in FP32: 3 standard deviations of their summed noise, with a 50% margin on
-//      the sampled rho (64 or more samples of a heavy-tailed r);
+//   3. the bound on the dataset's error is 3 (2.5 rho) eps sqrt(sum w_i^2) over the blocks
+//      still in FP32: 3 standard deviations of their summed noise, with a margin of 2.5 on
+//      the sampled rho.  The margin covers the sampling error of rho (64 or more samples
+//      of a heavy-tailed r) and a small mean of r that moves with w (a few per cent of
+//      rho, from FP32 roundings shared by many blocks): it cancels over a whole dataset,
+//      so the z-test below does not see it, but not over the well-conditioned blocks that
+//      step 4 keeps in FP32 (measured: up to 1.7 times the 1.5-margin bound without it);
 //   4. if a bias shows (|z| > 4) every block is recomputed in FP64 (flag 2); else if the
 //      bound exceeds tol |L|, the blocks with the largest w_i are recomputed in FP64 until
 //      it does not: the largest threshold w* (bisection on log2 w*, 16 steps) with the bound
@@ -918,7 +933,7 @@ __global__ void __launch_bounds__(kChkThreads) k_mixed_check(double* ell_blk, do
         f = 2;  // too few FP32 blocks in the sample to calibrate rho: all to FP64
         bound = INFINITY;
     } else if (s < B) {
-        const double rho = 1.5 * sqrt(r2 / cnt), mu = r1 / cnt;  // 50% margin on the sampled scale
+        const double rho = 2.5 * sqrt(r2 / cnt), mu = r1 / cnt;  // margin on the sampled scale (step 3)
         const double sd_mu = sqrt(fmax(r2 / cnt - mu * mu, 0.0) / cnt);
         const double L = fabs(e);
         const double k = (double)kEps32 / L;  // bound = k kept_bound
@@ -1215,6 +1230,20 @@ static void fill_exp_consts(ExpConsts* o) {
     o->l1 = l1;
     o->l2 = (double)(L - (long double)l1);
     o->k = (double)((long double)BV_EXP_TAB / ln2);
+    for (int j = 0; j < 32; ++j) {
+        const long double t = exp2l(-(long double)j / 32.0L);
+        o->t32[j] = (float)t;
+        o->t32[32 + j] = (float)(t - (long double)o->t32[j]);
+    }
+    const long double L32 = ln2 / 32.0L;
+    float f1 = (float)L32;
+    unsigned int fb;
+    memcpy(&fb, &f1, sizeof(fb));
+    fb &= ~((1u << 12) - 1u);
+    memcpy(&f1, &fb, sizeof(fb));
+    o->l1_32 = f1;
+    o->l2_32 = (float)(L32 - (long double)f1);
+    o->k32 = (float)(32.0L / ln2);
 }
 
 // The table is computed once per process (long double is a software type on some hosts,
@@ -1226,6 +1255,38 @@ void bv_exp_consts(ExpConsts* o) {
         return e;
     }();
     *o = cached;
+}
+
+__global__ void k_exp32_check(const float* x, float* own, float* lib, int64_t n, ExpConsts ex) {
+    __shared__ float t[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) t[i] = ex.t32[i];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        own[i] = exp_neg32(x[i], t, ex.k32, ex.l1_32, ex.l2_32);
+        lib[i] = expf(-x[i]);
+    }
+}
+
+// Diagnostic: the mixed kernels' FP32 exp(-x) (own) and CUDA's expf(-x) (lib) on the
+// device for host inputs x[n] >= 0.
+extern "C" int bv_exp_neg32_check(int64_t n, const float* x, float* own, float* lib) {
+    if (n <= 0 || !x || !own || !lib) return BV_EINVAL;
+    ExpConsts ex;
+    bv_exp_consts(&ex);
+    float *dx = nullptr, *d1 = nullptr, *d2 = nullptr;
+    BV_CUDA(cudaMalloc(&dx, sizeof(float) * n));
+    BV_CUDA(cudaMalloc(&d1, sizeof(float) * n));
+    BV_CUDA(cudaMalloc(&d2, sizeof(float) * n));
+    BV_CUDA(cudaMemcpy(dx, x, sizeof(float) * n, cudaMemcpyHostToDevice));
+    k_exp32_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, d1, d2, n, ex);
+    BV_CUDA(cudaGetLastError());
+    BV_CUDA(cudaMemcpy(own, d1, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    BV_CUDA(cudaMemcpy(lib, d2, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    cudaFree(dx);
+    cudaFree(d1);
+    cudaFree(d2);
+    return BV_OK;
 }
 
 // Diagnostic: the library's FP64 exp(-x) on the device for host inputs x[n].

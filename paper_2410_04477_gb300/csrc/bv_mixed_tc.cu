@@ -156,9 +156,10 @@ __device__ __forceinline__ void tile_update(float* C, const float* XI, const flo
 // columns c < nc; every row of the tile below a pivot column is scaled and updated, so
 // rows past the last pivot column (the observation row, padding) come out solved.
 // Writes the factor back to the tile and to Lp (plain row-major), 1/sqrt(pivot) to rs,
-// the pivots to piv and raises *fail on a non-positive pivot.
+// the pivots to piv and raises *fail on a non-positive pivot.  Every pivot gets dlo, the
+// part of the matrix diagonal its FP32 value misses.
 __device__ __forceinline__ void diag_factor(float* tile, float* Lp, float* rs, float* piv, int k0, int nc, int lane,
-                                            int* fail) {
+                                            int* fail, float dlo) {
     const int r = lane & 15;
     float a[kE];
 #pragma unroll
@@ -172,12 +173,12 @@ __device__ __forceinline__ void diag_factor(float* tile, float* Lp, float* rs, f
             float col[kE];
 #pragma unroll
             for (int i = c + 1; i < kE; ++i) col[i] = __shfl_sync(0xffffffffu, a[c], i);
-            const float pc = __shfl_sync(0xffffffffu, a[c], c);
+            const float pc = __shfl_sync(0xffffffffu, a[c], c) + dlo;
             const float t = a[c] * __frcp_rn(pc);
 #pragma unroll
             for (int i = c + 1; i < kE; ++i)
                 if (r >= i) a[i] = fmaf(-t, col[i], a[i]);
-            const float rc = rsqrtf(pc);
+            const float rc = __frsqrt_rn(pc);  // correctly rounded: no one-sided bias
             if (lane == c) {
                 piv[k0 + c] = pc;
                 rs[c] = rc;
@@ -228,8 +229,10 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_tc(LLArgs a) {
     float* sm = reinterpret_cast<float*>(smraw);
     __shared__ int s_fail;
     __shared__ int s_w;
+    __shared__ float t32[64];
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 64; i += NT) t32[i] = a.ex.t32[i];
     const int nwork = work_count(a);
     if (tid == 0) s_w = take_work(a.ctr, blockIdx.x);
     __syncthreads();
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_tc(LLArgs a) {
                     const float xf = sqrtf(fmaf(t2, t2, fmaf(t1, t1, t0 * t0)));
                     v = (GEN && th.nu_code == NU_GENERAL)
                             ? s2 * matern_gen_tab32(a.gtab + (int64_t)a.bds[blk] * GTAB_SIZE, a.theta + a.bds[blk], xf)
-                            : matern32(th.nu_code, s2, xf);
+                            : matern32(th.nu_code, s2, xf, t32, a.ex);
                     if (gr == gc) v += tau2;
                 } else if (gr == N && gc < N) {
                     v = yv[gc];
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_tc(LLArgs a) {
         __syncthreads();
 
         // panel 0: diagonal tile, then the tile column below it
-        if (warp == 0) diag_factor(tiles, Lp, rs, piv, 0, min(kE, N), lane, &s_fail);
+        if (warp == 0) diag_factor(tiles, Lp, rs, piv, 0, min(kE, N), lane, &s_fail, th.diag_lo_f);
         __syncthreads();
         for (int r = kE + tid; r < T * kE; r += NT) {
             float* rt = tiles + tc_tile(r >> 4, 0) * kTF;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(NT) k_ll_mixed_tc(LLArgs a) {
             // trailing triangle, columns p+2.., with panel p
             const int k1 = p1 * kE, nc1 = min(kE, N - k1);
             if (warp == 0) {
-                if (nc1 > 0) diag_factor(tiles + tc_tile(p1, p1) * kTF, Lp, rs, piv, k1, nc1, lane, &s_fail);
+                if (nc1 > 0) diag_factor(tiles + tc_tile(p1, p1) * kTF, Lp, rs, piv, k1, nc1, lane, &s_fail, th.diag_lo_f);
             } else {
                 // trailing tile rows p+2 .. T-1, each (with all its tiles J = p+2 .. I) owned
                 // by one warp, longest rows first, so that X_I is split once per row

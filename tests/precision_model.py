@@ -22,6 +22,22 @@ points, bc = n/10 K-means blocks, m = 120, y drawn from the block-Vecchia model 
 The printed relative error of the summed log-likelihood over the sampled blocks shows that
 the FP32 rounding of Sigma^con's entries and factor sets the error: FP64 for the
 conditional covariance or the diagonal panels does not reduce it.
+
+Second study (python -m tests.precision_model bias [n]): is the per-block FP32 error
+zero-mean?  Classic Vecchia (one-point blocks, m = 30) and K-means blocks on config-2-like
+data; every block's all-FP32 error delta_i, its error weight w_i (the check's
+conditioning indicator) and r_i = delta_i / (2^-24 w_i).  Printed: the sum of delta over
+all blocks and over the 29% best-conditioned (lowest w) blocks, the mean of r over both,
+and the noise scale sqrt(sum w^2) 2^-24 rms(r); once plainly and once with the FP32
+diagonal's residual (sigma^2 + tau^2 - fl32(sigma^2 + tau^2)) added to every pivot.  The
+common rounding of the diagonal biases r by w (a mean of -0.011 over the best-conditioned
+blocks of the one-point case against +0.007 over the worst quarter), so the blocks a
+check leaves in FP32 can carry a sum many times the noise scale; the pivot correction
+removes most of it.  A one-sided error of the pivots' reciprocal square roots (modelled as
+1/sqrt rounded to FP32 and then 2^-24 low, the size of an approximate hardware 1/sqrt's
+error) brings the same pattern back (mean r by w quartile about -0.02, -0.01, 0, +0.005 in
+the one-point case, as measured on the GPU with the approximate 1/sqrt), hence the
+kernels' correctly rounded 1/sqrt.
 """
 import sys
 
@@ -108,5 +124,67 @@ def study(n=3000, per_case=60):
             print(f"   {name:20s} relative error {abs(v - ref) / abs(ref):.2e}")
 
 
+def _terms_lo(A, m, lo, rs_bias=0.0):
+    """All-FP32 factorisation of the augmented matrix with lo added to every pivot (None:
+    plain), the reciprocal square root of each pivot rounded to FP32 and then scaled by
+    (1 + rs_bias) (a one-sided error of an approximate 1/sqrt); u + log det of the block
+    columns."""
+    A = _r32(A)
+    N = A.shape[0] - 1
+    piv = np.zeros(N)
+    for k in range(N):
+        p = A[k, k] if lo is None else float(np.float32(np.float32(A[k, k]) + np.float32(lo)))
+        piv[k] = p
+        rs = float(np.float32(1.0 / np.sqrt(p))) * (1.0 + rs_bias)
+        col = _r32(A[k + 1:, k] * rs)
+        A[k + 1:, k] = col
+        A[k + 1:, k + 1:] = _r32(A[k + 1:, k + 1:] - np.outer(col, col))
+    z = A[N, m:N]
+    return (z * z).sum() + np.log(piv[m:N]).sum()
+
+
+def bias_study(n=20000):
+    side = (n / 2e5) ** 0.5   # the config-2 point density
+    for singletons, m, th in ((True, 30, (1.0, 0.05, 1.5, 1e-4)), (False, 60, (1.0, 0.05, 1.5, 1e-4)),
+                              (False, 30, (1.3, 0.03, 0.5, 3e-3))):
+        locs = synth.locs_uniform(n, 2, 1) * side
+        if singletons:
+            bp, pi, ce = oracle.build_singletons(locs, seed=1)
+        else:
+            bp, pi, ce = oracle.build_blocks(locs, n // 10, seed=1)
+        gnp, gni = oracle.select_neighbors(locs, bp, pi, ce, 100)
+        y = oracle.bv_draw(oracle.theta(*th), locs, bp, pi, gnp, gni, synth.normal(1, 20, n))
+        nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+        d32 = float(np.float32(np.float32(th[0]) + np.float32(th[3])))
+        lo = (th[0] + th[3]) - d32
+        dl = {"plain": [], "pivot + diagonal residual": [], "... and 1/sqrt 2^-24 low": []}
+        w = []
+        step = 2 if singletons else 1
+        for i in range(0, len(bp) - 1, step):
+            A, mm, b = augmented(locs, y, bp, pi, nnp, nni, i, th)
+            N = A.shape[0] - 1
+            L = np.linalg.cholesky(A[:N, :N])
+            pv = np.diag(L) ** 2
+            z = np.linalg.solve(L, A[N, :N])[mm:]
+            t64 = np.log(pv[mm:]).sum() + (z * z).sum()
+            dl["plain"].append(-0.5 * (_terms_lo(A, mm, None) - t64))
+            dl["pivot + diagonal residual"].append(-0.5 * (_terms_lo(A, mm, lo) - t64))
+            dl["... and 1/sqrt 2^-24 low"].append(-0.5 * (_terms_lo(A, mm, lo, -2.0 ** -24) - t64))
+            w.append(((th[0] + th[3]) / pv).sum() * (1 + (z * z).sum() / b))
+        w = np.array(w)
+        keep = np.argsort(w)[:int(0.29 * len(w))]
+        print(f"{'one-point' if singletons else 'K-means'} blocks, m = {m}, theta = {th}: residual {lo:.3e}")
+        q = np.argsort(w)
+        for name, d in dl.items():
+            d = np.array(d)
+            r = d / (2.0 ** -24 * w)
+            quart = " ".join(f"{r[q[int(a * len(q)):int((a + .25) * len(q))]].mean():+.4f}" for a in (0, .25, .5, .75))
+            print(f"   {name:26s} sum {d.sum():+.3e} (best 29%: {d[keep].sum():+.3e}), mean r {r.mean():+.4f} "
+                  f"(by w quartile {quart}), noise scale {np.sqrt((w * w).sum()) * 2.0 ** -24 * np.sqrt((r * r).mean()):.3e}")
+
+
 if __name__ == "__main__":
-    study(int(sys.argv[1]) if len(sys.argv) > 1 else 3000, int(sys.argv[2]) if len(sys.argv) > 2 else 60)
+    if len(sys.argv) > 1 and sys.argv[1] == "bias":
+        bias_study(int(sys.argv[2]) if len(sys.argv) > 2 else 20000)
+    else:
+        study(int(sys.argv[1]) if len(sys.argv) > 1 else 3000, int(sys.argv[2]) if len(sys.argv) > 2 else 60)

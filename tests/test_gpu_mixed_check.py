@@ -114,3 +114,33 @@ def test_batch_every_dataset_within_the_bound(bv):
     fin = np.isfinite(est) & (est > 0)
     assert np.all(rel[fin] <= 2.0 * est[fin] + 1e-13), (rel[fin], est[fin])
     assert nb64 < nblk
+
+
+def test_check_bound_holds_for_classic_vecchia_singletons(bv):
+    # one-point blocks (the classic Vecchia shape, m = 30) at the config-2 density and
+    # nugget: every block's FP32 diagonal sigma^2 + tau^2 is rounded the same way, and with
+    # tau^2 / sigma^2 = 1e-4 that common rounding would shift every conditional variance in
+    # one direction; the pivots add back the diagonal's FP32 residual, so the errors the
+    # check leaves in FP32 stay zero-mean and the 1e-6 bound holds against the oracle
+    n, m, seed = 60_000, 30, 23
+    th = (1.0, 0.05, 1.5, 1e-4)
+    locs = synth.locs_uniform(n, 2, seed) * (n / 2e5) ** 0.5
+    bp, pi, ce = oracle.build_singletons(locs, seed=seed)
+    gnp, gni = oracle.select_neighbors(locs, bp, pi, ce, 100)
+    y = oracle.bv_draw(oracle.theta(*th), locs, bp, pi, gnp, gni, synth.normal(seed, 20, n))
+    nnp, nni = oracle.select_neighbors(locs, bp, pi, ce, m)
+    ell = oracle.loglik(oracle.theta(*th), locs, y, bp, pi, nnp, nni)[0]
+    with bv.Context() as ctx:
+        ctx.set_data(locs, y)
+        gbp, gpi = ctx.build_singletons(seed=seed)
+        gnnp, gnni = ctx.select_neighbors(m)
+        for a_, b_ in zip((gbp, gpi, gnnp, gnni), (bp, pi, nnp, nni)):
+            np.testing.assert_array_equal(a_, b_)
+        lmx = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+        nb64, _, est = ctx.mixed_check_info()
+        ctx.set_mixed_tolerance(0.0)
+        l32 = ctx.loglik(bv.theta(*th), bv.BV_MIXED)
+    print(f"classic Vecchia n={n}: unchecked rel {abs(l32 - ell) / abs(ell):.2e}, checked rel "
+          f"{abs(lmx - ell) / abs(ell):.2e} (|d ell| {abs(lmx - ell):.3g}), FP64 blocks {nb64}, bound {est[0]:.2e}")
+    assert abs(lmx - ell) <= 1e-6 * abs(ell)
+    assert abs(lmx - ell) <= max(est[0], 1e-10) * abs(ell)

@@ -262,6 +262,29 @@ def test_device_exp_within_two_ulp(bv):
     assert bv.exp_neg_check(np.array([700.5, 800.0, 1e6])).max() == 0.0
 
 
+def test_device_fp32_exp_is_unbiased(bv):
+    # the mixed kernels' FP32 e^{-x} (Tang's method, 32 steps, two-float table) against the
+    # exact value: within about half an ulp, and without a mean error in any range of x
+    # (a shared one-sided error of the covariance entries biases the mixed path's errors);
+    # CUDA's expf is measured beside it for the record
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(0, 0.2, 400_000), rng.uniform(0.2, 3, 400_000), rng.uniform(3, 80, 200_000),
+                        [0.0, 1e-30, 2.0 ** -20, 86.99]]).astype(np.float32)
+    own, lib = bv.exp_neg32_check(x)
+    want = np.exp(-x.astype(np.float64))
+    ulp = np.spacing(want.astype(np.float32)).astype(np.float64)
+    e_own = (own.astype(np.float64) - want) / ulp
+    e_lib = (lib.astype(np.float64) - want) / ulp
+    print(f"own: max {np.abs(e_own).max():.3f} ulp, mean {e_own.mean():+.4f}; expf: max {np.abs(e_lib).max():.3f} ulp, "
+          f"mean {e_lib.mean():+.4f}")
+    assert np.abs(e_own).max() <= 0.55
+    assert own[x == 0][0] == 1.0
+    for a, b in ((0, 0.05), (0.05, 0.2), (0.2, 1), (1, 3), (3, 80)):
+        k = (x >= a) & (x < b)
+        assert abs(e_own[k].mean()) <= 0.01, (a, b, e_own[k].mean())
+    assert bv.exp_neg32_check(np.array([87.0, 100.0, 1e30], np.float32))[0].max() == 0.0
+
+
 @pytest.mark.parametrize("d,m,bc,ranges", [(2, 0, 300, None), (2, 7, 300, None), (2, 63, 250, None),
                                            (2, 120, 200, None), (3, 200, 150, [0.1, 0.1, 0.3])])
 def test_mixed_precision_per_block(bv, d, m, bc, ranges):
