@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5 a
 # DRAM bytes (read + write) of one evaluation's likelihood-kernel launches, summed over
 # the size bins, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
 # reported as roofline.traffic for these workloads and precisions only.
-NCU_TRAFFIC = {("c2_m60", "fp64"): 40_704 + 36_864 + 632_576 + 10_817_280 + 2_585_856 + 42_240,
+NCU_TRAFFIC = {("c2_m60", "fp64"): 636_160 + 10_996_224 + 2_597_376 + 40_704 + 36_864 + 34_816,
                # config 3: the main bin's 5,937,920 bytes at n-scale 0.05 (4,974 of its 99,949
                # blocks; the other bins hold 51 blocks), times 20
                ("c3", "fp64"): 20 * 5_937_920}
