@@ -791,7 +791,9 @@ def main():
     ctx = bv.Context(local, stream.cuda_stream)
     locs, y_true, setup = setup_gpu(bv, ctx, w, log)
     thetas = make_thetas(bv, w, args.warmup + args.steps, w["seed"])
-    ctx.autotune(prec)
+    # plan, autotune and graph capture at the workload's own smoothness and scale (the
+    # first evaluation tunes at its theta; the kernels' cost depends on the Matern form)
+    ctx.loglik_multi(thetas[0], prec)
     info = ctx.plan_info(prec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     nd = len(thetas[0])

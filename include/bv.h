@@ -310,9 +310,16 @@ int bv_loglik_noalloc(const bv_theta* theta, const double* d_locs, const double*
 
 /* Run the launch-shape autotuner for `precision` now (otherwise it runs on first use).
  * Times each candidate of every size bin on the current structure and the current
- * parameters: one CTA per block with 96, 160, 288 or 544 threads, and for small blocks
- * (FP64 N <= 64, mixed N <= 128) one warp per block with 2, 4 or 8 warps per CTA.  The
- * environment variable BV_KERNEL_FORM=cta or =warp restricts the candidates to one form.
+ * parameters -- the theta of the last evaluation, or sigma^2 = 1, range 0.1, nu = 1/2,
+ * tau^2 = 1e-3 if none has run; the kernels' cost depends on the Matern form, so an
+ * evaluation at representative parameters first (which tunes on first use) gives the
+ * better plan.  Candidates: one CTA per block with 96, 160, 288 or 544 threads (FP64 with
+ * one- or two-column factorisation steps, and 1024 threads for N >= 128), one warp per
+ * block with 2, 4 or 8 warps per CTA for small blocks (FP64 N <= 64, mixed N <= 128), the
+ * tensor-core form for mixed N >= 64; then the whole evaluation with the size bins as
+ * parallel branches or in sequence.  The graph of an evaluation is timed against the
+ * same launches issued directly on first use, and the faster is kept.  The environment
+ * variable BV_KERNEL_FORM=cta, cta2, warp or tc restricts the candidates to one form.
  * Every form does the same per-block arithmetic, so the choice changes speed only (the
  * FP64 result is bit-identical across re-tuned plans).  Errors: BV_EINVAL (precision),
  * BV_ESTATE (no neighbours selected yet), BV_ECUDA. */

@@ -84,6 +84,7 @@ static void free_plan(bv_ctx* c, int prec) {
     for (int slot : {prec, prec == BV_MIXED ? 2 : prec}) {
         if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
         c->graph[slot] = nullptr;
+        c->eval_direct_known[slot] = false;
     }
 }
 
@@ -1151,6 +1152,7 @@ extern "C" int bv_autotune(bv_ctx* c, int32_t prec) {
     for (int slot : {prec, prec == BV_MIXED ? 2 : prec}) {
         if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
         c->graph[slot] = nullptr;
+        c->eval_direct_known[slot] = false;
     }
     return autotune(c, prec);
 }
@@ -1286,6 +1288,35 @@ static int ensure_graph(bv_ctx* c, int prec) {
     e = cudaGraphInstantiate(&c->graph[slot], g, 0);
     cudaGraphDestroy(g);
     BV_CUDA(e);
+    if (!c->eval_direct_known[slot]) {
+        // The graph against the same launches issued directly: with several size bins as
+        // parallel branches the graph has run up to 20% slower than the streams (config
+        // 2: 5.55 against 4.65 ms per evaluation), so the faster of the two is kept.
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float tg = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(e0, c->stream);
+            const cudaError_t el = cudaGraphLaunch(c->graph[slot], c->stream);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (el != cudaSuccess) break;
+            if (r > 0) tg = std::min(tg, ms);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        BV_CUDA(cudaGetLastError());
+        const float td = time_eval(c, prec);
+        BV_CUDA(cudaGetLastError());
+        c->eval_direct[slot] = td < 0.98f * tg;
+        c->eval_direct_known[slot] = true;
+        if (getenv("BV_LOG_PLAN"))
+            fprintf(stderr, "[bv plan] graph slot %d: graph %.3f ms, direct launches %.3f ms -> %s\n", slot, tg, td,
+                    c->eval_direct[slot] ? "direct" : "graph");
+    }
     return BV_OK;
 }
 
@@ -1295,7 +1326,9 @@ int bv_enqueue_loglik(bv_ctx* c, int prec, double* d_out, bool) {
     BV_TRY(ensure_graph(c, prec));
     BV_CUDA(cudaMemcpyAsync(c->d_theta, c->h_theta.data(), sizeof(DevTheta) * c->ndata, cudaMemcpyHostToDevice,
                             c->stream));
-    BV_CUDA(cudaGraphLaunch(c->graph[graph_slot(c, prec)], c->stream));
+    const int slot = graph_slot(c, prec);
+    if (c->eval_direct[slot]) BV_TRY(enqueue_eval_forked(c, prec));
+    else BV_CUDA(cudaGraphLaunch(c->graph[slot], c->stream));
     if (d_out && d_out != c->d_out)
         BV_CUDA(cudaMemcpyAsync(d_out, c->d_out, sizeof(double) * c->ndata, cudaMemcpyDeviceToDevice, c->stream));
     return BV_OK;

@@ -317,6 +317,10 @@ struct bv_ctx {
     // graphs of one evaluation: [0] FP64, [1] mixed with its check (captured at tolerance
     // graph_tol), [2] mixed without the check
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    // per graph slot: launch the evaluation's kernels directly instead of the graph
+    // (decided once per plan by timing both), and whether that was decided
+    bool eval_direct[3] = {false, false, false};
+    bool eval_direct_known[3] = {false, false, false};
     double graph_tol = 0.0;
     bool graph_gen[3] = {false, false, false};  // whether each graph holds the general-nu kernels
     bool cur_gen = false;                 // whether the current theta needs them
