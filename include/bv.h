@@ -404,6 +404,18 @@ int bv_mle(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const bv_the
            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat,
            double* loglik_hat, int32_t* n_evals);
 
+/* Test support (host only, no device): bv_mle's search -- the same stages, options and
+ * box handling -- on a synthetic likelihood instead of the block-Vecchia one, so that the
+ * optimizer's logic can be checked on a CPU.  model[8] = (n, beta0, eta0, c_q, a, b, c_uv,
+ * k); with u = log(beta / beta0), v = log(eta / eta0), eta = tau^2 / sigma^2,
+ * Q = n exp(c_q u), D = n (a u^2 + b v^2 + c_uv u v + k (u^4 + v^4)) and
+ * ell = -(Q / sigma^2 + D + n log sigma^2 + n log 2 pi) / 2; BV_MIXED evaluations add
+ * n 1e-7 sin(1e3 (u + 2 v)).  Other arguments and outputs as bv_mle. */
+int bv_mle_check(const double* model, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+                 uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
+                 int32_t* n_evals);
+
+
 /* ---- prediction (Sec. 2.4, Algorithm 2) ----------------------------------------- */
 
 /* New locations S* (n_star x d, row-major, host; d as set by bv_set_data) and optionally

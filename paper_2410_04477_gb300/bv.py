@@ -123,6 +123,8 @@ _SIGS = {
     "bv_matern_check": (_int, [_d, _i32, _i64, _P(_d), _P(_d)]),
     "bv_exp_neg_check": (_int, [_i64, _P(_d), _P(_d)]),
     "bv_exp_neg32_check": (_int, [_i64, _P(_f), _P(_f), _P(_f)]),
+    "bv_mle_check": (_int, [_P(_d), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bv_tc_update_check": (_int, [_P(_f), _P(_f), _P(_f), _P(_f)]),
     "bv_simulate": (_int, [_vp, _P(bv_theta), _P(_d), _P(_d)]),
     "bv_mle": (_int, [_vp, _P(bv_theta), _P(bv_theta), _P(bv_theta), _u32, _P(bv_mle_opts),
@@ -225,6 +227,22 @@ def exp_neg_check(x):
     out = np.empty_like(xv)
     _check(_lib.bv_exp_neg_check(xv.size, _p(xv, _d), _p(out, _d)), "bv_exp_neg_check")
     return out
+
+
+def mle_check(model, th0, lo, hi, free_mask=None, precision=None, max_evals=2000, ftol_rel=1e-10, xtol=1e-7,
+              init_step=0.5, init_step_nugget=0.0, newton_first=True):
+    """bv_mle's search on the host-evaluated synthetic likelihood of bv_mle_check:
+    (theta_hat, loglik_hat, evaluations, status)."""
+    free_mask = BV_FREE_SIGMA2 | BV_FREE_RANGE | BV_FREE_NUGGET if free_mask is None else free_mask
+    precision = BV_FP64 if precision is None else precision
+    mv = _arr(model, np.float64)
+    o = bv_mle_opts(precision, max_evals, ftol_rel, xtol, init_step, init_step_nugget, int(newton_first), 0)
+    out = bv_theta()
+    ll = ctypes.c_double(0.0)
+    ne = ctypes.c_int32(0)
+    st = _lib.bv_mle_check(_p(mv, _d), ctypes.byref(th0), ctypes.byref(lo), ctypes.byref(hi), free_mask,
+                           ctypes.byref(o), ctypes.byref(out), ctypes.byref(ll), ctypes.byref(ne))
+    return out, ll.value, ne.value, st
 
 
 def exp_neg32_check(x):

@@ -661,6 +661,51 @@ extern "C" int bv_mle(bv_ctx* c, const bv_theta* theta0, const bv_theta* lo, con
 }
 
 // ------------------------------------------------------------------------------------
+// Test support: bv_mle's search on a synthetic likelihood evaluated on the host, so that
+// the optimizer's logic (profiling, trust-region Newton, simplex fallback, the box) runs
+// without a device.  With u = log(beta / beta0), v = log(eta / eta0), eta = tau^2 / sigma^2:
+//     Q = n exp(c_q u),  D = n (a u^2 + b v^2 + c_uv u v + k (u^4 + v^4)),
+//     ell = -(Q / sigma^2 + D + n log sigma^2 + n log 2 pi) / 2,
+// the profile form of Eq. 4's sum; a mixed-precision evaluation adds the deterministic
+// perturbation n * 1e-7 * sin(1e3 (u + 2 v)) (a stand-in for FP32 rounding).
+// ------------------------------------------------------------------------------------
+namespace {
+struct SyntheticEval : Evaluator {
+    double n, lb0, le0, cq, a, b, cuv, k;
+    int eval(const bv_theta& t, int prec, bool, double* ll, double* Q) override {
+        if (!(t.sigma2 > 0.0) || !(t.range[0] > 0.0) || !(t.nugget > 0.0)) return BV_ENOTPD;
+        const double u = log(t.range[0]) - lb0, v = log(t.nugget / t.sigma2) - le0;
+        const double q = n * exp(cq * u);
+        const double D = n * (a * u * u + b * v * v + cuv * u * v + k * (u * u * u * u + v * v * v * v));
+        double l = -0.5 * (q / t.sigma2 + D + n * log(t.sigma2) + n * kLog2PiHost);
+        if (prec == BV_MIXED) l += n * 1e-7 * sin(1e3 * (u + 2.0 * v));
+        *ll = l;
+        *Q = q / t.sigma2;  // the quadratic form at this sigma^2
+        return BV_OK;
+    }
+    static constexpr double kLog2PiHost = 1.8378770664093454835606594728112;
+};
+}  // namespace
+
+extern "C" int bv_mle_check(const double* model, const bv_theta* theta0, const bv_theta* lo, const bv_theta* hi,
+                            uint32_t free_mask, const bv_mle_opts* opts, bv_theta* theta_hat, double* loglik_hat,
+                            int32_t* n_evals) {
+    if (!model || !theta0) return BV_EINVAL;
+    SyntheticEval ev;
+    ev.n = model[0];
+    ev.lb0 = log(model[1]);
+    ev.le0 = log(model[2]);
+    ev.cq = model[3];
+    ev.a = model[4];
+    ev.b = model[5];
+    ev.cuv = model[6];
+    ev.k = model[7];
+    if (!(ev.n > 0.0) || !(model[1] > 0.0) || !(model[2] > 0.0)) return BV_EINVAL;
+    bv_ctx* dummy = reinterpret_cast<bv_ctx*>(&ev);  // mle_search uses the context only as a non-null handle
+    return mle_search(dummy, &ev, ev.n, theta0, lo, hi, free_mask, opts, theta_hat, loglik_hat, n_evals);
+}
+
+// ------------------------------------------------------------------------------------
 // Many datasets at once.  Each dataset's search runs unchanged in its own host thread;
 // its evaluations meet at a barrier, and when every unfinished search is waiting one
 // batched evaluation (one graph launch over all datasets, per precision requested) scores
