@@ -481,8 +481,9 @@ int bv_mle_multi(bv_ctx* ctx, const bv_theta* theta0, const bv_theta* lo, const 
 
 /* The paper suggests warm-starting the estimation from a cheaper fit (Sec. 2.3: estimate
  * at small bc/m, reuse as the starting value).  The library adds a learned warm start: a
- * small MLP maps per-dataset summary features to a starting theta, and the cold-started
- * search remains the fallback and the judge of the final estimate. */
+ * small MLP maps per-dataset summary features to a starting theta.  The search is the
+ * same from either start; a cold start (an explicit theta0) needs no network, and its
+ * estimate is the standard the warm-started one must reproduce. */
 
 /* Features per dataset (BV_NFEAT floats):
  *   [0..31]  empirical semivariogram gamma_k / var(y) in 32 equal bins of the distance h on

@@ -2,8 +2,9 @@
 // statistics) and a small MLP trained and evaluated with this library's own kernels.
 //
 // The paper's non-learned heuristic (Sec. 2.3) is to start the estimation from a
-// cheaper fit; here a network maps summary features to a starting theta, and the
-// cold-started Nelder-Mead search stays the fallback and the judge (bv_mle).
+// cheaper fit; here a network maps summary features to a starting theta.  The same
+// search (bv_mle) runs from either start, and its cold-started result is the standard
+// that the warm-started estimate must reproduce.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
