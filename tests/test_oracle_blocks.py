@@ -170,6 +170,61 @@ def test_block_order_is_a_seeded_permutation():
     assert not np.array_equal(a[1], c[1])
 
 
+ZETA_STREAM = 0x7A6574615F6F7264  # the ASCII bytes of "zeta_ord"
+
+
+def fisher_yates(count, seed):
+    """The block permutation written out from its stated rule, in plain Python integers:
+    start from the identity; for i = count - 1 down to 1 take r_i = SplitMix64 output i of
+    the stream seed ^ "zeta_ord", j = floor(r_i (i + 1) / 2^64) (uniform on 0 .. i), and
+    swap entries i and j."""
+    perm = list(range(count))
+    stream = seed ^ ZETA_STREAM
+    for i in range(count - 1, 0, -1):
+        j = (oracle.splitmix64(stream, i) * (i + 1)) >> 64
+        perm[i], perm[j] = perm[j], perm[i]
+    return perm
+
+
+@pytest.mark.parametrize("n,d,bc,seed", [(1500, 2, 150, 4), (600, 3, 60, 77)])
+def test_block_order_follows_the_fisher_yates_rule(n, d, bc, seed):
+    # the non-empty K-means clusters in cluster-index order, shuffled by the stated rule:
+    # block position p holds cluster perm[p], its points ascending
+    locs = synth.locs_uniform(n, d, seed=seed + 2)
+    label, _ = oracle.kmeans(locs, bc, seed, iters=20)
+    clusters = [c for c in (np.flatnonzero(label == k) for k in range(bc)) if len(c)]
+    bp, pi, _ = oracle.build_blocks(locs, bc, seed, iters=20)
+    assert len(bp) - 1 == len(clusters)
+    for p, k in enumerate(fisher_yates(len(clusters), seed)):
+        np.testing.assert_array_equal(pi[bp[p]:bp[p + 1]], clusters[k])
+
+
+@pytest.mark.parametrize("n,seed", [(1, 3), (2, 0), (57, 9), (1000, 123456789)])
+def test_singleton_and_random_orders_follow_the_fisher_yates_rule(n, seed):
+    locs = synth.locs_uniform(n, 2, seed=seed + 1)
+    bp, pi, ce = oracle.build_singletons(locs, seed)
+    np.testing.assert_array_equal(pi, fisher_yates(n, seed))
+    np.testing.assert_array_equal(bp, np.arange(n + 1))
+    np.testing.assert_array_equal(ce, locs[pi])
+    np.testing.assert_array_equal(oracle.order_blocks(locs, "random", seed=seed), fisher_yates(n, seed))
+
+
+def test_block_order_law_is_uniform():
+    # a random block ordering makes every order equally likely: over 4,800 seeds each of
+    # the 24 orders of four singletons appears about 200 times (chi-square with 23 degrees
+    # of freedom within 5 sd).  A shuffle that never draws j = i (Sattolo's) yields only
+    # the 6 cyclic orders, one that draws j from all positions is biased.
+    locs = synth.locs_uniform(4, 2, seed=1)
+    counts = {}
+    for seed in range(4800):
+        key = tuple(oracle.build_singletons(locs, seed)[1].tolist())
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 24
+    e = 4800 / 24
+    chi2 = sum((v - e) ** 2 / e for v in counts.values())
+    assert chi2 < 23 + 5 * math.sqrt(2 * 23), chi2
+
+
 def _brute_nn(locs, bp, pi, ce, m):
     out = []
     for i in range(len(bp) - 1):

@@ -44,6 +44,12 @@ MUTANTS = {
     "maxmin ties to the highest position": ("if (!used[p] && dmin[p] > far)", "if (!used[p] && dmin[p] >= far)"),
     "KD-tree split at the wrong axis": ("const int ax = depth % d;", "const int ax = (depth + 1) % d;"),
     "Morton with the axes' bits swapped": ("<< (b * d + a);", "<< (b * d + (d - 1 - a));"),
+    "block order by Sattolo's shuffle (j < i)": (
+        "int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)i), (uint64_t)(i + 1));\n        int64_t t = perm[i];",
+        "int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)i), (uint64_t)i);\n        int64_t t = perm[i];"),
+    "block order drawn from the wrong stream position": (
+        "int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)i), (uint64_t)(i + 1));\n        int64_t t = perm[i];",
+        "int64_t j = (int64_t)or_mulhi(or_sm64(zs, (uint64_t)(i - 1)), (uint64_t)(i + 1));\n        int64_t t = perm[i];"),
     "k-means++ drawn proportional to D": [("W += (uint64_t)ldexp(D2[i], s);", "W += (uint64_t)ldexp(sqrt(D2[i]), s);"),
                                           ("pre += (uint64_t)ldexp(D2[i], s);",
                                            "pre += (uint64_t)ldexp(sqrt(D2[i]), s);")],
@@ -207,10 +213,21 @@ def _pin_kmeanspp():
     return bool((cent == locs[kmeanspp_picks(locs, 8, 21)]).all())
 
 
+def _pin_block_order():
+    from tests.test_oracle_blocks import fisher_yates
+    locs = synth.locs_uniform(400, 2, 6)
+    label, _ = oracle.kmeans(locs, 40, 11, iters=5)
+    clusters = [c for c in (np.flatnonzero(label == k) for k in range(40)) if len(c)]
+    bp, pi, _ = oracle.build_blocks(locs, 40, seed=11, iters=5)
+    return len(bp) - 1 == len(clusters) and all(
+        np.array_equal(pi[bp[p]:bp[p + 1]], clusters[k]) for p, k in enumerate(fisher_yates(len(clusters), 11)))
+
+
 PINS = {"hilbert adjacency": _pin_hilbert, "orderings": _pin_orders, "kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
         "conditional-simulation normals": _pin_csim_normal, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
-        "K-means exact tie": _pin_kmeans_tie, "k-means++ seeding rule": _pin_kmeanspp}
+        "K-means exact tie": _pin_kmeans_tie, "k-means++ seeding rule": _pin_kmeanspp,
+        "block order rule": _pin_block_order}
 
 
 def _pins():
