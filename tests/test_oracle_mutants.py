@@ -39,6 +39,9 @@ MUTANTS = {
         "key.idx = (int32_t)j;", "key.idx = (int32_t)(j > 0 ? j - 1 : 0);"),
     "Box-Muller radius without the factor 2": ("sqrt(-2.0 * log(u1))", "sqrt(-1.0 * log(u1))"),
     "Box-Muller pair reuses the cosine": ("rho * sin(2.0 * M_PI * u2)", "rho * cos(2.0 * M_PI * u2)"),
+    "conditional-simulation pairs without the location offset": (
+        "const uint64_t c = (uint64_t)j * half + (uint64_t)(r / 2);",
+        "const uint64_t c = (uint64_t)j + (uint64_t)(r / 2);"),
     "Hilbert without the Gray encoding": ("for (int i = 1; i < d; i++) X[i] ^= X[i - 1];",
                                           "for (int i = 1; i < d; i++) X[i] ^= 0;"),
     "maxmin ties to the highest position": ("if (!used[p] && dmin[p] > far)", "if (!used[p] && dmin[p] >= far)"),
@@ -172,6 +175,12 @@ def _pin_csim_normal():
     return stats.kstest(z, "norm").pvalue > 1e-3 and abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(len(a))
 
 
+def _pin_csim_rule():
+    from tests.test_oracle_predict import csim_normal_rule
+    return all(oracle.csim_normal(9, j, 11, r) == pytest.approx(csim_normal_rule(9, j, 11, r), rel=1e-14, abs=1e-15)
+               for j in (0, 1, 5) for r in range(11))
+
+
 def _pin_hilbert():
     import itertools
     cells = np.array(list(itertools.product(range(16), repeat=2)), np.uint64)
@@ -224,7 +233,7 @@ def _pin_block_order():
 
 
 PINS = {"hilbert adjacency": _pin_hilbert, "orderings": _pin_orders, "kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
-        "conditional-simulation normals": _pin_csim_normal, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
+        "conditional-simulation normals": _pin_csim_normal, "conditional-simulation draw rule": _pin_csim_rule, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
         "K-means exact tie": _pin_kmeans_tie, "k-means++ seeding rule": _pin_kmeanspp,
         "block order rule": _pin_block_order}

@@ -4,6 +4,8 @@ univariate conditional simulation (Sec. 2.4; PICP, Sec. 3.2).
 Each check compares the oracle with something the mathematics fixes, computed by a
 different route: dense kriging by library solves, SciPy's Gaussian density, brute-force
 neighbour ranking, and the normal distribution's CDF."""
+import math
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -136,6 +138,29 @@ def test_csim_normals_are_standard_normal():
     assert stats.kstest(a * a + b * b, "expon", args=(0, 2)).pvalue > 1e-3
     assert oracle.csim_normal(9, 0, 10, 5) != oracle.csim_normal(10, 0, 10, 5)
     assert oracle.csim_normal(9, 1, 10, 0) != oracle.csim_normal(9, 0, 10, 0)
+
+
+def csim_normal_rule(seed, j, rounds, r):
+    """Normal r of new location j written out from its stated rule: pair k = r // 2 of
+    location j takes SplitMix64 draws 2c and 2c + 1 of the stream seed ^ "condsim_", with
+    c = j ceil(R / 2) + k; u1 = 1 - (x >> 11) 2^-53, u2 = (x' >> 11) 2^-53; the even member
+    is sqrt(-2 ln u1) cos(2 pi u2), the odd one the same with sin."""
+    stream = seed ^ 0x636F6E6473696D5F          # the ASCII bytes of "condsim_"
+    c = j * ((rounds + 1) // 2) + r // 2
+    u1 = 1.0 - (oracle.splitmix64(stream, 2 * c) >> 11) * 2.0 ** -53
+    u2 = (oracle.splitmix64(stream, 2 * c + 1) >> 11) * 2.0 ** -53
+    rho = math.sqrt(-2.0 * math.log(u1))
+    return rho * (math.cos(2.0 * math.pi * u2) if r % 2 == 0 else math.sin(2.0 * math.pi * u2))
+
+
+@pytest.mark.parametrize("rounds", [1000, 1001, 2])
+def test_csim_normal_follows_its_stated_rule(rounds):
+    # every draw of the first and of a later location, and the location offsets: draws
+    # of different locations never share a pair
+    for seed, j in ((9, 0), (9, 1), (12345, 777)):
+        for r in list(range(min(rounds, 40))) + [rounds - 2, rounds - 1]:
+            want = csim_normal_rule(seed, j, rounds, r)
+            assert oracle.csim_normal(seed, j, rounds, r) == pytest.approx(want, rel=1e-14, abs=1e-15)
 
 
 def test_cond_sim_interval_and_coverage():
