@@ -160,6 +160,30 @@ def test_blocks_partition_and_centroids(n, d, bc):
     assert (np.argmin(D, axis=1) == own).mean() > 0.97
 
 
+def integer_mean(values, n, amax):
+    """A block centroid coordinate written out from its stated rule, in Python integers:
+    q = 61 - ceil(log2 n) - (e + 1), where 2^(e-1) <= max |coordinate| < 2^e over the
+    dataset of n points; S = the sum of the members' x 2^q, each rounded to the nearest
+    integer (ties to even); the centroid is (S / count, one rounded division) 2^-q."""
+    q = 61 - _ceil_log2(n) - (math.frexp(amax)[1] + 1)
+    S = sum(round(math.ldexp(float(v), q)) for v in values)
+    return math.ldexp(float(S) / len(values), -q)
+
+
+@pytest.mark.parametrize("n,d,bc,shift,scale", [(2000, 2, 200, 0.0, 1.0), (900, 3, 90, -0.5, 3.0),
+                                                (500, 1, 50, -7.25, 0.01)])
+def test_block_centroids_follow_the_integer_mean_rule(n, d, bc, shift, scale):
+    # bit for bit, with negative coordinates and other magnitudes: the exponent q follows
+    # the largest |coordinate|, so its choice shows in the last bits of every centroid
+    locs = synth.locs_uniform(n, d, seed=5) * scale + shift
+    bp, pi, ce = oracle.build_blocks(locs, bc, seed=3, iters=20)
+    amax = float(np.abs(locs).max())
+    for i in range(len(bp) - 1):
+        mem = pi[bp[i]:bp[i + 1]]
+        for k in range(d):
+            assert ce[i, k] == integer_mean(locs[mem, k], n, amax), (i, k)
+
+
 def test_block_order_is_a_seeded_permutation():
     locs = synth.locs_uniform(1000, 2, seed=3)
     a = oracle.build_blocks(locs, 100, seed=1)

@@ -30,6 +30,7 @@ MUTANTS = {
                                            "if (t <= best) { best = t; bi = (int32_t)c; }"),
     "centroid without the 2^-q scaling": ("cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q);",
                                           "cent[c * d + j] = ldexp((double)S[c * d + j] / (double)counts[c], -q + 1);"),
+    "centroid exponent q one bit short": ("*q_out = 61 - ln - (ea + 1);", "*q_out = 60 - ln - (ea + 1);"),
     "prediction cross-covariance with the nugget": (
         "locs_star + (int64_t)blk[k] * d, 0);", "locs_star + (int64_t)blk[k] * d, 1);"),
     "prediction covariance plus the correction": ("cov[r * b + c] -= t;", "cov[r * b + c] += t;"),
@@ -134,6 +135,15 @@ def _pin_centroids():
                for i in range(len(lbp) - 1))
 
 
+def _pin_centroid_rule():
+    from tests.test_oracle_blocks import integer_mean
+    locs = synth.locs_uniform(300, 2, 8) * 2.0 - 1.0
+    bp, pi, ce = oracle.build_blocks(locs, 30, seed=4, iters=5)
+    amax = float(np.abs(locs).max())
+    return all(ce[i, k] == integer_mean(locs[pi[bp[i]:bp[i + 1]], k], 300, amax)
+               for i in range(len(bp) - 1) for k in range(2))
+
+
 def _pin_kmeans_tie():
     # three collinear points; with the two seeded centres at the ends (iters = 0) the
     # middle point is exactly equidistant and must go to the lower centre index
@@ -235,6 +245,7 @@ def _pin_block_order():
 PINS = {"hilbert adjacency": _pin_hilbert, "orderings": _pin_orders, "kriging": _pin_kriging, "prediction neighbours": _pin_pred_neighbours,
         "conditional-simulation normals": _pin_csim_normal, "conditional-simulation draw rule": _pin_csim_rule, "matern": _pin_matern, "one block = Eq. 1": _pin_one_block, "dense precision": _pin_dense,
         "neighbours brute force": _pin_neighbours, "centroid = member mean": _pin_centroids,
+        "centroid integer-mean rule": _pin_centroid_rule,
         "K-means exact tie": _pin_kmeans_tie, "k-means++ seeding rule": _pin_kmeanspp,
         "block order rule": _pin_block_order}
 
