@@ -184,8 +184,9 @@ __global__ void k_gelu_fwd(const float* __restrict__ Y, float* __restrict__ Z, i
     if (i < n) Z[i] = gelu(Y[i]);
 }
 
-__global__ void k_gelu_bwd(const float* __restrict__ Y, const float* __restrict__ dZ, float* __restrict__ dY,
-                           int n) {
+// dZ and dY may be the same buffer (the backward pass scales a layer's gradient in place),
+// so neither is declared __restrict__; each thread reads and writes its own element only.
+__global__ void k_gelu_bwd(const float* __restrict__ Y, const float* dZ, float* dY, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dY[i] = dZ[i] * gelu_d(Y[i]);
 }
