@@ -320,21 +320,37 @@ def oracle_eval(parts, f=(1.0, 1.0, 1.0)):
         oracle.loglik(th, locs, y, bp, pi, nnp, nni, check=False)
 
 
-def cpu_oracle_sample(w, seconds=12.0):
-    """The FP64 oracle on a bounded sample of the workload (oracle_sample), repeated for
-    about `seconds`.  Returns evals/s of the FULL workload extrapolated by block count,
-    the sample description and the thread count."""
-    import oracle
-    parts, scale, desc = oracle_sample(w)
+def _time_oracle(parts, seconds):
+    """Repeat one oracle evaluation of the sample for about `seconds` (at least once):
+    (repetitions, seconds per evaluation)."""
     reps, t0 = 0, time.perf_counter()
     while True:
         oracle_eval(parts)
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds or reps >= 200:
-            break
-    per_eval_sample = el / reps
-    return (1.0 / (per_eval_sample * scale), f"{reps} evals of {desc}", oracle.num_threads(), per_eval_sample)
+            return reps, el / reps
+
+
+def cpu_oracle_sample(w, seconds=12.0, one_thread_seconds=4.0):
+    """The FP64 oracle on a bounded sample of the workload (oracle_sample), repeated for
+    about `seconds` on every host core, then for about `one_thread_seconds` on one thread
+    (skipped when 0).  Returns evals/s of the FULL workload extrapolated by block count,
+    the sample description, the thread count, the seconds per sample evaluation and the
+    one-thread figures (a dict, or None)."""
+    import oracle
+    parts, scale, desc = oracle_sample(w)
+    reps, per_eval_sample = _time_oracle(parts, seconds)
+    cores = oracle.num_threads()
+    one = None
+    if one_thread_seconds > 0:
+        oracle.set_num_threads(1)
+        try:
+            reps1, per1 = _time_oracle(parts, one_thread_seconds)
+        finally:
+            oracle.set_num_threads(cores)
+        one = {"value": 1.0 / (per1 * scale), "unit": UNIT, "cores": 1, "sample": f"{reps1} evals of {desc}"}
+    return (1.0 / (per_eval_sample * scale), f"{reps} evals of {desc}", cores, per_eval_sample, one)
 
 
 def run_reference(args, w):
@@ -901,8 +917,9 @@ def main():
                 extras["mle"] = {"error": repr(exc)}
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
-        v, sample, cores, per = cpu_oracle_sample(w)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v, sample, cores, per, one = cpu_oracle_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "one_thread": one}
 
     if rank == 0:
         line = {"metric": metric_of(w, args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

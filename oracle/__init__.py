@@ -137,6 +137,8 @@ def _bind(L):
                                       _P(_d), _P(_i64)]
             L.or_num_threads.restype = _int
             L.or_num_threads.argtypes = []
+            L.or_set_num_threads.restype = None
+            L.or_set_num_threads.argtypes = [_int]
     return L
 
 
@@ -183,6 +185,11 @@ class OracleError(RuntimeError):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """OpenMP threads for the oracle calls made from this thread from now on."""
+    lib().or_set_num_threads(int(k))
 
 
 def splitmix64(stream: int, counter: int) -> int:

@@ -1153,3 +1153,13 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads used by the parallel loops that the calling thread starts from now on (the
+ * CPU baseline is timed both on every host core and on one). */
+void or_set_num_threads(int k) {
+#ifdef _OPENMP
+    if (k >= 1) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}

@@ -41,3 +41,21 @@ def test_reference_arm_json(workload, unit):
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == unit
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    # the CPU-baseline leg of the GPU line: the oracle on every host core and on one
+    # thread, the thread count restored afterwards
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    oracle.build()
+    before = oracle.num_threads()
+    v, sample, cores, per, one = bench.cpu_oracle_sample(dict(bench.WORKLOADS["c2_m60"]), seconds=0.0,
+                                                         one_thread_seconds=0.0001)
+    assert oracle.num_threads() == before == cores
+    assert v > 0 and per > 0 and sample.startswith("1 evals of ")
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == "evals/s"
+    assert one["sample"].startswith("1 evals of ")
+    assert bench.cpu_oracle_sample(dict(bench.WORKLOADS["c2_m60"]), seconds=0.0, one_thread_seconds=0)[4] is None
