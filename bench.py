@@ -917,9 +917,12 @@ def main():
                 extras["mle"] = {"error": repr(exc)}
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
-        v, sample, cores, per, one = cpu_oracle_sample(w)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "one_thread": one}
+        try:
+            v, sample, cores, per, one = cpu_oracle_sample(w)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                   "one_thread": one}
+        except Exception as exc:  # reported, never hides the main line
+            cpu = {"kind": "oracle", "error": repr(exc)}
 
     if rank == 0:
         line = {"metric": metric_of(w, args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
