@@ -451,6 +451,19 @@ def run_mle(bv, ctx, w, log):
     return res
 
 
+def oracle_mle_estimate(wm, res, seconds=6.0):
+    """The FP64 oracle's MLE wall-time on the same workload, extrapolated: its time per
+    evaluation (cpu_oracle_sample on every host core) times the number of evaluations
+    that each FP64 search on the GPU needed.  Nothing of the search itself runs on the
+    CPU; the figure says what the same search would cost with the oracle as evaluator."""
+    v, sample, cores, _, _ = cpu_oracle_sample(wm, seconds=seconds, one_thread_seconds=0)
+    out = {"kind": "oracle, extrapolated", "evals_per_s": v, "cores": cores, "sample": sample}
+    for key in ("fp64_cold", "fp64_warm"):
+        if key in res:
+            out[f"{key}_wall_s"] = res[key]["evals"] / v
+    return out
+
+
 def pred_split(w):
     """Locations and the held-out mask (10%: SplitMix64 draw mod 10 == 0)."""
     locs = synth.locs_uniform(w["n"], w["d"], w["seed"])
@@ -904,6 +917,11 @@ def main():
         log(f"extras: {extras['other_precision']}")
         if args.workload == "c4_mle":
             extras["mle"] = run_mle(bv, ctx, w, log)
+            if not args.no_cpu:
+                try:
+                    extras["mle"]["cpu_oracle"] = oracle_mle_estimate(w, extras["mle"])
+                except Exception as exc:  # reported, never hides the main line
+                    extras["mle"]["cpu_oracle"] = {"error": repr(exc)}
         elif not args.no_mle and ws == 1 and args.workload == "c3":
             # the metric's second half: MLE wall-time on the n = 5e5 workload, in its own context
             wm = dict(WORKLOADS["c4_mle"])
@@ -915,6 +933,11 @@ def main():
                                          **run_mle(bv, mctx, wm, log))
             except Exception as exc:  # reported, never hides the main line
                 extras["mle"] = {"error": repr(exc)}
+            if not args.no_cpu and "error" not in extras["mle"]:
+                try:
+                    extras["mle"]["cpu_oracle"] = oracle_mle_estimate(wm, extras["mle"])
+                except Exception as exc:  # reported, never hides the main line
+                    extras["mle"]["cpu_oracle"] = {"error": repr(exc)}
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         try:

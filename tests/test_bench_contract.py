@@ -59,3 +59,17 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == "evals/s"
     assert one["sample"].startswith("1 evals of ")
     assert bench.cpu_oracle_sample(dict(bench.WORKLOADS["c2_m60"]), seconds=0.0, one_thread_seconds=0)[4] is None
+
+
+def test_oracle_mle_estimate_scales_the_gpu_call_counts():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    oracle.build()
+    res = {"fp64_cold": {"evals": 37}, "fp64_warm": {"evals": 19}, "mixed_cold": {"evals": 55}}
+    est = bench.oracle_mle_estimate(dict(bench.WORKLOADS["c4_mle"]), res, seconds=0.0)
+    assert est["kind"] == "oracle, extrapolated" and est["cores"] == oracle.num_threads()
+    assert est["fp64_cold_wall_s"] == 37 / est["evals_per_s"]
+    assert est["fp64_warm_wall_s"] == 19 / est["evals_per_s"]
+    assert "mixed_cold_wall_s" not in est
