@@ -513,8 +513,21 @@ int bv_features(bv_ctx* ctx, int32_t max_points, uint64_t seed, float* out);
  * X[n x BV_NFEAT], T[n x 4] = (log sigma^2, log beta, log tau^2, nu) (host).  Loss = mean
  * squared error of the standardised regression outputs / 3 + cross-entropy of the nu
  * class.  Mini-batches of `batch` from a seeded shuffle, `epochs` passes, Adam(lr, 0.9,
- * 0.999, 1e-8).  blob_out[BV_MLP_BLOB] receives the trained weights and standardisation;
- * loss_out[epochs] (may be NULL) the mean training loss per epoch. */
+ * 0.999, 1e-8) with its step count running across epochs.  blob_out[BV_MLP_BLOB] receives
+ * the trained weights and standardisation; loss_out[epochs] (may be NULL) the mean
+ * training loss per epoch.
+ *   Standardisation: per input column the mean and population standard deviation of X
+ *   (FP64 sums in row order, stored as float); a column whose deviation is at most
+ *   1e-6 (|mean| + 1) gets the scale 1e30.  The same for the three regression targets
+ *   (scale 1 below 1e-12).
+ *   Initial parameters: biases 0; every weight, in blob order, (2u - 1) a with
+ *   a = 1 / sqrtf(fan_in) (float) and u = (x_c >> 11) 2^-53, x_c = SplitMix64 draw c =
+ *   0, 1, 2, ... of the stream seed ^ 0x6d6c7077 ("mlpw"), rounded to float.
+ *   Shuffle: the row order starts as 0 .. n-1 and is carried from epoch to epoch; epoch e
+ *   (from 0) applies Fisher-Yates, for i = n-1 down to 1 swapping positions i and
+ *   j = floor(x_i (i + 1) / 2^64) with x_i = SplitMix64 draw i of the stream
+ *   seed + 1000003 (e + 1) (mod 2^64); the mini-batches are consecutive runs of `batch`
+ *   rows of that order, and a final partial run is skipped. */
 int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t epochs, int32_t batch, float lr,
                  uint64_t seed, float* blob_out, float* loss_out);
 

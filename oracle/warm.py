@@ -6,6 +6,7 @@ TEST INFRASTRUCTURE (see oracle/__init__.py).  Plain, slow definitions:
                  statistics, nearest-neighbour semivariance and distance)
   mlp_forward()  the MLP 40 -> 128 -> 128 -> 128 -> 6 with exact-erf GELU
   mlp_loss_grad()  the training loss and its gradient by explicit backpropagation
+  adam_step()    one step of Adam (Kingma and Ba 2015, Algorithm 1)
 """
 from __future__ import annotations
 
@@ -151,3 +152,16 @@ def mlp_loss_grad(blob, X, T):
             g = (g @ Ws[l].T) * _gelu_d(pres[l - 1])
     flat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in zip(grads_W, grads_b)])
     return loss, flat
+
+
+def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """Adam step t (t = 1, 2, ...; Kingma and Ba 2015, Algorithm 1): the biased first and
+    second moment estimates m <- b1 m + (1 - b1) g and v <- b2 v + (1 - b2) g^2, their
+    bias-corrected values m / (1 - b1^t) and v / (1 - b2^t), and the parameter update
+    theta <- theta - lr * mhat / (sqrt(vhat) + eps).  Returns (theta, m, v)."""
+    theta, g = np.asarray(theta, np.float64), np.asarray(g, np.float64)
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v

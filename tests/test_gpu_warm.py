@@ -2,6 +2,7 @@
 pass and backpropagated gradient against the FP64 oracle (relative error <= 1e-4 in
 FP32), training reduces the loss, and the trained network cuts the number of
 log-likelihood calls of the MLE while reaching the same optimum as the cold start."""
+import math
 import os
 
 import numpy as np
@@ -79,6 +80,88 @@ def test_training_reduces_loss(bv):
     # deterministic given the seed
     blob2, losses2 = bv.mlp_train(X, T.astype(np.float32), epochs=40, batch=128, lr=2e-3, seed=1)
     np.testing.assert_array_equal(losses, losses2)
+
+
+def _standardisation(X, T):
+    """The training set's standardisation by the documented rule (sequential FP64 sums,
+    population deviation, stored as float)."""
+    def col(v, tiny, big):
+        m = 0.0
+        for x in v:
+            m += float(x)
+        m /= len(v)
+        q = 0.0
+        for x in v:
+            q += (float(x) - m) * (float(x) - m)
+        sd = math.sqrt(q / len(v))
+        return np.float32(m), np.float32(sd if sd > tiny(m) else big)
+    xs = [col(X[:, k], lambda m: 1e-6 * (abs(m) + 1.0), 1e30) for k in range(warm.NFEAT)]
+    ts = [col(T[:, k], lambda m: 1e-12, 1.0) for k in range(3)]
+    return np.concatenate([[a for a, _ in xs], [b for _, b in xs], [a for a, _ in ts], [b for _, b in ts]])
+
+
+def _initial_parameters(seed):
+    """Initial weights by the documented rule: (2u - 1) / sqrtf(fan_in), u from SplitMix64
+    draws 0, 1, ... of the stream seed ^ "mlpw", in blob order; biases 0."""
+    P = np.zeros(warm.NPARAM, np.float32)
+    off, ctr, stream = 0, 0, seed ^ 0x6D6C7077
+    for i, o in warm.LAYERS:
+        a = float(np.float32(1.0) / np.sqrt(np.float32(i)))
+        for k in range(i * o):
+            u = (oracle.splitmix64(stream, ctr) >> 11) * 2.0 ** -53
+            P[off + k] = np.float32((2.0 * u - 1.0) * a)
+            ctr += 1
+        off += i * o + o
+    return P
+
+
+def _minibatches(n, batch, epochs, seed):
+    """Row sets of the training steps by the documented shuffle."""
+    order, out = list(range(n)), []
+    for ep in range(epochs):
+        stream = (seed + 1000003 * (ep + 1)) % 2 ** 64
+        for i in range(n - 1, 0, -1):
+            j = (oracle.splitmix64(stream, i) * (i + 1)) >> 64
+            order[i], order[j] = order[j], order[i]
+        out += [order[r:r + batch] for r in range(0, n - batch + 1, batch)]
+    return out
+
+
+def test_adam_training_matches_oracle(bv):
+    # bv_mlp_train's forward, backward and Adam kernels against the FP64 oracle: four
+    # mini-batch steps (two epochs of 2 x 24 rows, the row order reshuffled between them,
+    # so the moment estimates see different gradients), the oracle chain started from the
+    # documented initial weights and standardisation.  A small learning rate keeps the two
+    # chains on the same gradients: where a gradient entry is at FP32 noise its sign may
+    # differ, so parameters are compared where every step's oracle gradient is at least
+    # 0.1 of that step's RMS gradient.
+    rng = np.random.default_rng(12)
+    n, batch, epochs, lr, seed = 50, 24, 2, 1e-5, 77
+    X = rng.normal(size=(n, warm.NFEAT)).astype(np.float32)
+    T = np.column_stack([rng.normal(size=(n, 3)), rng.choice([0.5, 1.5, 2.5], n)]).astype(np.float32)
+    blob, _ = bv.mlp_train(X, T, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    std = _standardisation(X, T)
+    np.testing.assert_allclose(blob[:len(std)], std, rtol=1e-6)
+    P0 = _initial_parameters(seed)
+    P = P0.astype(np.float64)
+    m = v = np.zeros(warm.NPARAM)
+    det = np.ones(warm.NPARAM, bool)
+    steps = _minibatches(n, batch, epochs, seed)
+    assert len(steps) == 4
+    for t, rows in enumerate(steps, start=1):
+        _, g = warm.mlp_loss_grad(np.concatenate([std.astype(np.float64), P]), X[rows].astype(np.float64),
+                                  T[rows].astype(np.float64))
+        det &= np.abs(g) >= 0.1 * np.sqrt(np.mean(g * g))
+        P, m, v = warm.adam_step(P, g, m, v, t, lr)
+    got = blob[len(std):].astype(np.float64)
+    tol = 0.05 * lr + 3.0 * np.spacing(np.abs(P0)).astype(np.float64)
+    diff = np.abs(got - P)
+    print(f"compared {det.sum()} of {warm.NPARAM}; max |diff| / lr {diff[det].max() / lr:.3e}")
+    assert det.sum() > 2000
+    assert np.all(diff[det] <= tol[det]), (diff[det] / tol[det]).max()
+    # the parameters moved by Adam's steps of about lr each, never by more than 4 lr
+    assert np.median(np.abs(got - P0)[det]) > 0.5 * lr
+    assert np.all(np.abs(got - P0) <= 4 * lr * (1 + 1e-3) + tol)
 
 
 @pytest.mark.parametrize("prec_name", ["BV_FP64", "BV_MIXED"])

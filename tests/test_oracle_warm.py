@@ -95,3 +95,42 @@ def test_variogram_of_a_linear_field():
         d_nn += abs(xs[i] - xs[j])
     assert abs(f[38] - g_nn / n / var) <= 1e-12 * f[38]
     assert abs(f[39] - 64 * d_nn / n) <= 1e-12 * f[39]
+
+
+def test_adam_first_step_and_constant_gradient():
+    # the bias corrections make the first step (and every step under a constant gradient)
+    # move each parameter by lr g / (|g| + eps): a sign step of length lr up to eps
+    rng = np.random.default_rng(9)
+    th0 = rng.normal(size=50)
+    g = rng.normal(size=50) * np.logspace(-6, 2, 50)
+    lr, eps = 1e-3, 1e-8
+    th, m, v = th0, np.zeros(50), np.zeros(50)
+    for t in range(1, 11):
+        th, m, v = warm.adam_step(th, g, m, v, t, lr, eps=eps)
+        np.testing.assert_allclose(th, th0 - t * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_two_steps_closed_form():
+    # two gradients g1, g2: the bias-corrected moments are (b1 g1 + g2) / (1 + b1) and
+    # (b2 g1^2 + g2^2) / (1 + b2)
+    rng = np.random.default_rng(10)
+    th0, g1, g2 = rng.normal(size=(3, 40))
+    lr, b1, b2, eps = 2e-3, 0.9, 0.999, 1e-8
+    th1, m, v = warm.adam_step(th0, g1, np.zeros(40), np.zeros(40), 1, lr)
+    th2, _, _ = warm.adam_step(th1, g2, m, v, 2, lr)
+    mhat = (b1 * g1 + g2) / (1 + b1)
+    vhat = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    np.testing.assert_allclose(th2, th1 - lr * mhat / (np.sqrt(vhat) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_is_invariant_to_gradient_scale():
+    # with eps = 0 the trajectory does not change when every gradient is scaled by c > 0
+    rng = np.random.default_rng(11)
+    th0 = rng.normal(size=30)
+    gs = rng.normal(size=(6, 30))
+    a = b = th0
+    ma = va = mb = vb = np.zeros(30)
+    for t, g in enumerate(gs, start=1):
+        a, ma, va = warm.adam_step(a, g, ma, va, t, 1e-2, eps=0.0)
+        b, mb, vb = warm.adam_step(b, 37.5 * g, mb, vb, t, 1e-2, eps=0.0)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-15)
