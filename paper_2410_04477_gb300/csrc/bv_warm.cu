@@ -573,13 +573,17 @@ extern "C" int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t e
     const int B = (int)std::min<int64_t>(batch, n);
     MLPWork w;
     BV_TRY(w.alloc(B));
-    float *dX = nullptr, *dT = nullptr, *m1 = nullptr, *m2 = nullptr;
-    BV_CUDA(cudaMalloc(&dX, sizeof(float) * n * BV_NFEAT));
-    BV_CUDA(cudaMalloc(&dT, sizeof(float) * n * 4));
-    BV_CUDA(cudaMalloc(&m1, sizeof(float) * BV_MLP_NPARAM));
-    BV_CUDA(cudaMalloc(&m2, sizeof(float) * BV_MLP_NPARAM));
-    BV_CUDA(cudaMemset(m1, 0, sizeof(float) * BV_MLP_NPARAM));
-    BV_CUDA(cudaMemset(m2, 0, sizeof(float) * BV_MLP_NPARAM));
+    struct Moments {  // Adam's first and second moment estimates, freed on every return path
+        float *m1 = nullptr, *m2 = nullptr;
+        ~Moments() {
+            cudaFree(m1);
+            cudaFree(m2);
+        }
+    } mom;
+    BV_CUDA(cudaMalloc(&mom.m1, sizeof(float) * BV_MLP_NPARAM));
+    BV_CUDA(cudaMalloc(&mom.m2, sizeof(float) * BV_MLP_NPARAM));
+    BV_CUDA(cudaMemset(mom.m1, 0, sizeof(float) * BV_MLP_NPARAM));
+    BV_CUDA(cudaMemset(mom.m2, 0, sizeof(float) * BV_MLP_NPARAM));
     BV_CUDA(cudaMemcpy(w.P, P, sizeof(float) * BV_MLP_NPARAM, cudaMemcpyHostToDevice));
     std::vector<int64_t> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -605,7 +609,7 @@ extern "C" int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t e
             BV_CUDA(backward(w, B));
             ++step;
             const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-            k_adam<<<nb(BV_MLP_NPARAM), 256>>>(w.P, w.G, m1, m2, BV_MLP_NPARAM, lr, b1, b2, eps, c1, c2);
+            k_adam<<<nb(BV_MLP_NPARAM), 256>>>(w.P, w.G, mom.m1, mom.m2, BV_MLP_NPARAM, lr, b1, b2, eps, c1, c2);
             BV_CUDA(cudaGetLastError());
             BV_CUDA(cudaMemcpy(lrow.data(), w.loss, sizeof(float) * B, cudaMemcpyDeviceToHost));
             for (float v : lrow) lsum += v;
@@ -614,10 +618,6 @@ extern "C" int bv_mlp_train(const float* X, const float* T, int64_t n, int32_t e
         if (loss_out) loss_out[ep] = (float)(lsum / std::max<int64_t>(1, nb_ep * B));
     }
     BV_CUDA(cudaMemcpy(P, w.P, sizeof(float) * BV_MLP_NPARAM, cudaMemcpyDeviceToHost));
-    cudaFree(dX);
-    cudaFree(dT);
-    cudaFree(m1);
-    cudaFree(m2);
     return BV_OK;
 }
 

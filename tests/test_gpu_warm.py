@@ -1,7 +1,8 @@
 """GPU parity of the learned warm start: features against the oracle, the MLP's forward
 pass and backpropagated gradient against the FP64 oracle (relative error <= 1e-4 in
-FP32), training reduces the loss, and the trained network cuts the number of
-log-likelihood calls of the MLE while reaching the same optimum as the cold start."""
+FP32), training reduces the loss, four Adam training steps match the oracle's Adam chain,
+and the trained network cuts the number of log-likelihood calls of the MLE while reaching
+the same optimum as the cold start."""
 import math
 import os
 
